@@ -1,0 +1,264 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a textbook closed form, a
+brute-force computation by an independent route, an exactness property stated
+by the paper, or an invariant of the mathematics.  No GPU is used.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+from scipy.special import comb
+
+from oracle import bspline, closed_form, galerkin, ibq
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------------------
+# Univariate B-splines (Sec. 2.3) -- textbook special cases
+# ---------------------------------------------------------------------------------------
+def test_knots_and_greville_textbook():
+    t = bspline.open_uniform_knots(2, 2)
+    assert np.array_equal(t, [0, 0, 0, 0.5, 1, 1, 1])
+    # Greville abscissae of quadratic splines on knots (0,0,0,.5,1,1,1): 0, 1/4, 3/4, 1
+    assert np.allclose(bspline.greville(t, 2), [0.0, 0.25, 0.75, 1.0], atol=0, rtol=0)
+    assert bspline.dimension(bspline.open_uniform_knots(3, 48), 3) == 51
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
+def test_single_element_basis_is_bernstein(p):
+    """With one element the B-splines are the Bernstein polynomials C(p,i) x^i (1-x)^(p-i)."""
+    t = bspline.open_uniform_knots(p, 1)
+    x = np.linspace(0.0, 1.0, 17)
+    B = bspline.basis_matrix(t, p, x)
+    ref = np.stack([comb(p, i) * x ** i * (1 - x) ** (p - i) for i in range(p + 1)], axis=1)
+    assert np.abs(B - ref).max() < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
+def test_bernstein_mass_matrix_closed_form(p):
+    """Bernstein Gram matrix: int B_i B_j = C(p,i) C(p,j) / ((2p+1) C(2p, i+j))."""
+    Z = bspline.gramian(bspline.open_uniform_knots(p, 1), p)
+    ref = np.array([[comb(p, i) * comb(p, j) / ((2 * p + 1) * comb(2 * p, i + j))
+                     for j in range(p + 1)] for i in range(p + 1)])
+    assert np.abs(Z - ref).max() < 1e-15
+
+
+def test_linear_mass_matrix_textbook():
+    """Hat functions on a uniform mesh: h/6 * tridiag(1, 4, 1) with 2 at both ends."""
+    ne = 6
+    h = 1.0 / ne
+    Z = bspline.gramian(bspline.open_uniform_knots(1, ne), 1)
+    ref = np.diag([4.0] * (ne + 1)) + np.diag([1.0] * ne, 1) + np.diag([1.0] * ne, -1)
+    ref[0, 0] = ref[-1, -1] = 2.0
+    assert np.abs(Z - h / 6.0 * ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("p,ne", [(2, 7), (3, 5), (4, 9)])
+def test_spline_identities(p, ne):
+    t = bspline.open_uniform_knots(p, ne)
+    n = bspline.dimension(t, p)
+    x = np.linspace(0, 1, 101)
+    B = bspline.basis_matrix(t, p, x)
+    assert np.abs(B.sum(axis=1) - 1.0).max() < 1e-14          # partition of unity
+    assert B.min() >= 0.0
+    xi = bspline.greville(t, p)
+    assert np.abs(B @ xi - x).max() < 1e-14                   # linear precision of Greville abscissae
+    Z = bspline.gramian(t, p)
+    integrals = np.array([(t[i + p + 1] - t[i]) / (p + 1) for i in range(n)])
+    assert np.abs(Z.sum(axis=1) - integrals).max() < 1e-15   # int B_i = (t_{i+p+1}-t_i)/(p+1)
+    assert np.abs(Z - Z.T).max() < 1e-16
+    assert np.linalg.eigvalsh(Z).min() > 0
+    Bt = bspline.collocation_matrix(t, p)
+    assert np.abs(Bt.sum(axis=1) - 1.0).max() < 1e-14
+    assert np.abs(Bt @ xi - xi).max() < 1e-14
+
+
+def test_mixed_mass_matrix():
+    """M_k = int B~_i B_j: equals Z when the spaces coincide; sums to |[0,1]| = 1 in general."""
+    t = bspline.open_uniform_knots(2, 6)
+    assert np.abs(bspline.mass_matrix(t, 2, t, 2) - bspline.gramian(t, 2)).max() < 1e-16
+    tt = bspline.open_uniform_knots(3, 9)
+    M = bspline.mass_matrix(tt, 3, t, 2)
+    assert abs(M.sum() - 1.0) < 1e-14
+    # row i integrates B~_i against sum_j B_j = 1
+    assert np.abs(M.sum(axis=1) - [(tt[i + 4] - tt[i]) / 4 for i in range(M.shape[0])]).max() < 1e-15
+
+
+def test_galerkin_gramian_matches_kron():
+    """Two independent quadrature codes: tensor Gauss over all elements vs Kronecker of 1D Z_k."""
+    P = ibq.Problem(2, [2, 3], [3, 2], kernel="gauss", L=0.5)
+    _, Zg = galerkin.galerkin_matrices(P, q=4)
+    assert np.abs(Zg - P.kron("Z")).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------------------
+# Closed-form 1D spectrum (Remark in Sec. 6.1) pinned by a brute-force Nystrom solve
+# ---------------------------------------------------------------------------------------
+def nystrom_exp_1d(num, ell, panels=400, q=8):
+    x, w = [], []
+    for a in range(panels):
+        xg, wg = bspline.gauss_legendre(q, a / panels, (a + 1) / panels)
+        x.append(xg)
+        w.append(wg)
+    x, w = np.concatenate(x), np.concatenate(w)
+    K = np.exp(-np.abs(x[:, None] - x[None, :]) / ell)
+    sw = np.sqrt(w)
+    vals = np.linalg.eigvalsh(sw[:, None] * K * sw[None, :])
+    return vals[::-1][:num]
+
+
+@pytest.mark.parametrize("ell", [1.0, 0.3])
+def test_closed_form_matches_nystrom(ell):
+    lam = closed_form.exp_kernel_1d(10, ell)
+    ny = nystrom_exp_1d(10, ell)
+    assert np.abs(lam - ny).max() / lam[0] < 2e-6
+    assert np.all(np.diff(lam) < 0)
+    assert lam.sum() < 1.0  # sum of all eigenvalues equals sigma^2 |D| = 1
+
+
+def test_closed_form_golden():
+    with open(os.path.join(GOLDEN, "exp_kernel_closed_form.json")) as f:
+        g = json.load(f)
+    lam = closed_form.exp_kernel_1d(len(g["unit_interval_ell1"]), 1.0)
+    assert np.abs(lam - np.array(g["unit_interval_ell1"])).max() < 1e-15
+    prod = closed_form.exp_separable_box(len(g["unit_square_ell1"]), 1.0, [1.0, 1.0])
+    assert np.abs(prod - np.array(g["unit_square_ell1"])).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------------------
+# IBQ machinery (Sec. 4.2-4.3): exact on its target space
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,p,ne,pt,net,m,lo,hi", [
+    (1, 2, 5, None, None, 2, [0.0], [1.0]),
+    (1, 3, 4, 3, 6, 3, [-1.0], [2.0]),
+    (2, [2, 1], [3, 4], None, None, 1, [0.0, 0.0], [1.0, 1.0]),
+    (2, 2, [3, 2], [3, 2], [4, 3], 2, [0.5, -1.0], [2.0, 1.5]),
+])
+def test_ibq_exact_for_kernel_in_target_space(dim, p, ne, pt, net, m, lo, hi):
+    """A kernel whose pull-back G lies in B~ (x) B~ is integrated exactly (Sec. 4.2, end of Sec. 4.3).
+
+    The polynomial kernel prod_k (1 + x_k x'_k)^m with m <= p~ and an affine map is such a kernel,
+    so the IBQ matrix A~ must equal the brute-force Gauss Galerkin matrix A."""
+    P = ibq.Problem(dim, p, ne, kernel="poly", L=m, pt=pt, net=net, lo=lo, hi=hi)
+    At = P.dense()["At"]
+    pmax = max(d.p for d in P.dirs)
+    A, _ = galerkin.galerkin_matrices(P, q=pmax + m + 1)
+    assert np.abs(At - A).max() / np.abs(A).max() < 1e-12
+
+
+def test_ibq_error_decreases_for_gaussian():
+    """Outside the target space IBQ is an approximation that converges under refinement."""
+    errs = []
+    for net in (2, 4, 8):
+        P = ibq.Problem(1, 2, 3, kernel="gauss", L=0.5, pt=3, net=net)
+        At = P.dense()["At"]
+        A, _ = galerkin.galerkin_matrices(P, q=12)
+        errs.append(np.linalg.norm(At - A, 2) / np.linalg.norm(A, 2))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-4
+
+
+# ---------------------------------------------------------------------------------------
+# Reformulation (Sec. 4.1) and the Kronecker structure (Sec. 2.2)
+# ---------------------------------------------------------------------------------------
+def test_generalized_equals_standard():
+    P = ibq.Problem(2, 2, [4, 6], kernel="exp", L=0.7)
+    D = P.dense()
+    wg, Vg = ibq.generalized_eigs(D["At"], D["Z"])
+    ws, Vs = ibq.standard_eigs(0.5 * (D["Ap"] + D["Ap"].T))
+    assert np.abs(wg - ws).max() / ws[0] < 1e-13
+    # v' = L^T v maps Z-orthonormal generalized vectors to orthonormal standard ones
+    Vp = D["L"].T @ Vg
+    assert np.abs(Vp.T @ Vp - np.eye(P.N)).max() < 1e-11
+
+
+def test_separable_kernel_gives_kronecker_spectrum_2d():
+    """Identity map + separable kernel: A~' = A~'_2 (x) A~'_1, so the 2D spectrum is all 1D products.
+
+    Different meshes per direction make a transposed Kronecker order fail."""
+    P = ibq.Problem(2, [2, 3], [5, 7], kernel="exp_sep", L=0.8)
+    w2 = np.linalg.eigvalsh(P.dense_operator())[::-1]
+    w_1 = np.linalg.eigvalsh(ibq.Problem(1, 2, 5, kernel="exp", L=0.8).dense_operator())
+    w_2 = np.linalg.eigvalsh(ibq.Problem(1, 3, 7, kernel="exp", L=0.8).dense_operator())
+    prods = np.sort(np.outer(w_2, w_1).ravel())[::-1]
+    assert np.abs(w2 - prods).max() / w2[0] < 1e-13
+
+
+def test_separable_gaussian_3d_kronecker_spectrum():
+    P = ibq.Problem(3, 2, [2, 3, 4], kernel="gauss", L=0.6)
+    w3 = np.linalg.eigvalsh(P.dense_operator())[::-1]
+    ws = [np.linalg.eigvalsh(ibq.Problem(1, 2, ne, kernel="gauss", L=0.6).dense_operator()) for ne in (2, 3, 4)]
+    prods = np.sort(np.einsum("i,j,k->ijk", ws[2], ws[1], ws[0]).ravel())[::-1]
+    assert np.abs(w3 - prods).max() / w3[0] < 1e-13
+
+
+def test_matrix_free_algorithm_matches_dense():
+    """Algorithm 1 stage by stage (mode contractions, triangular/LU solves, on-the-fly Gamma)."""
+    P = ibq.Problem(3, [2, 2, 3], [3, 4, 2], kernel="exp", L=0.5, pt=[3, 2, 3], net=[4, 4, 3],
+                    lo=[0, 0, 0], hi=[1.0, 2.0, 0.5])
+    Ap = P.dense()["Ap"]
+    v = np.random.default_rng(3).standard_normal((P.N, 3))
+    y = P.apply(v, stage5_rows=37)
+    ref = Ap @ v
+    assert np.abs(y - ref).max() / np.abs(ref).max() < 1e-12
+    y2 = P.backward(P.stage5(P.points_and_J()[0], P.forward(v)))
+    assert np.abs(y2 - ref).max() / np.abs(ref).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# Convergence to the closed form and invariants
+# ---------------------------------------------------------------------------------------
+def test_convergence_to_closed_form_1d():
+    """Discrete IBQ eigenvalues approach the analytic ones under h-refinement (Sec. 6.1)."""
+    ref = closed_form.exp_kernel_1d(5, 1.0)
+    errs = []
+    for ne in (10, 20, 40, 80):
+        w = np.linalg.eigvalsh(ibq.Problem(1, 2, ne, kernel="exp", L=1.0).dense_operator())[::-1][:5]
+        errs.append(np.abs(w - ref).max() / ref[0])
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 5e-5
+    # the observed order is at least that of the h^{3/2} interpolation estimate (caption of Fig. 3b)
+    assert math.log2(errs[-2] / errs[-1]) > 1.4
+
+
+def test_unit_square_config_against_closed_form():
+    """The 2D unit-square, p=2, 20x20, separable exponential (sigma=L=1) top-10 vs 1D-product closed form."""
+    P = ibq.Problem(2, 2, 20, kernel="exp_sep", L=1.0)
+    w = np.linalg.eigvalsh(P.dense_operator())[::-1][:10]
+    ref = closed_form.exp_separable_box(10, 1.0, [1.0, 1.0])
+    assert np.abs(w - ref).max() / ref[0] < 2e-3   # IBQ eigenvalue error at h = 1/20 is ~1e-3
+
+
+def test_invariants():
+    P = ibq.Problem(2, 2, [6, 5], kernel="exp", L=0.5)
+    Ap = P.dense()["Ap"]
+    assert np.abs(Ap - Ap.T).max() / np.abs(Ap).max() < 1e-14        # symmetric
+    w = np.linalg.eigvalsh(0.5 * (Ap + Ap.T))
+    assert w.min() > -1e-14 * w.max()                                  # PSD (congruence with Gamma)
+    assert w[::-1][:20].sum() <= 1.0 * (1 + 1e-6)                      # sum_k lambda_k <= sigma^2 |D|
+    # trace of A~' is the discrete total variance; it tends to int Gamma(x, x) dx = sigma^2 |D| = 1
+    errs = [abs(np.trace(ibq.Problem(1, 2, ne, kernel="exp", L=0.5).dense_operator()) - 1.0)
+            for ne in (5, 10, 20, 40)]
+    assert all(a > b for a, b in zip(errs, errs[1:])) and errs[-1] < 0.01
+
+
+def test_similarity_scaling():
+    """Scaling the box and L by s scales every eigenvalue by s^d exactly (J = s^{d/2})."""
+    s = 2.0
+    P1 = ibq.Problem(2, 2, [4, 3], kernel="exp", L=0.5)
+    Ps = ibq.Problem(2, 2, [4, 3], kernel="exp", L=0.5 * s, lo=[0, 0], hi=[s, s])
+    w1 = np.linalg.eigvalsh(P1.dense_operator())
+    ws = np.linalg.eigvalsh(Ps.dense_operator())
+    assert np.abs(ws - s ** 2 * w1).max() / ws.max() < 1e-13
+
+
+def test_cube_symmetry_multiplicities():
+    """Euclidean exponential kernel on the unit cube: eigenvalue clusters of size 1, 2 or 3 from cube symmetry."""
+    P = ibq.Problem(3, 2, 3, kernel="exp", L=0.5)
+    w = np.linalg.eigvalsh(P.dense_operator())[::-1][:10]
+    assert abs(w[1] - w[2]) / w[0] < 1e-13 and abs(w[2] - w[3]) / w[0] < 1e-13
