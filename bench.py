@@ -1,0 +1,305 @@
+"""Benchmark: time to the 20 leading Karhunen-Loeve eigenpairs at relative residual 1e-8 and the
+kernel-evaluation rate, plain float64 block Lanczos vs the mixed-precision form, on the unit-cube
+workload (degree-2 splines, 32^3 elements, 34^3 = 39,304 Greville points, exponential kernel
+exp(-|x-x'|/L), sigma = 1, L = 0.5).
+
+One step = one complete eigensolve through the C ABI (kl_eigs): every operator application runs
+all nine stages of Algorithm 1 on the GPU.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+--impl reference times the CPU oracle (plain NumPy float64 stage-5 product on the host cores) on
+a bounded sample of the same workload, in the same unit.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 20 eigenpairs @res 1e-8 and kernel evals/s, chosen form vs plain FP64"
+UNIT = "kernel evals/s"
+DEFAULT_WORKLOAD = "cube-p2-32^3-exp-L0.5"
+TOL = 1e-8
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 vector rate (nominal)
+# algorithmic float64 flops of one kernel evaluation (paper's convention: one flop per add,
+# subtract, multiply; FMA = 2): distance 3 sub + 3 mul + 2 add, pre-scaled coordinates carry 1/L
+# (the 9th flop of the survey's count is folded into set-up); sqrt by one Heron correction
+# (mul, fma, mul, fma = 6); exp by Tang's method (fma, sub, fma, 4 fma + mul, fma = 16);
+# plus 2 flops per vector for the product.
+FLOPS_PER_PAIR = {"exp": 8 + 6 + 16, "gauss": 8 + 16, "exp_sep": 3 + 2 + 16, "poly": 12}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--plain-block", type=int, default=4)
+    ap.add_argument("--mixed-block", type=int, default=16)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(w, rows, seed=0):
+    """Kernel evaluations per second of the oracle's float64 stage-5 product on `rows` rows."""
+    import numpy as np
+
+    from oracle import ibq
+    from paper_2011_13861_gb300 import inputs
+    P = ibq.Problem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, 1, seed=seed)
+    idx = np.linspace(0, P.Nt - 1, rows).astype(np.int64)
+    t0 = time.perf_counter()
+    P.stage5(X, u, rows=256, row_index=idx)
+    dt = time.perf_counter() - t0
+    return rows * P.Nt / dt, dt, P.Nt
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2011_13861_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    rows = 2000
+    for _ in range(args.warmup):
+        oracle_rate(w, rows // 4)
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, dt, Nt = oracle_rate(w, rows)
+        rates.append(r)
+        secs.append(dt)
+    value = statistics.mean(rates)
+    sample = "%d of %d rows of the float64 stage-5 product (oracle.ibq.Problem.stage5), %d columns each" % (
+        rows, Nt, Nt)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "Ntilde": Nt, "L2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2011_13861_gb300 as kl
+    from paper_2011_13861_gb300 import inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    w = inputs.WORKLOADS[args.workload]
+    k = w["k"]
+    G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    N, Nt = G.N, G.Nt
+    # each rank solves its own instance (independent problems: weak scaling, no collective)
+    seed = 1 + rank
+    start_p = torch.from_numpy(inputs.random_block(N, args.plain_block, seed=seed).T.copy()).cuda()
+    start_m = torch.from_numpy(inputs.random_block(N, args.mixed_block, seed=seed).T.copy()).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def solve_plain():
+        return G.eigs(k, TOL, method=0, block=args.plain_block, start=start_p)
+
+    def solve_mixed():
+        return G.eigs(k, TOL, method=1, block=args.mixed_block, start=start_m)
+
+    for _ in range(args.warmup):
+        solve_plain()
+        solve_mixed()
+    torch.cuda.synchronize()
+
+    def timed(fn, clocks=None):
+        times, infos = [], []
+        if clocks:
+            clocks.start()
+        launches0 = kl.kernel_launches()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ev, vec, info = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append((ev, info))
+        if world > 1:
+            dist.barrier()
+        launches = kl.kernel_launches() - launches0
+        clk = clocks.stop() if clocks else None
+        return times, infos, launches, clk
+
+    clocks = ClockSampler(local)
+    t_plain, i_plain, launches_plain, clk = timed(solve_plain, clocks)
+    t_mixed, i_mixed, launches_mixed, _ = timed(solve_mixed)
+
+    ms_plain = statistics.mean(t_plain)
+    ms_mixed = statistics.mean(t_mixed)
+    if world > 1:
+        tt = torch.tensor([ms_plain, ms_mixed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_plain, ms_mixed = tt.tolist()
+    info_p = i_plain[-1][1]
+    info_m = i_mixed[-1][1]
+    ev_p, ev_m = i_plain[-1][0], i_mixed[-1][0]
+    applies_p = info_p["applies"]
+    value = world * applies_p * float(Nt) * Nt / (ms_plain * 1e-3)
+
+    # roofline of the dominant kernel (float64 stage 5) from the events recorded around it
+    fl = FLOPS_PER_PAIR[w["kernel"]]
+    calls = info_p["stage5_calls_fp64"]
+    ms5 = info_p["ms_stage5_fp64"] / max(calls, 1)
+    vecs_per_call = applies_p / max(calls, 1)
+    flops_per_launch = float(Nt) * Nt * (fl + 2 * vecs_per_call)
+    achieved = flops_per_launch / (ms5 * 1e-3) / 1e12
+    stage5_share = info_p["ms_stage5_fp64"] / ms_plain
+
+    # end to end through the public API with host buffers: create + H2D start block + solve + D2H vectors
+    def e2e_once():
+        t0 = time.perf_counter()
+        G2 = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+        host = torch.from_numpy(inputs.random_block(N, args.plain_block, seed=seed).T.copy()).pin_memory()
+        dev = host.to("cuda", non_blocking=True)
+        ev, vec, info = G2.eigs(k, TOL, method=0, block=args.plain_block, start=dev)
+        out = torch.empty((k, N), dtype=torch.float64).pin_memory()
+        out.copy_(vec, non_blocking=True)
+        torch.cuda.synchronize()
+        G2.close()
+        return time.perf_counter() - t0, info
+    e2e_t, e2e_info = e2e_once()
+    e2e_value = world * e2e_info["applies"] * float(Nt) * Nt / e2e_t
+
+    cpu = None
+    if rank == 0 and world == 1:
+        rows = 1500
+        r, dt, _ = oracle_rate(w, rows)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d of %d rows of the float64 stage-5 product (NumPy, single thread), %.1f s" % (
+                   rows, Nt, dt)}
+
+    peaks = read_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_plain, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "dim": w["dim"], "degree": w["p"], "elements": w["ne"],
+                   "kernel": w["kernel"], "L": w["L"], "sigma": w["sigma"], "N": N, "Ntilde": Nt, "k": k,
+                   "tol": TOL, "plain": "float64 thick-restart block Lanczos, block %d" % args.plain_block,
+                   "L2": "flushed between steps (256 MB write)"},
+        "time_to_solution_s": {"plain_fp64": ms_plain / 1e3, "chosen_mixed": ms_mixed / 1e3,
+                               "speedup": ms_plain / ms_mixed},
+        "plain_fp64": {"applies": applies_p, "block_applies": info_p["block_applies"],
+                       "restarts": info_p["restarts"], "max_resid": max(info_p["resid"]),
+                       "evals_per_s": value, "eigenvalues": [float(x) for x in ev_p]},
+        "chosen_form": {"method": "float32 stage-5 block Lanczos (block %d) + float64 polish" % args.mixed_block,
+                        "ms": ms_mixed, "applies": info_m["applies"], "applies_fp64": info_m["applies_fp64"],
+                        "max_resid": max(info_m["resid"]),
+                        "max_rel_eig_diff_vs_plain": float(np.max(np.abs(ev_m - ev_p) / np.abs(ev_p))),
+                        "evals_per_s": world * info_m["applies"] * float(Nt) * Nt / (ms_mixed * 1e-3),
+                        "ms_fp32_phase": info_m["ms_fp32_phase"],
+                        "stage5_fp32_ms_per_call": info_m["ms_stage5_fp32"] / max(info_m["stage5_calls_fp32"], 1),
+                        "stage5_fp64_ms_per_call": info_m["ms_stage5_fp64"] / max(info_m["stage5_calls_fp64"], 1)},
+        "roofline": {"bound": "alu", "kernel": "covmv64_kernel (float64 stage 5, exponential)",
+                     "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "peak_source": "nominal GB300 FP64 vector rate (recipe table); not in MEASURED_PEAKS.json",
+                     "flops_per_pair": fl, "ms_per_launch": ms5, "launches": calls,
+                     "stage5_share_of_step": stage5_share},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * args.plain_block * 8,
+                "d2h_bytes_per_step": k * N * 8 + k * 8, "seconds": e2e_t},
+        "gpu_launches": launches_plain,
+        "clocks": clk,
+        "peaks_file": {k2: peaks.get(k2) for k2 in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

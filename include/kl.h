@@ -1,0 +1,201 @@
+/*
+ * kl.h -- C ABI of the GB300 matrix-free isogeometric Karhunen-Loeve operator.
+ *
+ * The library computes the discrete Karhunen-Loeve eigenpairs of a covariance
+ * kernel with the interpolation-based-quadrature (IBQ) Galerkin method of
+ * Mika, Hughes, Schillinger, Wriggers, Hiemstra (arXiv 2011.13861):
+ *
+ *   standard-form operator (Sec. 4.4.1):
+ *     A~' = L^{-1} M^T B~^{-1} J Gamma J B~^{-T} M L^{-T}
+ *   with the univariate Kronecker factors Z_k = L_k L_k^T (Sec. 4.1, eq. cholesky),
+ *   the Greville collocation matrices B~_k (Sec. 4.2, eq. interpolation_matrix),
+ *   the mixed mass matrices M_k (Sec. 4.3, eq. univariate_mass_matrix2),
+ *   J = diag(sqrt(det DF)) at the mapped Greville points and Gamma the kernel
+ *   evaluated on the fly at every pair of mapped Greville points (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - Vectors are float64, column-major blocks of `nvec` columns with leading
+ *     dimension `ld` (elements).  A trial-space vector has N = n_1 ... n_d entries,
+ *     an interpolation-space vector Ntilde = n~_1 ... n~_d entries, both in the
+ *     paper's vec ordering (Sec. 2.2): index i_1 + i_2 n_1 + i_3 n_1 n_2, i_1 fastest.
+ *   - Pointers named *_dev are device pointers owned by the caller; the library
+ *     never frees them.  *_host pointers are host memory owned by the caller.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream are asynchronous on it unless stated otherwise.
+ *   - Every call returns a kl_status.  On error nothing is aborted; a message is
+ *     available from kl_last_error() (thread-local, valid until the next call
+ *     on the same thread).  There is no CPU fallback: every compute step runs in
+ *     the library's CUDA kernels.
+ *   - A handle owns its device workspace (allocated in kl_create and grown on
+ *     demand by kl_apply / kl_eigs, which then synchronise the stream once);
+ *     kl_destroy frees it.  A handle may be used by one thread at a time.
+ */
+#ifndef KL_H_
+#define KL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kl_handle_s* kl_handle;
+
+typedef enum {
+    KL_OK = 0,
+    KL_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or unsupported combination */
+    KL_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    KL_ERR_OOM = 3,           /* device allocation failed */
+    KL_ERR_NOT_CONVERGED = 4, /* kl_eigs reached maxiter before every residual met tol */
+    KL_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+    KL_ERR_NUMERIC = 6        /* non-finite values or a failed factorisation */
+} kl_status;
+
+/* Geometry map F of the parametric cube [0,1]^d onto the physical domain (Sec. 2.4).
+ * KL_GEOM_BOX is the affine map F(x^) = lo + (hi - lo) * x^ (det DF constant). */
+typedef enum { KL_GEOM_BOX = 0 } kl_geom_kind;
+
+typedef struct {
+    int dim;        /* d = 1, 2 or 3 */
+    int kind;       /* kl_geom_kind */
+    double lo[3];   /* box corner, hi[k] > lo[k] */
+    double hi[3];
+} kl_geometry;
+
+/* Trial space B_h (degree deg[k], elems[k] uniform elements, C^{deg-1}, Sec. 2.3)
+ * and interpolation space B~_h (interp_deg / interp_elems; 0 = same as trial;
+ * Sec. 4.2).  Open uniform knot vectors on [0,1]: n_k = elems[k] + deg[k]. */
+typedef struct {
+    int deg[3];
+    int elems[3];
+    int interp_deg[3];
+    int interp_elems[3];
+} kl_space;
+
+/* Covariance kernels (Sec. 3.1 names the exponential and Gaussian kernels with
+ * variance sigma^2 and a correlation length; formulas as read for this library):
+ *   KL_K_EXP            sigma^2 exp(-|x - x'|_2 / L)
+ *   KL_K_GAUSS          sigma^2 exp(-|x - x'|_2^2 / L^2)
+ *   KL_K_EXP_SEPARABLE  sigma^2 exp(-sum_k |x_k - x'_k| / L)
+ *   KL_K_POLY_TEST      sigma^2 prod_k (1 + x_k x'_k)^m, m = (int)L  (test kernel, 0 <= m <= 8) */
+typedef enum { KL_K_EXP = 0, KL_K_GAUSS = 1, KL_K_EXP_SEPARABLE = 2, KL_K_POLY_TEST = 3 } kl_kernel_kind;
+
+typedef struct {
+    int kind;       /* kl_kernel_kind */
+    double sigma;   /* > 0 */
+    double L;       /* > 0 */
+} kl_kernel;
+
+/* Arithmetic of the on-the-fly kernel product (stage 5 of Algorithm 1).
+ *   KL_P_FP64  kernel, distance and accumulation in float64 (matvec rel. error ~1e-14).
+ *   KL_P_FP32  kernel and distance in float32 (MUFU ex2 / rsqrt), float32 partial sums
+ *              over column chunks combined in float64; contractions in float32.
+ *              Relative error ~1e-6. */
+typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1 } kl_precision;
+
+/* Build the univariate factors, the mapped Greville grid and J on the host in
+ * float64 (Sec. 3.5, 4.1-4.3), upload them, and return a handle.
+ * Fails with KL_ERR_INVALID_ARG for dim outside 1..3, deg < 1, elems < 1,
+ * n~_k > 4096, Ntilde > 2^31-1, or a non-positive sigma / L / box extent.
+ * Synchronous. */
+kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_kernel* kernel,
+                    kl_handle* out);
+
+/* N = trial-space dimension, Ntilde = number of interpolation (Greville) points. */
+kl_status kl_size(kl_handle h, int64_t* N, int64_t* Ntilde);
+
+/* Per-direction sizes: n[k] = trial functions, ntilde[k] = Greville points of direction k
+ * (k = 0..2; directions beyond dim report 1).  Either pointer may be NULL. */
+kl_status kl_dims(kl_handle h, int* n, int* ntilde);
+
+/* y = A~' v for nvec columns (Algorithm 1, all nine stages), float64 arithmetic.
+ * v_dev, y_dev: N x nvec, leading dimension ldv >= N; v and y must not overlap. */
+kl_status kl_apply(kl_handle h, const double* v_dev, double* y_dev, int nvec, int64_t ldv,
+                   void* stream);
+
+/* Same as kl_apply with the stage-5 arithmetic chosen by `precision` (kl_precision). */
+kl_status kl_apply_prec(kl_handle h, int precision, const double* v_dev, double* y_dev, int nvec,
+                        int64_t ldv, void* stream);
+
+/* Stages 1-4 of Algorithm 1: u = J . B~^{-T} M L^{-T} v   (N x nvec -> Ntilde x nvec). */
+kl_status kl_forward(kl_handle h, const double* v_dev, int64_t ldv, double* u_dev, int64_t ldu,
+                     int nvec, void* stream);
+
+/* Stage 5 of Algorithm 1: z = Gamma u with Gamma(x_k, x_l) evaluated on the fly at the
+ * mapped Greville points (never stored).  u, z: Ntilde x nvec. */
+kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev,
+                   int64_t ldz, int nvec, void* stream);
+
+/* Stages 6-9 of Algorithm 1: y = L^{-1} M^T B~^{-1} (J . z)   (Ntilde x nvec -> N x nvec). */
+kl_status kl_backward(kl_handle h, const double* z_dev, int64_t ldz, double* y_dev, int64_t ldy,
+                      int nvec, void* stream);
+
+/* Copy set-up data to host memory (synchronous), for inspection and checks:
+ * C_host: n~_k x n_k row-major matrix C_k = B~_k^{-T} M_k L_k^{-T} of direction k (0-based);
+ * X_host: Ntilde x 3 row-major mapped Greville points (unused coordinates 0);
+ * J_host: Ntilde values sqrt(det DF).  Any pointer may be NULL. */
+kl_status kl_get_factor(kl_handle h, int k, double* C_host);
+kl_status kl_get_points(kl_handle h, double* X_host, double* J_host);
+
+/* Eigensolver options for kl_eigs.
+ *   method 0 (plain):  thick-restart block Lanczos, every operator application in
+ *                      float64 (the paper's implicitly restarted Lanczos, Sec. 4.4.2).
+ *   method 1 (mixed):  the same iteration with KL_P_FP32 operator applications until the
+ *                      residual estimates reach `tol_low`, then block Lanczos with the
+ *                      float64 operator from the float32 Ritz vectors (float64 polish).
+ *   block   b >= 1 (1 = classic single-vector Lanczos); ncv = basis size (0 = default
+ *           max(2k+1, k + 3b) rounded up to a multiple of b; at most 160).
+ *   start_dev: optional N x block start block (leading dimension N); NULL = seeded
+ *           counter-based random block from `seed` (splitmix64, uniform(-1,1)). */
+typedef struct {
+    int method;
+    int block;
+    int ncv;
+    int maxiter;            /* maximum restarts (0 = 1000) */
+    uint64_t seed;
+    const double* start_dev;
+    double tol_low;         /* method 1: switch-over residual (0 = 1e-5) */
+    int verify;             /* 1 = finish with an explicit float64 residual A~'y - theta y */
+} kl_eig_opts;
+
+typedef struct {
+    int applies;            /* operator applications counted per vector, all precisions */
+    int applies_fp64;       /* of which float64 */
+    int block_applies;      /* kl_apply launches (each on up to `block` or more vectors) */
+    int restarts;
+    int converged;          /* number of wanted pairs meeting tol */
+    double resid[64];       /* ||A~'y_i - theta_i y_i||_2 / |theta_i|, float64 operator if verify */
+    double ms_total;        /* wall time of the call */
+    double ms_fp32_phase;   /* method 1: time spent before the float64 polish */
+    /* stage-5 launches (kernel product + split combine) timed with CUDA events on `stream` */
+    int stage5_calls_fp64, stage5_calls_fp32;
+    double ms_stage5_fp64, ms_stage5_fp32;
+    double pairs_fp64, pairs_fp32;  /* kernel evaluations performed (Ntilde^2 per launch group) */
+} kl_eig_info;
+
+/* The k (<= 64) largest eigenvalues of A~' (descending) to relative residual tol.
+ * evals_host: k values (host).  evecs_dev: N x k orthonormal eigenvectors in standard
+ * form (v'^T v' = I), leading dimension ldv (may be NULL).  info may be NULL.
+ * Synchronous on `stream`.  Returns KL_ERR_NOT_CONVERGED (with the best pairs found
+ * written out) when maxiter restarts did not converge every wanted pair. */
+kl_status kl_eigs(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host,
+                  double* evecs_dev, int64_t ldv, kl_eig_info* info, void* stream);
+
+/* v = L^{-T} v' : B-spline coefficients of the eigenfunctions, phi = sum v_i B_i / sqrt(det DF)
+ * (Sec. 3.4, eq. basis; Sec. 4.1).  N x nvec blocks. */
+kl_status kl_to_bspline(kl_handle h, const double* vprime_dev, double* v_dev, int nvec, int64_t ld,
+                        void* stream);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all handles, all
+ * threads); for tracing and launch accounting. */
+uint64_t kl_kernel_launches(void);
+
+const char* kl_last_error(void);
+void kl_destroy(kl_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KL_H_ */

@@ -1,0 +1,258 @@
+"""ctypes binding of libkl.so (include/kl.h).  Argument marshalling only."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+KL_GEOM_BOX = 0
+KL_K_EXP, KL_K_GAUSS, KL_K_EXP_SEPARABLE, KL_K_POLY_TEST = 0, 1, 2, 3
+KL_P_FP64, KL_P_FP32 = 0, 1
+KERNEL_KINDS = {"exp": KL_K_EXP, "gauss": KL_K_GAUSS, "exp_sep": KL_K_EXP_SEPARABLE, "poly": KL_K_POLY_TEST}
+STATUS = {0: "KL_OK", 1: "KL_ERR_INVALID_ARG", 2: "KL_ERR_CUDA", 3: "KL_ERR_OOM",
+          4: "KL_ERR_NOT_CONVERGED", 5: "KL_ERR_TIMEOUT", 6: "KL_ERR_NUMERIC"}
+
+# every entry point declared in include/kl.h, with (restype, argtypes)
+_c_int64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+
+
+class KLGeometry(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("kind", ctypes.c_int), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3)]
+
+
+class KLSpace(ctypes.Structure):
+    _fields_ = [("deg", ctypes.c_int * 3), ("elems", ctypes.c_int * 3), ("interp_deg", ctypes.c_int * 3),
+                ("interp_elems", ctypes.c_int * 3)]
+
+
+class KLKernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("L", ctypes.c_double)]
+
+
+class KLEigOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("block", ctypes.c_int), ("ncv", ctypes.c_int),
+                ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("start_dev", _vp),
+                ("tol_low", ctypes.c_double), ("verify", ctypes.c_int)]
+
+
+class KLEigInfo(ctypes.Structure):
+    _fields_ = [("applies", ctypes.c_int), ("applies_fp64", ctypes.c_int), ("block_applies", ctypes.c_int),
+                ("restarts", ctypes.c_int), ("converged", ctypes.c_int), ("resid", ctypes.c_double * 64),
+                ("ms_total", ctypes.c_double), ("ms_fp32_phase", ctypes.c_double),
+                ("stage5_calls_fp64", ctypes.c_int), ("stage5_calls_fp32", ctypes.c_int),
+                ("ms_stage5_fp64", ctypes.c_double), ("ms_stage5_fp32", ctypes.c_double),
+                ("pairs_fp64", ctypes.c_double), ("pairs_fp32", ctypes.c_double)]
+
+
+SIGNATURES = {
+    "kl_create": (ctypes.c_int, [ctypes.POINTER(KLGeometry), ctypes.POINTER(KLSpace), ctypes.POINTER(KLKernel),
+                                 ctypes.POINTER(_vp)]),
+    "kl_size": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_int64)]),
+    "kl_dims": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "kl_apply": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _c_int64, _vp]),
+    "kl_apply_prec": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _c_int64, _vp]),
+    "kl_forward": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
+    "kl_covmv": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
+    "kl_backward": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
+    "kl_get_factor": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "kl_get_points": (ctypes.c_int, [_vp, _vp, _vp]),
+    "kl_eigs": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(KLEigOpts), _vp, _vp, _c_int64,
+                               ctypes.POINTER(KLEigInfo), _vp]),
+    "kl_to_bspline": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _c_int64, _vp]),
+    "kl_kernel_launches": (ctypes.c_uint64, []),
+    "kl_last_error": (ctypes.c_char_p, []),
+    "kl_destroy": (None, [_vp]),
+}
+
+_LIB = None
+
+
+class KLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def library_path():
+    return os.path.join(HERE, "libkl.so")
+
+
+def load(path=None):
+    """Load libkl.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libkl.so not found at %s; build it with `python -m paper_2011_13861_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def exported_symbols(path=None):
+    """Names from SIGNATURES that the shared object exports (no CUDA call is made)."""
+    lib = ctypes.CDLL(path or library_path())
+    return [n for n in SIGNATURES if hasattr(lib, n)]
+
+
+def kernel_launches():
+    """Kernels launched by libkl since it was loaded."""
+    return int(load().kl_kernel_launches())
+
+
+def _check(status):
+    if status != 0:
+        raise KLError(status, load().kl_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _per_dir(v, dim, default=0):
+    if v is None:
+        return [default] * 3
+    if isinstance(v, (int, float)):
+        v = [v] * dim
+    v = list(v) + [default] * (3 - len(v))
+    return v[:3]
+
+
+class KLProblem:
+    """One discretised KL problem on the GPU (a kl_handle).
+
+    dim, p, ne: spatial dimension, trial degree and element count per direction;
+    kernel: 'exp' | 'gauss' | 'exp_sep' | 'poly';  pt, net: interpolation space (default = trial);
+    lo, hi: box map.  All vectors are float64 CUDA tensors of shape (N,) or (N, nvec)
+    (column-major blocks are handled by passing the transposed storage, see _block).
+    """
+
+    def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None, lo=None, hi=None):
+        lib = load()
+        g = KLGeometry(dim, KL_GEOM_BOX, (ctypes.c_double * 3)(*_per_dir(lo, dim, 0.0)),
+                       (ctypes.c_double * 3)(*_per_dir(hi, dim, 1.0)))
+        sp = KLSpace((ctypes.c_int * 3)(*_per_dir(p, dim)), (ctypes.c_int * 3)(*_per_dir(ne, dim)),
+                     (ctypes.c_int * 3)(*_per_dir(pt, dim)), (ctypes.c_int * 3)(*_per_dir(net, dim)))
+        kk = KLKernel(KERNEL_KINDS[kernel] if isinstance(kernel, str) else int(kernel), float(sigma), float(L))
+        h = ctypes.c_void_p()
+        _check(lib.kl_create(ctypes.byref(g), ctypes.byref(sp), ctypes.byref(kk), ctypes.byref(h)))
+        self._h = h
+        self.dim = dim
+        N, Nt = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.kl_size(h, ctypes.byref(N), ctypes.byref(Nt)))
+        self.N, self.Nt = N.value, Nt.value
+        n3, nt3 = (ctypes.c_int * 3)(), (ctypes.c_int * 3)()
+        _check(lib.kl_dims(h, n3, nt3))
+        self.n, self.nt = list(n3)[:dim], list(nt3)[:dim]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- helpers: a block of nvec column vectors of length n is stored as a (nvec, n)
+    #    row-major torch tensor, i.e. column-major (n x nvec) with leading dimension n.
+    @staticmethod
+    def _block(x, n):
+        import torch
+        if x.dtype != torch.float64 or not x.is_cuda:
+            raise TypeError("expected a float64 CUDA tensor")
+        if x.dim() == 1:
+            x = x.reshape(1, -1)
+        if x.shape[-1] != n or not x.is_contiguous():
+            raise ValueError("expected a contiguous (nvec, %d) tensor" % n)
+        return x
+
+    def apply(self, v, precision=KL_P_FP64, out=None, stream=None):
+        """y = A~' v (all nine stages of Algorithm 1).  v: (N,) or (nvec, N)."""
+        import torch
+        vb = self._block(v, self.N)
+        y = out if out is not None else torch.empty_like(vb)
+        _check(load().kl_apply_prec(self._h, int(precision), _ptr(vb), _ptr(y), vb.shape[0], self.N, _stream(stream)))
+        return y.reshape(v.shape)
+
+    def forward(self, v, stream=None):
+        import torch
+        vb = self._block(v, self.N)
+        u = torch.empty((vb.shape[0], self.Nt), dtype=torch.float64, device=vb.device)
+        _check(load().kl_forward(self._h, _ptr(vb), self.N, _ptr(u), self.Nt, vb.shape[0], _stream(stream)))
+        return u if v.dim() == 2 else u[0]
+
+    def covmv(self, u, precision=KL_P_FP64, stream=None):
+        import torch
+        ub = self._block(u, self.Nt)
+        z = torch.empty_like(ub)
+        _check(load().kl_covmv(self._h, int(precision), _ptr(ub), self.Nt, _ptr(z), self.Nt, ub.shape[0],
+                               _stream(stream)))
+        return z.reshape(u.shape)
+
+    def backward(self, z, stream=None):
+        import torch
+        zb = self._block(z, self.Nt)
+        y = torch.empty((zb.shape[0], self.N), dtype=torch.float64, device=zb.device)
+        _check(load().kl_backward(self._h, _ptr(zb), self.Nt, _ptr(y), self.N, zb.shape[0], _stream(stream)))
+        return y if z.dim() == 2 else y[0]
+
+    def to_bspline(self, vp, stream=None):
+        import torch
+        vb = self._block(vp, self.N)
+        out = torch.empty_like(vb)
+        _check(load().kl_to_bspline(self._h, _ptr(vb), _ptr(out), vb.shape[0], self.N, _stream(stream)))
+        return out.reshape(vp.shape)
+
+    def factor(self, k):
+        """C_k = B~_k^{-T} M_k L_k^{-T} of direction k (n~_k x n_k numpy array)."""
+        import numpy as np
+        C = np.zeros((self.nt[k], self.n[k]))
+        _check(load().kl_get_factor(self._h, k, C.ctypes.data_as(ctypes.c_void_p)))
+        return C
+
+    def points(self):
+        import numpy as np
+        X = np.zeros((self.Nt, 3))
+        J = np.zeros(self.Nt)
+        _check(load().kl_get_points(self._h, X.ctypes.data_as(ctypes.c_void_p), J.ctypes.data_as(ctypes.c_void_p)))
+        return X[:, :self.dim].copy(), J
+
+    def eigs(self, k, tol=1e-8, method=0, block=1, ncv=0, maxiter=0, seed=1, start=None, tol_low=0.0,
+             verify=True, want_vectors=True, stream=None, raise_on_nonconv=True):
+        """The k largest eigenpairs (descending).  Returns (evals numpy, evecs (k, N) tensor or None, info dict)."""
+        import numpy as np
+        import torch
+        opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1),
+                         _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0)
+        ev = np.zeros(k)
+        vecs = None
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if want_vectors:
+            vecs = torch.empty((k, self.N), dtype=torch.float64, device=dev)
+        info = KLEigInfo()
+        st = load().kl_eigs(self._h, int(k), float(tol), ctypes.byref(opts), ev.ctypes.data_as(ctypes.c_void_p),
+                            _ptr(vecs), self.N, ctypes.byref(info), _stream(stream))
+        if st != 0 and (raise_on_nonconv or st != 4):
+            _check(st)
+        d = {"applies": info.applies, "applies_fp64": info.applies_fp64, "block_applies": info.block_applies,
+             "restarts": info.restarts, "converged": info.converged, "resid": list(info.resid[:k]),
+             "ms_total": info.ms_total, "ms_fp32_phase": info.ms_fp32_phase, "status": st,
+             "stage5_calls_fp64": info.stage5_calls_fp64, "stage5_calls_fp32": info.stage5_calls_fp32,
+             "ms_stage5_fp64": info.ms_stage5_fp64, "ms_stage5_fp32": info.ms_stage5_fp32,
+             "pairs_fp64": info.pairs_fp64, "pairs_fp32": info.pairs_fp32}
+        return ev, vecs, d

@@ -1,0 +1,559 @@
+// C ABI entry points, handle set-up and the operator application of Algorithm 1.
+#include <math.h>
+
+#include <atomic>
+#include <chrono>
+#include <type_traits>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kl_internal.h"
+
+namespace kl {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}
+
+void count_launches(int n) { g_launches.fetch_add(uint64_t(n), std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+kl_status fail(kl_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+kl_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? KL_ERR_OOM : KL_ERR_CUDA;
+}
+
+kl_status ensure(DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes) return KL_OK;
+    if (b.ptr) {
+        cudaError_t e = cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    b.bytes = bytes;
+    return KL_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+namespace {
+
+template <typename T>
+kl_status upload(T** dst, const T* src, size_t count) {
+    KL_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), count * sizeof(T)));
+    KL_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return KL_OK;
+}
+
+int64_t stride_of(kl_handle h) { return h->ldw; }
+
+kl_status check_block(kl_handle h, const void* a, const void* b, int nvec, int64_t lda, int64_t rows_a,
+                      int64_t ldb, int64_t rows_b) {
+    if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
+    if (nvec < 0) return fail(KL_ERR_INVALID_ARG, "nvec < 0");
+    if (nvec == 0) return KL_OK;
+    if (!a || !b) return fail(KL_ERR_INVALID_ARG, "null vector pointer");
+    if (lda < rows_a || ldb < rows_b) return fail(KL_ERR_INVALID_ARG, "leading dimension smaller than the vector length");
+    return KL_OK;
+}
+
+// workspace for nvec columns of the intermediate tensors
+kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32) {
+    const int64_t ld = stride_of(h);
+    KL_TRY(ensure(h->w_a, size_t(ld) * nvec * sizeof(double)));
+    KL_TRY(ensure(h->w_b, size_t(ld) * nvec * sizeof(double)));
+    if (fp32) {
+        KL_TRY(ensure(h->w_f32a, size_t(ld) * nvec * sizeof(float)));
+        KL_TRY(ensure(h->w_f32b, size_t(ld) * nvec * sizeof(float)));
+    }
+    const int s64 = covmv_splits(h->Nt, nvec, false), s32 = covmv_splits(h->Nt, nvec, true);
+    const size_t part = size_t(h->Nt) * (size_t(s64) * 16 > size_t(s32) * 32 ? size_t(s64) * 16 : size_t(s32) * 32);
+    KL_TRY(ensure(h->w_part, part * sizeof(double)));
+    return KL_OK;
+}
+
+CovParams cov_params(kl_handle h) {
+    CovParams cp;
+    cp.kind = h->kernel.kind;
+    cp.poly_m = int(h->kernel.L);
+    cp.Nt = h->Nt;
+    cp.ldp = h->Nt;
+    cp.P64 = h->dP;
+    cp.P32 = h->fP;
+    cp.tab = h->dTab;
+    return cp;
+}
+
+}  // namespace
+
+// ---- stages 1-4: u = J . C v  (C = C_d (x) ... (x) C_1) ----------------------------------
+template <typename Tc, typename Tout>
+static kl_status forward_generic(kl_handle h, const double* v, int64_t ldv, Tout* u, int64_t ldu, int nvec,
+                                 Tc* const* Ct, const Tc* J, void* bufA, void* bufB, cudaStream_t s) {
+    const int d = h->dim;
+    const int64_t ld = stride_of(h);
+    // sizes: after processing modes < k the tensor is [n_d..n_{k}][nt_{k-1}..nt_1]
+    const void* cur = v;
+    int64_t ldcur = ldv;
+    bool cur_is_double = true;
+    for (int k = 0; k < d; ++k) {
+        int64_t A = 1, B = 1;
+        for (int i = k + 1; i < d; ++i) A *= h->n[i];
+        for (int i = 0; i < k; ++i) B *= h->nt[i];
+        const bool last = (k == d - 1);
+        void* out = last ? static_cast<void*>(u) : ((k % 2 == 0) ? bufA : bufB);
+        const int64_t ldo = last ? ldu : ld;
+        cudaError_t e;
+        const Tc* sc = last ? J : nullptr;
+        if (cur_is_double) {
+            if (last)
+                e = launch_contract<double, Tc, Tout>(static_cast<const double*>(cur), ldcur, static_cast<Tout*>(out), ldo,
+                                                      Ct[k], A, h->n[k], h->nt[k], B, nvec, sc, s);
+            else
+                e = launch_contract<double, Tc, Tc>(static_cast<const double*>(cur), ldcur, static_cast<Tc*>(out), ldo,
+                                                    Ct[k], A, h->n[k], h->nt[k], B, nvec, sc, s);
+        } else {
+            if (last)
+                e = launch_contract<Tc, Tc, Tout>(static_cast<const Tc*>(cur), ldcur, static_cast<Tout*>(out), ldo,
+                                                  Ct[k], A, h->n[k], h->nt[k], B, nvec, sc, s);
+            else
+                e = launch_contract<Tc, Tc, Tc>(static_cast<const Tc*>(cur), ldcur, static_cast<Tc*>(out), ldo,
+                                                Ct[k], A, h->n[k], h->nt[k], B, nvec, sc, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "forward contraction");
+        cur = out;
+        ldcur = ldo;
+        cur_is_double = std::is_same<Tc, double>::value;
+    }
+    return KL_OK;
+}
+
+// ---- stages 6-9 (J already applied to z by the stage-5 epilogue): y = C^T z -----------------
+template <typename Tc>
+static kl_status backward_generic(kl_handle h, const double* z, int64_t ldz, double* y, int64_t ldy, int nvec,
+                                  Tc* const* C, void* bufA, void* bufB, cudaStream_t s) {
+    const int d = h->dim;
+    const int64_t ld = stride_of(h);
+    const void* cur = z;
+    int64_t ldcur = ldz;
+    bool cur_is_double = true;
+    for (int k = 0; k < d; ++k) {
+        int64_t A = 1, B = 1;
+        for (int i = k + 1; i < d; ++i) A *= h->nt[i];
+        for (int i = 0; i < k; ++i) B *= h->n[i];
+        const bool last = (k == d - 1);
+        void* out = last ? static_cast<void*>(y) : ((k % 2 == 0) ? bufA : bufB);
+        const int64_t ldo = last ? ldy : ld;
+        cudaError_t e;
+        if (cur_is_double) {
+            if (last)
+                e = launch_contract<double, Tc, double>(static_cast<const double*>(cur), ldcur, static_cast<double*>(out), ldo,
+                                                        C[k], A, h->nt[k], h->n[k], B, nvec, nullptr, s);
+            else
+                e = launch_contract<double, Tc, Tc>(static_cast<const double*>(cur), ldcur, static_cast<Tc*>(out), ldo,
+                                                    C[k], A, h->nt[k], h->n[k], B, nvec, nullptr, s);
+        } else {
+            if (last)
+                e = launch_contract<Tc, Tc, double>(static_cast<const Tc*>(cur), ldcur, static_cast<double*>(out), ldo,
+                                                    C[k], A, h->nt[k], h->n[k], B, nvec, nullptr, s);
+            else
+                e = launch_contract<Tc, Tc, Tc>(static_cast<const Tc*>(cur), ldcur, static_cast<Tc*>(out), ldo,
+                                                C[k], A, h->nt[k], h->n[k], B, nvec, nullptr, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "backward contraction");
+        cur = out;
+        ldcur = ldo;
+        cur_is_double = std::is_same<Tc, double>::value;
+    }
+    return KL_OK;
+}
+
+kl_status forward_impl(kl_handle h, const double* v, int64_t ldv, double* u, int64_t ldu, int nvec,
+                       cudaStream_t s) {
+    KL_TRY(ensure_apply_ws(h, nvec, false));
+    return forward_generic<double, double>(h, v, ldv, u, ldu, nvec, h->dCt, h->dJ, h->w_a.ptr, h->w_b.ptr, s);
+}
+
+kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, double* z, int64_t ldz,
+                     int nvec, bool withJ, cudaStream_t s) {
+    KL_TRY(ensure_apply_ws(h, nvec, precision == KL_P_FP32));
+    CovParams cp = cov_params(h);
+    const double s2 = h->kernel.sigma * h->kernel.sigma;
+    const double* J = withJ ? h->dJ : nullptr;
+    cudaError_t e;
+    if (precision == KL_P_FP64) {
+        e = launch_covmv64(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
+                           covmv_splits(h->Nt, nvec, false), s);
+    } else {
+        float* uf = static_cast<float*>(h->w_f32a.ptr);
+        const int64_t ld = stride_of(h);
+        e = launch_to_float(u, ldu, uf, ld, h->Nt, nvec, s);
+        if (e == cudaSuccess)
+            e = launch_covmv32(cp, uf, ld, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
+                               covmv_splits(h->Nt, nvec, true), s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product");
+    return KL_OK;
+}
+
+kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, int64_t ldy, int nvec,
+                        bool zHasJ, cudaStream_t s) {
+    KL_TRY(ensure_apply_ws(h, nvec, false));
+    if (!zHasJ) {
+        // stage 6 on its own: w = J . z into the second buffer (first buffer is the mode-1 output)
+        double* tmp = static_cast<double*>(h->w_b.ptr);
+        const int64_t ld = stride_of(h);
+        // J . z as a 1 x 1 "contraction" with factor 1.0 (table entry 2^0) and scale J
+        cudaError_t e = launch_contract<double, double, double>(z, ldz, tmp, ld, h->dTab /*entry 0 == 1.0*/, h->Nt, 1, 1,
+                                                                1, nvec, h->dJ, s);
+        if (e != cudaSuccess) return cuda_fail(e, "stage 6 scaling");
+        // the mode passes read tmp once, so it can serve as the second ping-pong buffer
+        return backward_generic<double>(h, tmp, ld, y, ldy, nvec, h->dC, h->w_a.ptr, tmp, s);
+    }
+    return backward_generic<double>(h, z, ldz, y, ldy, nvec, h->dC, h->w_a.ptr, h->w_b.ptr, s);
+}
+
+// Stage-5 event timing: while kl_eigs runs, every stage-5 launch group is bracketed by a
+// pair of CUDA events on the launching stream; the pairs are read once the solve is done.
+static kl_status prof_begin(kl_handle h, bool fp64, int nvec, cudaStream_t s, int* slot) {
+    *slot = -1;
+    if (!h->prof_on) return KL_OK;
+    const int need = int(h->prof_rec.size()) * 2 + 2;
+    while (int(h->prof_ev.size()) < need) {
+        cudaEvent_t ev;
+        KL_CUDA(cudaEventCreate(&ev));
+        h->prof_ev.push_back(ev);
+    }
+    *slot = int(h->prof_rec.size()) * 2;
+    h->prof_rec.push_back({*slot, fp64, nvec});
+    KL_CUDA(cudaEventRecord(h->prof_ev[*slot], s));
+    return KL_OK;
+}
+
+static kl_status prof_end(kl_handle h, int slot, cudaStream_t s) {
+    if (slot < 0) return KL_OK;
+    KL_CUDA(cudaEventRecord(h->prof_ev[slot + 1], s));
+    return KL_OK;
+}
+
+kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, double* y, int64_t ldy, int nvec,
+                     cudaStream_t s) {
+    if (nvec == 0) return KL_OK;
+    const bool fp32 = (precision == KL_P_FP32);
+    KL_TRY(ensure_apply_ws(h, nvec, fp32));
+    const int64_t ld = stride_of(h);
+    double* A = static_cast<double*>(h->w_a.ptr);
+    double* B = static_cast<double*>(h->w_b.ptr);
+    CovParams cp = cov_params(h);
+    const double s2 = h->kernel.sigma * h->kernel.sigma;
+    if (!fp32) {
+        // stages 1-4 -> u in A (the mode passes ping-pong through A/B and end in `u`)
+        double* u = (h->dim % 2 == 1) ? A : B;
+        KL_TRY(forward_generic<double, double>(h, v, ldv, u, ld, nvec, h->dCt, h->dJ, A, B, s));
+        double* z = (u == A) ? B : A;
+        int slot;
+        KL_TRY(prof_begin(h, true, nvec, s, &slot));
+        cudaError_t e = launch_covmv64(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                                       covmv_splits(h->Nt, nvec, false), s);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp64)");
+        KL_TRY(prof_end(h, slot, s));
+        double* other = (z == A) ? B : A;
+        // mode 1 reads z into `other`; z is then free to serve as the second buffer
+        return backward_generic<double>(h, z, ld, y, ldy, nvec, h->dC, other, z, s);
+    }
+    float* FA = static_cast<float*>(h->w_f32a.ptr);
+    float* FB = static_cast<float*>(h->w_f32b.ptr);
+    float* u = (h->dim % 2 == 1) ? FA : FB;
+    KL_TRY(forward_generic<float, float>(h, v, ldv, u, ld, nvec, h->fCt, h->fJ, FA, FB, s));
+    double* z = A;
+    int slot;
+    KL_TRY(prof_begin(h, false, nvec, s, &slot));
+    cudaError_t e = launch_covmv32(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                                   covmv_splits(h->Nt, nvec, true), s);
+    if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp32)");
+    KL_TRY(prof_end(h, slot, s));
+    return backward_generic<float>(h, z, ld, y, ldy, nvec, h->fC, FA, FB, s);
+}
+
+}  // namespace kl
+
+using namespace kl;
+
+extern "C" {
+
+kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_kernel* kernel, kl_handle* out) {
+    if (!geom || !space || !kernel || !out) return fail(KL_ERR_INVALID_ARG, "null argument to kl_create");
+    *out = nullptr;
+    const int d = geom->dim;
+    if (d < 1 || d > 3) return fail(KL_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
+    if (geom->kind != KL_GEOM_BOX) return fail(KL_ERR_INVALID_ARG, "unsupported geometry kind");
+    if (kernel->kind < KL_K_EXP || kernel->kind > KL_K_POLY_TEST) return fail(KL_ERR_INVALID_ARG, "unknown kernel kind");
+    if (!(kernel->sigma > 0.0) || !(kernel->L > 0.0) || !isfinite(kernel->sigma) || !isfinite(kernel->L))
+        return fail(KL_ERR_INVALID_ARG, "sigma and L must be positive and finite");
+    if (kernel->kind == KL_K_POLY_TEST && (kernel->L < 1.0 || kernel->L > 8.0))
+        return fail(KL_ERR_INVALID_ARG, "polynomial test kernel needs 1 <= m = L <= 8");
+    for (int k = 0; k < d; ++k)
+        if (!(geom->hi[k] > geom->lo[k]) || !isfinite(geom->lo[k]) || !isfinite(geom->hi[k]))
+            return fail(KL_ERR_INVALID_ARG, "box extent must be positive");
+
+    kl_handle h = new (std::nothrow) kl_handle_s();
+    if (!h) return fail(KL_ERR_OOM, "host allocation failed");
+    h->dim = d;
+    h->kernel = *kernel;
+    h->N = 1;
+    h->Nt = 1;
+    double det = 1.0;
+    for (int k = 0; k < d; ++k) {
+        const int p = space->deg[k], ne = space->elems[k];
+        const int pt = space->interp_deg[k] > 0 ? space->interp_deg[k] : p;
+        const int net = space->interp_elems[k] > 0 ? space->interp_elems[k] : ne;
+        kl_status st = build_direction(p, ne, pt, net, &h->dir[k]);
+        if (st != KL_OK) {
+            delete h;
+            return st;
+        }
+        h->n[k] = h->dir[k].n;
+        h->nt[k] = h->dir[k].nt;
+        h->N *= h->n[k];
+        h->Nt *= h->nt[k];
+        h->lo[k] = geom->lo[k];
+        h->hi[k] = geom->hi[k];
+        det *= geom->hi[k] - geom->lo[k];
+    }
+    if (h->Nt > 2147483647LL || h->N > 2147483647LL) {
+        delete h;
+        return fail(KL_ERR_INVALID_ARG, "problem too large (more than 2^31-1 points)");
+    }
+    h->Jval = sqrt(det);
+    // largest intermediate tensor of the forward (n -> n~) and backward (n~ -> n) mode passes
+    h->ldw = h->N > h->Nt ? h->N : h->Nt;
+    for (int k = 0; k < d; ++k) {
+        int64_t f = 1, b = 1;
+        for (int i = 0; i < d; ++i) {
+            f *= (i <= k) ? h->nt[i] : h->n[i];
+            b *= (i <= k) ? h->n[i] : h->nt[i];
+        }
+        if (f > h->ldw) h->ldw = f;
+        if (b > h->ldw) h->ldw = b;
+    }
+
+    // mapped Greville points in vec order (direction 1 fastest) and J
+    const int64_t Nt = h->Nt;
+    h->X_host.assign(size_t(Nt) * 3, 0.0);
+    for (int64_t idx = 0; idx < Nt; ++idx) {
+        int64_t r = idx;
+        for (int k = 0; k < d; ++k) {
+            const int64_t ik = r % h->nt[k];
+            r /= h->nt[k];
+            h->X_host[size_t(idx) * 3 + k] = h->lo[k] + (h->hi[k] - h->lo[k]) * h->dir[k].xi[size_t(ik)];
+        }
+    }
+    // device copies: coordinates scaled per kernel kind
+    const int kind = kernel->kind;
+    const double L = kernel->L;
+    const double log2e = 1.4426950408889634;
+    double s64 = 1.0, s32 = 1.0;
+    if (kind == KL_K_EXP || kind == KL_K_EXP_SEPARABLE) {
+        s64 = 1.0 / L;
+        s32 = log2e / L;
+    } else if (kind == KL_K_GAUSS) {
+        s64 = 1.0 / L;
+        s32 = sqrt(log2e) / L;
+    }
+    std::vector<double> P(size_t(Nt) * 3);
+    std::vector<float> Pf(size_t(Nt) * 3);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t i = 0; i < Nt; ++i) {
+            const double x = h->X_host[size_t(i) * 3 + c];
+            P[size_t(c) * Nt + i] = x * s64;
+            Pf[size_t(c) * Nt + i] = float(x * s32);
+        }
+    std::vector<double> J(size_t(Nt), h->Jval);
+    std::vector<float> Jf(size_t(Nt), float(h->Jval));
+    std::vector<double> tab(64);
+    for (int j = 0; j < 64; ++j) tab[j] = exp2(double(j) / 64.0);
+
+    kl_status st = KL_OK;
+    auto chk = [&](kl_status s2) {
+        if (st == KL_OK) st = s2;
+    };
+    chk(upload(&h->dP, P.data(), P.size()));
+    chk(upload(&h->fP, Pf.data(), Pf.size()));
+    chk(upload(&h->dJ, J.data(), J.size()));
+    chk(upload(&h->fJ, Jf.data(), Jf.size()));
+    chk(upload(&h->dTab, tab.data(), tab.size()));
+    for (int k = 0; k < d && st == KL_OK; ++k) {
+        const Direction& D = h->dir[k];
+        const int n = D.n, nt = D.nt;
+        // forward factor C_k (nt x n); the contraction kernel wants Ct[j * m + i] = C[i][j]
+        std::vector<double> Ct(size_t(n) * nt), Cb(size_t(nt) * n);
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < n; ++j) {
+                Ct[size_t(j) * nt + i] = D.C[size_t(i) * n + j];
+                // backward factor C_k^T (n x nt): layout Ct'[jj * n + ii] = C^T[ii][jj] = C[jj][ii]
+                Cb[size_t(i) * n + j] = D.C[size_t(i) * n + j];
+            }
+        std::vector<float> Ctf(Ct.begin(), Ct.end()), Cbf(Cb.begin(), Cb.end());
+        chk(upload(&h->dCt[k], Ct.data(), Ct.size()));
+        chk(upload(&h->dC[k], Cb.data(), Cb.size()));
+        chk(upload(&h->fCt[k], Ctf.data(), Ctf.size()));
+        chk(upload(&h->fC[k], Cbf.data(), Cbf.size()));
+        // L_k^{-T} as a contraction factor: out[i] = sum_j (L^{-T})[i][j] in[j];  layout [j*n + i] = Linv[j][i]
+        std::vector<double> LT(size_t(n) * n);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) LT[size_t(j) * n + i] = D.Linv[size_t(j) * n + i];
+        chk(upload(&h->dLinvT[k], LT.data(), LT.size()));
+    }
+    if (st == KL_OK) st = ensure_apply_ws(h, 1, true);
+    if (st != KL_OK) {
+        kl_destroy(h);
+        return st;
+    }
+    *out = h;
+    return KL_OK;
+}
+
+kl_status kl_size(kl_handle h, int64_t* N, int64_t* Ntilde) {
+    if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
+    if (N) *N = h->N;
+    if (Ntilde) *Ntilde = h->Nt;
+    return KL_OK;
+}
+
+kl_status kl_dims(kl_handle h, int* n, int* ntilde) {
+    if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
+    for (int k = 0; k < 3; ++k) {
+        if (n) n[k] = h->n[k];
+        if (ntilde) ntilde[k] = h->nt[k];
+    }
+    return KL_OK;
+}
+
+kl_status kl_apply_prec(kl_handle h, int precision, const double* v_dev, double* y_dev, int nvec, int64_t ldv,
+                        void* stream) {
+    KL_TRY(check_block(h, v_dev, y_dev, nvec, ldv, h ? h->N : 0, ldv, h ? h->N : 0));
+    if (precision != KL_P_FP64 && precision != KL_P_FP32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    return apply_impl(h, precision, v_dev, ldv, y_dev, ldv, nvec, static_cast<cudaStream_t>(stream));
+}
+
+kl_status kl_apply(kl_handle h, const double* v_dev, double* y_dev, int nvec, int64_t ldv, void* stream) {
+    return kl_apply_prec(h, KL_P_FP64, v_dev, y_dev, nvec, ldv, stream);
+}
+
+kl_status kl_forward(kl_handle h, const double* v_dev, int64_t ldv, double* u_dev, int64_t ldu, int nvec,
+                     void* stream) {
+    KL_TRY(check_block(h, v_dev, u_dev, nvec, ldv, h ? h->N : 0, ldu, h ? h->Nt : 0));
+    if (nvec == 0) return KL_OK;
+    return forward_impl(h, v_dev, ldv, u_dev, ldu, nvec, static_cast<cudaStream_t>(stream));
+}
+
+kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev, int64_t ldz,
+                   int nvec, void* stream) {
+    KL_TRY(check_block(h, u_dev, z_dev, nvec, ldu, h ? h->Nt : 0, ldz, h ? h->Nt : 0));
+    if (precision != KL_P_FP64 && precision != KL_P_FP32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    if (nvec == 0) return KL_OK;
+    return covmv_impl(h, precision, u_dev, ldu, z_dev, ldz, nvec, false, static_cast<cudaStream_t>(stream));
+}
+
+kl_status kl_backward(kl_handle h, const double* z_dev, int64_t ldz, double* y_dev, int64_t ldy, int nvec,
+                      void* stream) {
+    KL_TRY(check_block(h, z_dev, y_dev, nvec, ldz, h ? h->Nt : 0, ldy, h ? h->N : 0));
+    if (nvec == 0) return KL_OK;
+    return backward_impl(h, z_dev, ldz, y_dev, ldy, nvec, false, static_cast<cudaStream_t>(stream));
+}
+
+kl_status kl_get_factor(kl_handle h, int k, double* C_host) {
+    if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
+    if (k < 0 || k >= h->dim) return fail(KL_ERR_INVALID_ARG, "direction out of range");
+    if (C_host) std::memcpy(C_host, h->dir[k].C.data(), h->dir[k].C.size() * sizeof(double));
+    return KL_OK;
+}
+
+kl_status kl_get_points(kl_handle h, double* X_host, double* J_host) {
+    if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
+    if (X_host) std::memcpy(X_host, h->X_host.data(), h->X_host.size() * sizeof(double));
+    if (J_host)
+        for (int64_t i = 0; i < h->Nt; ++i) J_host[i] = h->Jval;
+    return KL_OK;
+}
+
+kl_status kl_to_bspline(kl_handle h, const double* vprime_dev, double* v_dev, int nvec, int64_t ld, void* stream) {
+    KL_TRY(check_block(h, vprime_dev, v_dev, nvec, ld, h ? h->N : 0, ld, h ? h->N : 0));
+    if (nvec == 0) return KL_OK;
+    KL_TRY(ensure_apply_ws(h, nvec, false));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int d = h->dim;
+    const int64_t lds = stride_of(h);
+    const double* cur = vprime_dev;
+    int64_t ldcur = ld;
+    for (int k = 0; k < d; ++k) {
+        int64_t A = 1, B = 1;
+        for (int i = k + 1; i < d; ++i) A *= h->n[i];
+        for (int i = 0; i < k; ++i) B *= h->n[i];
+        const bool last = (k == d - 1);
+        double* out = last ? v_dev : static_cast<double*>((k % 2 == 0) ? h->w_a.ptr : h->w_b.ptr);
+        cudaError_t e = launch_contract<double, double, double>(cur, ldcur, out, last ? ld : lds, h->dLinvT[k], A,
+                                                                h->n[k], h->n[k], B, nvec, nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(e, "L^{-T} contraction");
+        cur = out;
+        ldcur = last ? ld : lds;
+    }
+    return KL_OK;
+}
+
+kl_status kl_eigs(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host, double* evecs_dev,
+                  int64_t ldv, kl_eig_info* info, void* stream) {
+    if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
+    if (k < 1 || k > 64 || k >= h->N) return fail(KL_ERR_INVALID_ARG, "need 1 <= k <= 64 and k < N");
+    if (!(tol > 0.0)) return fail(KL_ERR_INVALID_ARG, "tol must be positive");
+    if (!evals_host) return fail(KL_ERR_INVALID_ARG, "evals_host is NULL");
+    if (evecs_dev && ldv < h->N) return fail(KL_ERR_INVALID_ARG, "ldv < N");
+    return eigs_impl(h, k, tol, opts, evals_host, evecs_dev, ldv, info, static_cast<cudaStream_t>(stream));
+}
+
+uint64_t kl_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* kl_last_error(void) { return g_last_error.c_str(); }
+
+void kl_destroy(kl_handle h) {
+    if (!h) return;
+    for (int k = 0; k < 3; ++k) {
+        if (h->dCt[k]) cudaFree(h->dCt[k]);
+        if (h->dC[k]) cudaFree(h->dC[k]);
+        if (h->fCt[k]) cudaFree(h->fCt[k]);
+        if (h->fC[k]) cudaFree(h->fC[k]);
+        if (h->dLinvT[k]) cudaFree(h->dLinvT[k]);
+    }
+    if (h->dP) cudaFree(h->dP);
+    if (h->fP) cudaFree(h->fP);
+    if (h->dJ) cudaFree(h->dJ);
+    if (h->fJ) cudaFree(h->fJ);
+    if (h->dTab) cudaFree(h->dTab);
+    release(h->w_a);
+    release(h->w_b);
+    release(h->w_f32a);
+    release(h->w_f32b);
+    release(h->w_part);
+    for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
+    delete h;
+}
+
+}  // extern "C"

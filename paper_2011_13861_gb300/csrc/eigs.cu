@@ -1,0 +1,425 @@
+// Eigensolver driver: thick-restart block Lanczos with full float64 re-orthogonalisation.
+//
+// The paper solves the standard-form problem A~' v' = lambda v' with implicitly restarted
+// Lanczos (Sec. 4.4.2).  Here the same Krylov iteration is organised as a thick restart
+// (equivalent to implicit restarting with exact shifts) in blocks of b vectors, so that one
+// on-the-fly kernel evaluation serves b right-hand sides:
+//
+//   expansion:  W = A~' Q_j;  H = V^T W;  W -= V H (twice, classical Gram-Schmidt);
+//               W = Q_{j+1} R (block Cholesky-QR, twice);  T holds V^T A~' V
+//   restart:    T = S Theta S^T (Jacobi);  keep p Ritz vectors Y = V S_{:,1:p};
+//               A~' Y = Y Theta_p + F S_{m-b:m,1:p}  with F the last orthogonalised W,
+//               so the new basis is [Y, orth(F)] with T = [Theta_p, (R S_last)^T; R S_last, .]
+//   residual:   ||A~' y_i - theta_i y_i|| = ||F s_i^{last}||  (Lanczos estimate), checked at the
+//               end with an explicit float64 application when requested.
+//
+// Method 1 ("mixed") runs the iteration with the float32 stage-5 kernel until the estimates
+// reach tol_low, then continues from the float32 Ritz vectors with the float64 operator in
+// one wide block (b = number of kept vectors), which converges in a few block steps.
+// Everything stays on the device; per restart the host reads back the Ritz values and
+// residual estimates of the wanted pairs (a few hundred bytes).
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "kl_internal.h"
+
+namespace kl {
+namespace {
+
+struct Eig {
+    kl_handle h;
+    cudaStream_t s;
+    int64_t N;
+    int mmax;    // capacity of the basis
+    int bmax;    // capacity of a block
+    kl::DevBuf bV, bW, bY, bT, bTc, bS, bSw, bTheta, bH, bH2, bG, bR, bR1, bRinv, bRtmp, bPart, bEst, bFlag, bSweeps;
+    double* V() { return static_cast<double*>(bV.ptr); }
+    double* W() { return static_cast<double*>(bW.ptr); }
+    double* Y() { return static_cast<double*>(bY.ptr); }
+    double* T() { return static_cast<double*>(bT.ptr); }
+    double* S() { return static_cast<double*>(bS.ptr); }
+    double* Sw() { return static_cast<double*>(bSw.ptr); }
+    double* Theta() { return static_cast<double*>(bTheta.ptr); }
+    double* H() { return static_cast<double*>(bH.ptr); }
+    double* H2() { return static_cast<double*>(bH2.ptr); }
+    double* G() { return static_cast<double*>(bG.ptr); }
+    double* R() { return static_cast<double*>(bR.ptr); }
+    double* R1() { return static_cast<double*>(bR1.ptr); }
+    double* Rinv() { return static_cast<double*>(bRinv.ptr); }
+    double* Rtmp() { return static_cast<double*>(bRtmp.ptr); }
+    double* Part() { return static_cast<double*>(bPart.ptr); }
+    double* Est() { return static_cast<double*>(bEst.ptr); }
+    int* Flag() { return static_cast<int*>(bFlag.ptr); }
+    int* Sweeps() { return static_cast<int*>(bSweeps.ptr); }
+    int maxparts = 0;
+    // statistics
+    int applies = 0, applies64 = 0, block_applies = 0;
+    uint64_t rng_offset = 0;
+    uint64_t seed = 1;
+
+    ~Eig() {
+        kl::DevBuf* all[] = {&bV, &bW, &bY, &bT, &bTc, &bS, &bSw, &bTheta, &bH, &bH2, &bG, &bR, &bR1, &bRinv, &bRtmp, &bPart, &bEst, &bFlag, &bSweeps};
+        for (auto* b : all) release(*b);
+    }
+
+    kl_status alloc(int m, int b) {
+        mmax = m;
+        bmax = b;
+        const size_t N8 = size_t(N) * sizeof(double);
+        KL_TRY(ensure(bV, N8 * (m + b)));
+        KL_TRY(ensure(bW, N8 * std::max(b, 64)));
+        KL_TRY(ensure(bY, N8 * std::max(m, 64)));
+        KL_TRY(ensure(bT, sizeof(double) * m * m));
+        KL_TRY(ensure(bTc, sizeof(double) * m * m));
+        KL_TRY(ensure(bS, sizeof(double) * m * m));
+        KL_TRY(ensure(bSw, sizeof(double) * m * m));
+        KL_TRY(ensure(bTheta, sizeof(double) * m));
+        KL_TRY(ensure(bH, sizeof(double) * m * b));
+        KL_TRY(ensure(bH2, sizeof(double) * m * b));
+        KL_TRY(ensure(bG, sizeof(double) * b * b));
+        KL_TRY(ensure(bR, sizeof(double) * b * b));
+        KL_TRY(ensure(bR1, sizeof(double) * b * b));
+        KL_TRY(ensure(bRinv, sizeof(double) * b * b));
+        KL_TRY(ensure(bRtmp, sizeof(double) * b * b));
+        maxparts = gram_parts(N);
+        KL_TRY(ensure(bPart, sizeof(double) * size_t(maxparts) * std::max(192 * 32, 64 * 64)));
+        KL_TRY(ensure(bEst, sizeof(double) * (m + 64)));
+        KL_TRY(ensure(bFlag, sizeof(int) * 4));
+        KL_TRY(ensure(bSweeps, sizeof(int) * 4));
+        return KL_OK;
+    }
+
+    kl_status apply(int prec, const double* Q, double* Wout, int b) {
+        KL_TRY(apply_impl(h, prec, Q, N, Wout, N, b, s));
+        applies += b;
+        if (prec == KL_P_FP64) applies64 += b;
+        block_applies += 1;
+        return KL_OK;
+    }
+
+    // H (j x b, ld mmax) = V[:, 0:j]^T W ; W -= V H   (twice); returns accumulated H in H()
+    kl_status orthogonalize(double* Wb, int b, int j) {
+        if (j == 0) return KL_OK;
+        cudaError_t e = launch_gram(V(), N, j, Wb, N, b, N, H(), mmax, Part(), maxparts, s);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        e = launch_gemm_tall(-1.0, V(), N, N, j, H(), mmax, b, 1.0, Wb, N, s);
+        if (e != cudaSuccess) return cuda_fail(e, "update");
+        e = launch_gram(V(), N, j, Wb, N, b, N, H2(), mmax, Part(), maxparts, s);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        e = launch_gemm_tall(-1.0, V(), N, N, j, H2(), mmax, b, 1.0, Wb, N, s);
+        if (e != cudaSuccess) return cuda_fail(e, "update");
+        // H += H2 (both stored with ld mmax, j rows, b columns)
+        for (int c = 0; c < b; ++c) {
+            e = launch_add_inplace(H() + size_t(c) * mmax, H2() + size_t(c) * mmax, j, s);
+            if (e != cudaSuccess) return cuda_fail(e, "accumulate");
+        }
+        return KL_OK;
+    }
+
+    // W = Q R with Q orthonormal (CholQR2).  R (b x b, ld b) in R(); Q written to dst (ld N).
+    // Returns true in *deficient when the block is numerically rank deficient.
+    kl_status cholqr(double* Wb, int b, double* dst, bool* deficient) {
+        int flags[2] = {0, 0};
+        double* cur = Wb;
+        for (int pass = 0; pass < 2; ++pass) {
+            cudaError_t e = launch_gram(cur, N, b, cur, N, b, N, G(), b, Part(), maxparts, s);
+            if (e != cudaSuccess) return cuda_fail(e, "gram");
+            double* Rp = pass == 0 ? R1() : Rtmp();
+            e = launch_chol_inv(G(), b, b, Rinv(), Rp, Flag() + pass, s);
+            if (e != cudaSuccess) return cuda_fail(e, "chol");
+            double* out = (pass == 0) ? Y() : dst;
+            e = launch_gemm_tall(1.0, cur, N, N, b, Rinv(), b, b, 0.0, out, N, s);
+            if (e != cudaSuccess) return cuda_fail(e, "scale");
+            cur = out;
+        }
+        // R = R2 R1 (upper triangular product), computed as a tiny "tall" product with N = b rows
+        // R^T = R1^T R2^T ; use gemm on the transposes: R[i][j] = sum_c R2[i][c] R1[c][j]
+        // gemm_tall computes C[r, :] = A[r, :] B with A = R2 (b x b, ld b), B = R1.
+        cudaError_t e = launch_gemm_tall(1.0, Rtmp(), b, b, b, R1(), b, b, 0.0, R(), b, s);
+        if (e != cudaSuccess) return cuda_fail(e, "R product");
+        KL_CUDA(cudaMemcpyAsync(flags, Flag(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        KL_CUDA(cudaStreamSynchronize(s));
+        *deficient = (flags[0] != 0);
+        return KL_OK;
+    }
+
+    // fresh random directions orthogonal to V[:, 0:j] written into dst (N x b)
+    kl_status random_orthonormal(double* dst, int b, int j) {
+        for (int attempt = 0; attempt < 3; ++attempt) {
+            cudaError_t e = launch_random_block(W(), N, N, b, seed ^ 0xA5A5A5A5ull, rng_offset, s);
+            rng_offset += uint64_t(N) * b;
+            if (e != cudaSuccess) return cuda_fail(e, "random block");
+            KL_TRY(orthogonalize(W(), b, j));
+            bool def = false;
+            KL_TRY(cholqr(W(), b, dst, &def));
+            if (!def) return KL_OK;
+        }
+        return fail(KL_ERR_NUMERIC, "could not extend the Krylov basis");
+    }
+
+    kl_status sym_eig(int m) {
+        cudaError_t e = launch_sym_eig_ws(T(), mmax, m, Theta(), S(), mmax, Sw(), Sweeps(), s);
+        if (e != cudaSuccess) return cuda_fail(e, "small eigensolver");
+        return KL_OK;
+    }
+};
+
+struct Phase {
+    int prec;
+    int b;
+    int m;
+    int keep;
+    double tol;
+    bool early_rr;     // Rayleigh-Ritz after every block step (used for the float64 polish)
+    int maxrestart;
+    int exit_vecs;     // Ritz vectors left in V[:, 0:exit_vecs] on exit (>= k)
+};
+
+// Runs one thick-restart block Lanczos phase.  On entry V[:, 0:j0] holds an orthonormal basis
+// whose last b columns form the active block and T[0:j0, 0:j0] = V^T A V is valid for all
+// but the active block's column (the next expansion recomputes it).  On exit V[:, 0:k] holds
+// the k wanted Ritz vectors, Theta their values and est[] the residual estimates.
+kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::vector<double>& theta,
+                    std::vector<double>& est, bool* converged) {
+    const int b = P.b, m = P.m;
+    int j = j0;
+    *converged = false;
+    theta.assign(m, 0.0);
+    est.assign(m, 0.0);
+    for (int it = 0;; ++it) {
+        // ---- expansion until the basis is full ----
+        bool full = false;
+        while (!full) {
+            double* Q = E.V() + size_t(j - b) * E.N;
+            KL_TRY(E.apply(P.prec, Q, E.W(), b));
+            KL_TRY(E.orthogonalize(E.W(), b, j));
+            cudaError_t e = launch_fill_T_block(E.T(), E.mmax, 0, j - b, E.H(), E.mmax, j, b, true, E.s);
+            if (e != cudaSuccess) return cuda_fail(e, "fill T");
+            if (j + b > m) {
+                full = true;
+                break;
+            }
+            if (P.early_rr) {
+                // Rayleigh-Ritz on the current basis, residual block = W (not yet normalised)
+                KL_TRY(E.sym_eig(j));
+                e = launch_gram(E.W(), E.N, b, E.W(), E.N, b, E.N, E.G(), b, E.Part(), E.maxparts, E.s);
+                if (e != cudaSuccess) return cuda_fail(e, "gram");
+                const int nc = std::min(j, k);
+                e = launch_residual_norms(E.G(), b, E.S(), E.mmax, j - b, b, nc, E.Est(), E.s);
+                if (e != cudaSuccess) return cuda_fail(e, "residual norms");
+                std::vector<double> th(nc), rs(nc);
+                KL_CUDA(cudaMemcpyAsync(th.data(), E.Theta(), nc * sizeof(double), cudaMemcpyDeviceToHost, E.s));
+                KL_CUDA(cudaMemcpyAsync(rs.data(), E.Est(), nc * sizeof(double), cudaMemcpyDeviceToHost, E.s));
+                KL_CUDA(cudaStreamSynchronize(E.s));
+                bool ok = (nc == k);
+                for (int i = 0; i < nc && ok; ++i) ok = rs[i] <= P.tol * fabs(th[i]);
+                if (ok) {
+                    // Ritz vectors into V[:, 0:k]
+                    e = launch_gemm_tall(1.0, E.V(), E.N, E.N, j, E.S(), E.mmax, k, 0.0, E.Y(), E.N, E.s);
+                    if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
+                    e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, k, E.s);
+                    if (e != cudaSuccess) return cuda_fail(e, "copy");
+                    for (int i = 0; i < k; ++i) {
+                        theta[i] = th[i];
+                        est[i] = rs[i];
+                    }
+                    *converged = true;
+                    return KL_OK;
+                }
+            }
+            bool def = false;
+            double* dst = E.V() + size_t(j) * E.N;
+            KL_TRY(E.cholqr(E.W(), b, dst, &def));
+            if (def) {
+                KL_TRY(E.random_orthonormal(dst, b, j));
+                // coupling is lost: the new block is a fresh direction (R = 0)
+                e = cudaMemsetAsync(E.R(), 0, sizeof(double) * b * b, E.s);
+                if (e != cudaSuccess) return cuda_fail(e, "memset");
+            }
+            // T[j:j+b, j-b:j] = R ; symmetric
+            e = launch_fill_T_block(E.T(), E.mmax, j, j - b, E.R(), b, b, b, true, E.s);
+            if (e != cudaSuccess) return cuda_fail(e, "fill T");
+            j += b;
+        }
+        // ---- Rayleigh-Ritz on the full basis ----
+        KL_TRY(E.sym_eig(j));
+        cudaError_t e = launch_gram(E.W(), E.N, b, E.W(), E.N, b, E.N, E.G(), b, E.Part(), E.maxparts, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        const int nk = std::min(P.keep, j);
+        e = launch_residual_norms(E.G(), b, E.S(), E.mmax, j - b, b, nk, E.Est(), E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "residual norms");
+        KL_CUDA(cudaMemcpyAsync(theta.data(), E.Theta(), j * sizeof(double), cudaMemcpyDeviceToHost, E.s));
+        KL_CUDA(cudaMemcpyAsync(est.data(), E.Est(), nk * sizeof(double), cudaMemcpyDeviceToHost, E.s));
+        KL_CUDA(cudaStreamSynchronize(E.s));
+        bool ok = true;
+        for (int i = 0; i < k; ++i) ok = ok && (est[i] <= P.tol * fabs(theta[i]));
+        const bool last = (it >= P.maxrestart);
+        const int keep = ok || last ? std::min(std::max(k, P.exit_vecs), j) : P.keep;
+        // Ritz vectors V S[:, 0:keep] -> Y -> V[:, 0:keep]
+        e = launch_gemm_tall(1.0, E.V(), E.N, E.N, j, E.S(), E.mmax, keep, 0.0, E.Y(), E.N, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
+        e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, keep, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy");
+        if (ok || last) {
+            *converged = ok;
+            return KL_OK;
+        }
+        ++*restarts;
+        // residual block F = W -> orthonormal block after the kept Ritz vectors
+        bool def = false;
+        double* dst = E.V() + size_t(keep) * E.N;
+        KL_TRY(E.orthogonalize(E.W(), b, keep));   // F is orthogonal to V already; cleans round-off
+        KL_TRY(E.cholqr(E.W(), b, dst, &def));
+        if (def) {
+            KL_TRY(E.random_orthonormal(dst, b, keep));
+            e = cudaMemsetAsync(E.R(), 0, sizeof(double) * b * b, E.s);
+            if (e != cudaSuccess) return cuda_fail(e, "memset");
+        }
+        e = launch_set_restart_T(E.T(), E.mmax, E.mmax, E.Theta(), keep, E.R(), b, E.S(), E.mmax, j - b, b, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "restart T");
+        j = keep + b;
+    }
+}
+
+}  // namespace
+
+kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, double* evals_host, double* evecs_dev,
+                    int64_t ldv, kl_eig_info* info, cudaStream_t s) {
+    auto t0 = std::chrono::steady_clock::now();
+    kl_eig_opts o{};
+    o.method = 0;
+    o.block = 1;
+    o.ncv = 0;
+    o.maxiter = 0;
+    o.seed = 1;
+    o.start_dev = nullptr;
+    o.tol_low = 0.0;
+    o.verify = 1;
+    if (opts_in) o = *opts_in;
+    const int b = std::max(1, o.block);
+    if (o.method != 0 && o.method != 1) return fail(KL_ERR_INVALID_ARG, "method must be 0 or 1");
+    if (b > 64) return fail(KL_ERR_INVALID_ARG, "block size above 64");
+    const int64_t N = h->N;
+    int m = o.ncv > 0 ? o.ncv : std::max(2 * k + 1, k + 3 * b);
+    m = (m + b - 1) / b * b;
+    if (m > 160) m = 160 / b * b;
+    if (m < k + 2 * b) return fail(KL_ERR_INVALID_ARG, "basis size too small for k and the block size (need ncv >= k + 2 block, <= 160)");
+    if (m > N) return fail(KL_ERR_INVALID_ARG, "basis size exceeds the problem dimension; use a smaller ncv / block");
+    const int maxrestart = o.maxiter > 0 ? o.maxiter : 1000;
+    // kept Ritz vectors: m - c b with c ~ (m - k) / (2b), at least k
+    int c = std::max(1, (m - k) / (2 * b));
+    int keep = m - c * b;
+    if (keep < k) keep = k;
+    while ((m - keep) % b != 0) --keep;
+
+    // float64 polish of the mixed method: one wide block over the kept float32 Ritz vectors
+    const int pol_b = std::min(std::max(k + 4, b), 48);
+    const int pol_m = std::min(3 * pol_b, 160 / pol_b * pol_b);
+
+    // stage-5 event timing for the whole call (read back at the end)
+    h->prof_on = (info != nullptr);
+    h->prof_rec.clear();
+    struct ProfOff {
+        kl_handle h;
+        ~ProfOff() { h->prof_on = false; }
+    } prof_off{h};
+
+    Eig E;
+    E.h = h;
+    E.s = s;
+    E.N = N;
+    E.seed = o.seed;
+    const int cap_m = std::max(m, pol_m), cap_b = std::max(b, pol_b);
+    KL_TRY(E.alloc(cap_m, cap_b));
+    cudaError_t e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+
+    // ---- start block ----
+    if (o.start_dev) {
+        e = launch_copy_block(o.start_dev, N, E.W(), N, N, b, s);
+    } else {
+        e = launch_random_block(E.W(), N, N, b, o.seed, 0, s);
+        E.rng_offset = uint64_t(N) * b;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "start block");
+    bool def = false;
+    KL_TRY(E.cholqr(E.W(), b, E.V(), &def));
+    if (def) KL_TRY(E.random_orthonormal(E.V(), b, 0));
+
+    std::vector<double> theta, est;
+    int restarts = 0;
+    bool conv = false;
+    double ms32 = 0.0;
+    if (o.method == 0) {
+        Phase P{KL_P_FP64, b, m, keep, tol, false, maxrestart, k};
+        KL_TRY(run_phase(E, P, k, b, &restarts, theta, est, &conv));
+    } else {
+        const double tl = o.tol_low > 0.0 ? o.tol_low : 1e-5;
+        const int pb = std::min(pol_b, m);
+        Phase P1{KL_P_FP32, b, m, keep, std::max(tl, tol), false, maxrestart, pb};
+        KL_TRY(run_phase(E, P1, k, b, &restarts, theta, est, &conv));
+        KL_CUDA(cudaStreamSynchronize(s));
+        ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
+        // they form the first, wide block of a float64 block Lanczos run.
+        Phase P2{KL_P_FP64, pb, pol_m, pb, tol, true, maxrestart, k};
+        // the active block is V[:, 0:pb]; T is rebuilt by the first expansion
+        e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
+        if (e != cudaSuccess) return cuda_fail(e, "memset");
+        KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
+    }
+
+    // ---- outputs ----
+    for (int i = 0; i < k; ++i) evals_host[i] = theta[i];
+    std::vector<double> resid(k, 0.0);
+    for (int i = 0; i < k; ++i) resid[i] = est[i] / std::max(fabs(theta[i]), 1e-300);
+    if (o.verify) {
+        // explicit float64 residuals ||A y - theta y|| / |theta|
+        KL_TRY(E.apply(KL_P_FP64, E.V(), E.Y(), k));
+        KL_CUDA(cudaMemcpyAsync(E.Theta(), theta.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+        e = launch_ritz_resid(E.Y(), E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
+        if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
+        KL_CUDA(cudaMemcpyAsync(resid.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (evecs_dev) {
+        e = launch_copy_block(E.V(), N, evecs_dev, ldv, N, k, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy eigenvectors");
+    }
+    KL_CUDA(cudaStreamSynchronize(s));
+    int nconv = 0;
+    for (int i = 0; i < k; ++i) nconv += (resid[i] <= tol) ? 1 : 0;
+    if (info) {
+        info->applies = E.applies;
+        info->applies_fp64 = E.applies64;
+        info->block_applies = E.block_applies;
+        info->restarts = restarts;
+        info->converged = nconv;
+        for (int i = 0; i < 64; ++i) info->resid[i] = i < k ? resid[i] : 0.0;
+        info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        info->ms_fp32_phase = ms32;
+        info->stage5_calls_fp64 = info->stage5_calls_fp32 = 0;
+        info->ms_stage5_fp64 = info->ms_stage5_fp32 = 0.0;
+        info->pairs_fp64 = info->pairs_fp32 = 0.0;
+        const double pairs = double(h->Nt) * double(h->Nt);
+        for (const auto& r : h->prof_rec) {
+            float ms = 0.f;
+            KL_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[r.ev], h->prof_ev[r.ev + 1]));
+            if (r.fp64) {
+                info->stage5_calls_fp64 += 1;
+                info->ms_stage5_fp64 += ms;
+                info->pairs_fp64 += pairs;
+            } else {
+                info->stage5_calls_fp32 += 1;
+                info->ms_stage5_fp32 += ms;
+                info->pairs_fp32 += pairs;
+            }
+        }
+    }
+    if (nconv < k) return fail(KL_ERR_NOT_CONVERGED, "not every wanted eigenpair reached the tolerance");
+    return KL_OK;
+}
+
+}  // namespace kl

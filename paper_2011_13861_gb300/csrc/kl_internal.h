@@ -1,0 +1,158 @@
+// Internal declarations shared by the translation units of libkl.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kl.h"
+
+namespace kl {
+
+// ----------------------------------------------------------------------------------------
+// error handling
+// ----------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+kl_status fail(kl_status st, const std::string& msg);
+kl_status cuda_fail(cudaError_t e, const char* what);
+void count_launches(int n);   // kernel-launch accounting (kl_kernel_launches)
+
+#define KL_CUDA(...)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (__VA_ARGS__);                                        \
+        if (e_ != cudaSuccess) return ::kl::cuda_fail(e_, #__VA_ARGS__);       \
+    } while (0)
+
+#define KL_TRY(...)                                                    \
+    do {                                                                \
+        kl_status s_ = (__VA_ARGS__);                                          \
+        if (s_ != KL_OK) return s_;                                     \
+    } while (0)
+
+// ----------------------------------------------------------------------------------------
+// host set-up (setup.cpp)
+// ----------------------------------------------------------------------------------------
+struct Direction {
+    int p = 0, ne = 0, pt = 0, net = 0;
+    int n = 0, nt = 0;
+    std::vector<double> xi;   // Greville abscissae of the interpolation space (nt)
+    std::vector<double> C;    // C_k = B~_k^{-T} M_k L_k^{-T}, nt x n row-major
+    std::vector<double> Linv; // L_k^{-1}, n x n row-major (lower triangular)
+};
+
+kl_status build_direction(int p, int ne, int pt, int net, Direction* out);
+
+// ----------------------------------------------------------------------------------------
+// device kernels (launchers)
+// ----------------------------------------------------------------------------------------
+// Mode-k contraction of a block of nvec tensors viewed as [A][n][B]:
+//   Y[v][a][i][b] = sum_j Ct[j * m + i] * X[v][a][j][b] (* scale[a][i][b] if scale != null)
+template <typename Tin, typename Tc, typename Tout>
+cudaError_t launch_contract(const Tin* X, int64_t ldx, Tout* Y, int64_t ldy, const Tc* Ct, int64_t A,
+                            int n, int m, int64_t B, int nvec, const Tc* scale, cudaStream_t s);
+
+struct CovParams {
+    int kind;              // kl_kernel_kind
+    int poly_m;            // exponent of the polynomial test kernel
+    int64_t Nt;            // number of points
+    int64_t ldp;           // stride between the x, y, z coordinate arrays
+    const double* P64;     // 3 x ldp, coordinates (pre-scaled for EXP/GAUSS/EXP_SEPARABLE)
+    const float* P32;      // 3 x ldp, float coordinates pre-scaled for base-2 exponentials
+    const double* tab;     // 64-entry table 2^(j/64)
+};
+
+// Stage 5: z[:, v] = scale2 * (J .) sum_l Gamma(x_k, x_l) u[:, v]; partial sums over column
+// splits go to `part` (splits * nvec * Nt doubles) and are combined in fixed order.
+cudaError_t launch_covmv64(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z,
+                           int64_t ldz, double scale2, const double* J, double* part, int splits,
+                           cudaStream_t s);
+cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z,
+                           int64_t ldz, double scale2, const double* J, double* part, int splits,
+                           cudaStream_t s);
+int covmv_splits(int64_t Nt, int nvec, bool fp32);
+
+// dense block linear algebra (linalg.cu)
+cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
+                        int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s);
+int gram_parts(int64_t N);
+cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t N, int p,
+                             const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
+                             cudaStream_t s);
+cudaError_t launch_chol_inv(double* G, int ldg, int b, double* Rinv, double* R, int* flag,
+                            cudaStream_t s);
+cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64_t seed,
+                                uint64_t offset, cudaStream_t s);
+cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, double* S, int lds,
+                              double* work, int* sweeps_out, cudaStream_t s);
+cudaError_t launch_residual_norms(const double* G, int ldg, const double* S, int lds, int srow0,
+                                  int b, int ncols, double* out, cudaStream_t s);
+cudaError_t launch_ritz_resid(const double* AY, const double* Y, int64_t ld, int64_t N, int k,
+                              const double* theta, double* part, int maxparts, double* out,
+                              cudaStream_t s);
+cudaError_t launch_set_restart_T(double* T, int ldt, int m, const double* theta, int p,
+                                 const double* R, int ldr, const double* S, int lds, int srow0,
+                                 int b, cudaStream_t s);
+cudaError_t launch_copy_block(const double* src, int64_t lds, double* dst, int64_t ldd,
+                              int64_t rows, int cols, cudaStream_t s);
+cudaError_t launch_to_float(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
+                            int cols, cudaStream_t s);
+cudaError_t launch_fill_T_block(double* T, int ldt, int r0, int c0, const double* H, int ldh,
+                                int rows, int cols, bool symmetric, cudaStream_t s);
+cudaError_t launch_add_inplace(double* H, const double* H2, int n, cudaStream_t s);
+
+// ----------------------------------------------------------------------------------------
+// handle
+// ----------------------------------------------------------------------------------------
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+kl_status ensure(DevBuf& b, size_t bytes);
+void release(DevBuf& b);
+
+}  // namespace kl
+
+struct kl_handle_s {
+    int dim = 0;
+    kl_kernel kernel{};
+    kl::Direction dir[3];
+    int n[3] = {1, 1, 1}, nt[3] = {1, 1, 1};
+    int64_t N = 0, Nt = 0;
+    int64_t ldw = 0;              // leading dimension of the intermediate tensors (largest stage size)
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    double Jval = 1.0;
+    std::vector<double> X_host;  // Nt x 3 row-major physical points
+    // device set-up data
+    double* dCt[3] = {nullptr, nullptr, nullptr};   // forward operator of mode k, layout n_k x nt_k
+    double* dC[3] = {nullptr, nullptr, nullptr};    // backward operator of mode k, layout nt_k x n_k
+    float* fCt[3] = {nullptr, nullptr, nullptr};
+    float* fC[3] = {nullptr, nullptr, nullptr};
+    double* dLinvT[3] = {nullptr, nullptr, nullptr}; // (L_k^{-T})^T layout for kl_to_bspline
+    double* dP = nullptr;     // 3 x Nt pre-scaled coordinates
+    float* fP = nullptr;      // 3 x Nt float coordinates scaled for ex2
+    double* dJ = nullptr;     // Nt
+    float* fJ = nullptr;      // Nt
+    double* dTab = nullptr;   // 64
+    // workspace
+    kl::DevBuf w_a, w_b, w_f32a, w_f32b, w_part;
+    // stage-5 event timing (enabled by kl_eigs while it runs)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;       // pool, two per record
+    struct ProfRec { int ev; bool fp64; int nvec; };
+    std::vector<ProfRec> prof_rec;
+};
+
+namespace kl {
+kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, double* y,
+                     int64_t ldy, int nvec, cudaStream_t s);
+kl_status forward_impl(kl_handle h, const double* v, int64_t ldv, double* u, int64_t ldu, int nvec,
+                       cudaStream_t s);
+kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, double* z,
+                     int64_t ldz, int nvec, bool withJ, cudaStream_t s);
+kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, int64_t ldy,
+                        int nvec, bool zHasJ, cudaStream_t s);
+kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host,
+                    double* evecs_dev, int64_t ldv, kl_eig_info* info, cudaStream_t s);
+}  // namespace kl

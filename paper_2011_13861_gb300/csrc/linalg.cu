@@ -1,0 +1,532 @@
+// Float64 block linear algebra of the eigensolver: tall-skinny Gram products and updates,
+// block Cholesky-QR, counter-based random blocks, the small symmetric eigenproblem of the
+// Rayleigh-Ritz step, residual norms and restart bookkeeping.  Every reduction is
+// two-stage with a fixed combination order, so repeated runs are bit-identical.
+#include <math.h>
+
+#include "kl_internal.h"
+
+namespace kl {
+namespace {
+
+constexpr int kGramThreads = 256;
+constexpr int kGramRows = 16;
+constexpr int kGramMaxP = 192;
+constexpr int kGramMaxQ = 32;
+
+// part[g][i*q + j] = sum over this CTA's rows r of A[r, i] * B[r, j]
+__global__ void __launch_bounds__(kGramThreads)
+gram_partial(const double* __restrict__ A, int64_t lda, int p, const double* __restrict__ B,
+             int64_t ldb, int q, int64_t N, int64_t rows_per_part, double* __restrict__ part) {
+    __shared__ double sA[kGramRows][kGramMaxP + 1];
+    __shared__ double sB[kGramRows][kGramMaxQ + 1];
+    const int outs = p * q;
+    constexpr int kMaxPer = (kGramMaxP * kGramMaxQ + kGramThreads - 1) / kGramThreads;
+    double acc[kMaxPer];
+#pragma unroll
+    for (int t = 0; t < kMaxPer; ++t) acc[t] = 0.0;
+    const int64_t r_begin = int64_t(blockIdx.x) * rows_per_part;
+    int64_t r_end = r_begin + rows_per_part;
+    if (r_end > N) r_end = N;
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramRows) {
+        __syncthreads();
+        const int rl = threadIdx.x % kGramRows;
+        const int64_t r = r0 + rl;
+        for (int c = threadIdx.x / kGramRows; c < p; c += kGramThreads / kGramRows)
+            sA[rl][c] = (r < r_end) ? A[c * lda + r] : 0.0;
+        for (int c = threadIdx.x / kGramRows; c < q; c += kGramThreads / kGramRows)
+            sB[rl][c] = (r < r_end) ? B[c * ldb + r] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kMaxPer; ++t) {
+            const int e = threadIdx.x + t * kGramThreads;
+            if (e < outs) {
+                const int i = e / q, j = e - i * q;
+                double s = acc[t];
+#pragma unroll 8
+                for (int rr = 0; rr < kGramRows; ++rr) s = fma(sA[rr][i], sB[rr][j], s);
+                acc[t] = s;
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kMaxPer; ++t) {
+        const int e = threadIdx.x + t * kGramThreads;
+        if (e < outs) part[int64_t(blockIdx.x) * outs + e] = acc[t];
+    }
+}
+
+__global__ void gram_reduce(const double* __restrict__ part, int parts, int p, int q,
+                            double* __restrict__ out, int ldo) {
+    const int outs = p * q;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < outs; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < parts; ++g) s += part[int64_t(g) * outs + e];
+        const int i = e / q, j = e - i * q;
+        out[i + int64_t(j) * ldo] = s;
+    }
+}
+
+// C[r, 0:q] = alpha * A[r, 0:p] B + beta * C[r, 0:q], one row per thread, B in shared memory
+template <int QB>
+__global__ void __launch_bounds__(256)
+gemm_tall_kernel(double alpha, const double* __restrict__ A, int64_t lda, int64_t N, int p,
+                 const double* __restrict__ B, int ldb, int q, double beta, double* __restrict__ C,
+                 int64_t ldc) {
+    extern __shared__ double sBm[];   // p x QB
+    for (int e = threadIdx.x; e < p * QB; e += blockDim.x) {
+        const int i = e / QB, j = e - i * QB;
+        sBm[e] = (j < q) ? B[i + int64_t(j) * ldb] : 0.0;
+    }
+    __syncthreads();
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < N;
+         r += int64_t(gridDim.x) * blockDim.x) {
+        double acc[QB];
+#pragma unroll
+        for (int j = 0; j < QB; ++j) acc[j] = 0.0;
+        for (int i = 0; i < p; ++i) {
+            const double a = A[i * lda + r];
+#pragma unroll
+            for (int j = 0; j < QB; ++j) acc[j] = fma(a, sBm[i * QB + j], acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < QB; ++j) {
+            if (j < q) {
+                double* c = C + j * ldc + r;
+                *c = (beta == 0.0) ? alpha * acc[j] : fma(alpha, acc[j], beta * (*c));
+            }
+        }
+    }
+}
+
+// G (b x b, column-major) = R^T R with R upper triangular; also R^{-1}.  One CTA.
+// flag is set to 1 when a pivot is not positive (rank-deficient block).
+__global__ void chol_inv_kernel(const double* __restrict__ G, int ldg, int b, double* __restrict__ Rinv,
+                                double* __restrict__ R, int* flag) {
+    extern __shared__ double sR[];   // b x b, column-major
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) sR[e] = 0.0;
+    __syncthreads();
+    double gmax = 0.0;
+    for (int i = 0; i < b; ++i) gmax = fmax(gmax, G[i + int64_t(i) * ldg]);
+    for (int j = 0; j < b; ++j) {
+        if (threadIdx.x == 0) {
+            double s = G[j + int64_t(j) * ldg];
+            for (int k = 0; k < j; ++k) s -= sR[k + j * b] * sR[k + j * b];
+            if (!(s > 1e-28 * gmax) || !isfinite(s)) {
+                bad = 1;
+                s = 1e-28 * gmax + 1e-300;
+            }
+            sR[j + j * b] = sqrt(s);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) {
+            double s = G[j + int64_t(i) * ldg];
+            for (int k = 0; k < j; ++k) s -= sR[k + j * b] * sR[k + i * b];
+            sR[j + i * b] = s / sR[j + j * b];
+        }
+        __syncthreads();
+    }
+    // R^{-1}: column c solves R x = e_c by back substitution
+    for (int c = threadIdx.x; c < b; c += blockDim.x) {
+        for (int i = b - 1; i >= 0; --i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) s -= sR[i + k * b] * Rinv[k + c * b];
+            Rinv[i + c * b] = (i <= c) ? s / sR[i + i * b] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) R[e] = sR[e];
+    if (threadIdx.x == 0) *flag = bad;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): uniform(-1, 1) from (seed, counter)
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return double(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+__global__ void random_block_kernel(double* V, int64_t ldv, int64_t N, int b, uint64_t seed,
+                                    uint64_t offset) {
+    const int64_t total = N * b;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = e / N, r = e - c * N;
+        V[c * ldv + r] = splitmix_uniform(seed, offset + uint64_t(e));
+    }
+}
+
+// ---- small symmetric eigenproblem: parallel cyclic Jacobi (round-robin pair ordering) ----
+constexpr int kEigThreads = 256;
+constexpr int kEigMax = 160;
+
+__device__ __forceinline__ void rr_pair(int i, int r, int mp, int* a, int* b) {
+    // round r of the circle method for mp (even) players; pair i
+    if (i == 0) {
+        *a = 0;
+        *b = ((mp - 2 + r) % (mp - 1)) + 1;
+    } else {
+        *a = ((i - 1 + r) % (mp - 1)) + 1;
+        *b = ((mp - 2 - i + r) % (mp - 1)) + 1;
+    }
+}
+
+__global__ void __launch_bounds__(kEigThreads)
+sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restrict__ evals,
+               double* __restrict__ Sout, int lds, double* __restrict__ W, int* sweeps_out) {
+    extern __shared__ double sT[];          // m x m, row-major with stride m
+    __shared__ double cs[kEigMax / 2 + 1][2];
+    __shared__ int prs[kEigMax / 2 + 1][2];
+    __shared__ int rotated;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e - i * m;
+        sT[e] = 0.5 * (Tin[i + int64_t(j) * ldt] + Tin[j + int64_t(i) * ldt]);
+        W[i + int64_t(j) * m] = (i == j) ? 1.0 : 0.0;    // eigenvector accumulator, column-major
+    }
+    __syncthreads();
+    const int mp = (m % 2 == 0) ? m : m + 1;
+    const int npairs = mp / 2;
+    int sweep = 0;
+    for (; sweep < 40; ++sweep) {
+        if (tid == 0) rotated = 0;
+        __syncthreads();
+        for (int r = 0; r < mp - 1; ++r) {
+            for (int i = tid; i < npairs; i += blockDim.x) {
+                int a, b;
+                rr_pair(i, r, mp, &a, &b);
+                if (a > b) { int t = a; a = b; b = t; }
+                double c = 1.0, s = 0.0;
+                if (b < m) {
+                    const double apq = sT[a * m + b];
+                    const double app = sT[a * m + a], aqq = sT[b * m + b];
+                    if (fabs(apq) > 1e-17 * sqrt(fabs(app * aqq)) && apq != 0.0) {
+                        const double theta = (aqq - app) / (2.0 * apq);
+                        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(t * t + 1.0);
+                        s = t * c;
+                        rotated = 1;
+                    }
+                }
+                prs[i][0] = a;
+                prs[i][1] = b;
+                cs[i][0] = c;
+                cs[i][1] = s;
+            }
+            __syncthreads();
+            // rows: T <- J^T T
+            for (int e = tid; e < npairs * m; e += blockDim.x) {
+                const int i = e / m, j = e - i * m;
+                const int a = prs[i][0], b = prs[i][1];
+                if (b >= m || cs[i][1] == 0.0) continue;
+                const double c = cs[i][0], s = cs[i][1];
+                const double ta = sT[a * m + j], tb = sT[b * m + j];
+                sT[a * m + j] = c * ta - s * tb;
+                sT[b * m + j] = s * ta + c * tb;
+            }
+            __syncthreads();
+            // columns: T <- T J ; eigenvectors W <- W J
+            for (int e = tid; e < npairs * m; e += blockDim.x) {
+                const int i = e / m, j = e - i * m;
+                const int a = prs[i][0], b = prs[i][1];
+                if (b >= m || cs[i][1] == 0.0) continue;
+                const double c = cs[i][0], s = cs[i][1];
+                const double ta = sT[j * m + a], tb = sT[j * m + b];
+                sT[j * m + a] = c * ta - s * tb;
+                sT[j * m + b] = s * ta + c * tb;
+                const double wa = W[j + int64_t(a) * m], wb = W[j + int64_t(b) * m];
+                W[j + int64_t(a) * m] = c * wa - s * wb;
+                W[j + int64_t(b) * m] = s * wa + c * wb;
+            }
+            __syncthreads();
+            for (int i = tid; i < npairs; i += blockDim.x) {
+                const int a = prs[i][0], b = prs[i][1];
+                if (b < m && cs[i][1] != 0.0) {
+                    sT[a * m + b] = 0.0;
+                    sT[b * m + a] = 0.0;
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!rotated) break;
+    }
+    // sort descending: rank by (value desc, index asc)
+    for (int i = tid; i < m; i += blockDim.x) {
+        const double di = sT[i * m + i];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+            const double dj = sT[j * m + j];
+            if (dj > di || (dj == di && j < i)) ++rank;
+        }
+        evals[rank] = di;
+        for (int r = 0; r < m; ++r) Sout[r + int64_t(rank) * lds] = W[r + int64_t(i) * m];
+    }
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// out[i] = sqrt(s_i^T G s_i), s_i = S[srow0 : srow0 + b, i]
+__global__ void residual_norms_kernel(const double* __restrict__ G, int ldg, const double* __restrict__ S,
+                                      int lds, int srow0, int b, int ncols, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncols; i += gridDim.x * blockDim.x) {
+        const double* s = S + int64_t(i) * lds + srow0;
+        double acc = 0.0;
+        for (int a = 0; a < b; ++a) {
+            double t = 0.0;
+            for (int c = 0; c < b; ++c) t = fma(G[a + int64_t(c) * ldg], s[c], t);
+            acc = fma(s[a], t, acc);
+        }
+        out[i] = sqrt(fmax(acc, 0.0));
+    }
+}
+
+// part[g][i] = sum over this CTA's rows of (AY[r,i] - theta_i Y[r,i])^2
+__global__ void ritz_resid_partial(const double* __restrict__ AY, const double* __restrict__ Y, int64_t ld,
+                                   int64_t N, int k, const double* __restrict__ theta,
+                                   int64_t rows_per_part, double* __restrict__ part) {
+    __shared__ double red[256];
+    const int64_t r_begin = int64_t(blockIdx.x) * rows_per_part;
+    int64_t r_end = r_begin + rows_per_part;
+    if (r_end > N) r_end = N;
+    for (int i = 0; i < k; ++i) {
+        const double th = theta[i];
+        double s = 0.0;
+        for (int64_t r = r_begin + threadIdx.x; r < r_end; r += blockDim.x) {
+            const double d = AY[i * ld + r] - th * Y[i * ld + r];
+            s = fma(d, d, s);
+        }
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[int64_t(blockIdx.x) * k + i] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void ritz_resid_final(const double* __restrict__ part, int parts, int k,
+                                 const double* __restrict__ theta, double* __restrict__ out) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < parts; ++g) s += part[int64_t(g) * k + i];
+        out[i] = sqrt(s) / fabs(theta[i]);
+    }
+}
+
+// T = 0 except T[i][i] = theta_i (i < p) and the coupling rows/columns p..p+b-1:
+// T[p + a][i] = T[i][p + a] = sum_c R[a][c] S[srow0 + c][i]
+__global__ void set_restart_T_kernel(double* __restrict__ T, int ldt, int m, const double* __restrict__ theta,
+                                     int p, const double* __restrict__ R, int ldr,
+                                     const double* __restrict__ S, int lds, int srow0, int b) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+        const int i = e % m, j = e / m;
+        double v = 0.0;
+        if (i == j && i < p) v = theta[i];
+        int a = -1, col = -1;
+        if (i >= p && i < p + b && j < p) { a = i - p; col = j; }
+        if (j >= p && j < p + b && i < p) { a = j - p; col = i; }
+        if (a >= 0) {
+            double s = 0.0;
+            for (int c = a; c < b; ++c) s = fma(R[a + c * ldr], S[(srow0 + c) + int64_t(col) * lds], s);
+            v = s;
+        }
+        T[i + int64_t(j) * ldt] = v;
+    }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ src, int64_t lds, float* __restrict__ dst,
+                                int64_t ldd, int64_t rows, int cols) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = e / rows, r = e - c * rows;
+        dst[c * ldd + r] = float(src[c * lds + r]);
+    }
+}
+
+// T[r0 + i][c0 + j] = H[i][j]; if symmetric also T[c0 + j][r0 + i] = H[i][j]
+// (an overlapping diagonal block is symmetrised).
+__global__ void fill_T_block_kernel(double* __restrict__ T, int ldt, int r0, int c0,
+                                    const double* __restrict__ H, int ldh, int rows, int cols,
+                                    bool symmetric) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x) {
+        const int i = e % rows, j = e / rows;
+        const int gi = r0 + i, gj = c0 + j;
+        double v = H[i + int64_t(j) * ldh];
+        const bool diag_block = symmetric && gi >= c0 && gi < c0 + cols && gj >= r0 && gj < r0 + rows;
+        if (diag_block) v = 0.5 * (v + H[(gj - r0) + int64_t(gi - c0) * ldh]);
+        T[gi + int64_t(gj) * ldt] = v;
+        if (symmetric) T[gj + int64_t(gi) * ldt] = v;
+    }
+}
+
+__global__ void add_inplace_kernel(double* __restrict__ H, const double* __restrict__ H2, int n) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) H[e] += H2[e];
+}
+
+int grid_for(int64_t work, int threads, int cap) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return int(b);
+}
+
+}  // namespace
+
+int gram_parts(int64_t N) {
+    int64_t parts = (N + 255) / 256;
+    if (parts > 152 * 2) parts = 152 * 2;
+    if (parts < 1) parts = 1;
+    return int(parts);
+}
+
+cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
+                        int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s) {
+    if (p > kGramMaxP) return cudaErrorInvalidValue;
+    int parts = gram_parts(N);
+    if (parts > maxparts) parts = maxparts;
+    int64_t rpp = (N + parts - 1) / parts;
+    rpp = (rpp + kGramRows - 1) / kGramRows * kGramRows;
+    parts = int((N + rpp - 1) / rpp);
+    if (parts < 1) parts = 1;
+    for (int j0 = 0; j0 < q; j0 += kGramMaxQ) {
+        const int qq = (q - j0 < kGramMaxQ) ? q - j0 : kGramMaxQ;
+        count_launches(2);
+        gram_partial<<<parts, kGramThreads, 0, s>>>(A, lda, p, B + int64_t(j0) * ldb, ldb, qq, N, rpp, part);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        gram_reduce<<<grid_for(int64_t(p) * qq, 256, 64), 256, 0, s>>>(part, parts, p, qq,
+                                                                      out + int64_t(j0) * ldo, ldo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t N, int p,
+                             const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
+                             cudaStream_t s) {
+    if (N == 0 || q == 0) return cudaSuccess;
+    if (p == 0) {
+        // C = beta * C
+        return (beta == 1.0) ? cudaSuccess : cudaErrorInvalidValue;
+    }
+    for (int j0 = 0; j0 < q; j0 += 32) {
+        const int qq = (q - j0 < 32) ? q - j0 : 32;
+        const int QB = qq <= 1 ? 1 : qq <= 4 ? 4 : qq <= 8 ? 8 : qq <= 16 ? 16 : 32;
+        const size_t smem = size_t(p) * QB * sizeof(double);
+        const int blocks = grid_for(N, 256, 152 * 8);
+        const double* Bj = B + int64_t(j0) * ldb;
+        count_launches(1);
+        double* Cj = C + int64_t(j0) * ldc;
+        cudaError_t e = cudaSuccess;
+#define KL_GEMM_CASE(QQ)                                                                        \
+    case QQ:                                                                                    \
+        if (smem > 48 * 1024)                                                                   \
+            e = cudaFuncSetAttribute(gemm_tall_kernel<QQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
+        if (e != cudaSuccess) return e;                                                         \
+        gemm_tall_kernel<QQ><<<blocks, 256, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc); \
+        break;
+        switch (QB) {
+            KL_GEMM_CASE(1)
+            KL_GEMM_CASE(4)
+            KL_GEMM_CASE(8)
+            KL_GEMM_CASE(16)
+            KL_GEMM_CASE(32)
+        }
+#undef KL_GEMM_CASE
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_chol_inv(double* G, int ldg, int b, double* Rinv, double* R, int* flag,
+                            cudaStream_t s) {
+    chol_inv_kernel<<<1, 64, size_t(b) * b * sizeof(double), s>>>(G, ldg, b, Rinv, R, flag);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64_t seed,
+                                uint64_t offset, cudaStream_t s) {
+    random_block_kernel<<<grid_for(N * b, 256, 152 * 4), 256, 0, s>>>(V, ldv, N, b, seed, offset);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, double* S, int lds,
+                              double* work, int* sweeps_out, cudaStream_t s) {
+    if (m > kEigMax || m < 1) return cudaErrorInvalidValue;
+    const size_t smem = size_t(m) * m * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    sym_eig_kernel<<<1, kEigThreads, smem, s>>>(T, ldt, m, evals, S, lds, work, sweeps_out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norms(const double* G, int ldg, const double* S, int lds, int srow0,
+                                  int b, int ncols, double* out, cudaStream_t s) {
+    residual_norms_kernel<<<grid_for(ncols, 64, 64), 64, 0, s>>>(G, ldg, S, lds, srow0, b, ncols, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ritz_resid(const double* AY, const double* Y, int64_t ld, int64_t N, int k,
+                              const double* theta, double* part, int maxparts, double* out,
+                              cudaStream_t s) {
+    int parts = gram_parts(N);
+    if (parts > maxparts) parts = maxparts;
+    const int64_t rpp = (N + parts - 1) / parts;
+    ritz_resid_partial<<<parts, 256, 0, s>>>(AY, Y, ld, N, k, theta, rpp, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launches(2);
+    ritz_resid_final<<<1, 64, 0, s>>>(part, parts, k, theta, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_restart_T(double* T, int ldt, int m, const double* theta, int p,
+                                 const double* R, int ldr, const double* S, int lds, int srow0,
+                                 int b, cudaStream_t s) {
+    set_restart_T_kernel<<<grid_for(int64_t(m) * m, 256, 128), 256, 0, s>>>(T, ldt, m, theta, p, R, ldr, S,
+                                                                           lds, srow0, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_block(const double* src, int64_t lds, double* dst, int64_t ldd,
+                              int64_t rows, int cols, cudaStream_t s) {
+    return cudaMemcpy2DAsync(dst, size_t(ldd) * sizeof(double), src, size_t(lds) * sizeof(double),
+                             size_t(rows) * sizeof(double), size_t(cols), cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t launch_to_float(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
+                            int cols, cudaStream_t s) {
+    to_float_kernel<<<grid_for(rows * cols, 256, 152 * 8), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_T_block(double* T, int ldt, int r0, int c0, const double* H, int ldh,
+                                int rows, int cols, bool symmetric, cudaStream_t s) {
+    fill_T_block_kernel<<<grid_for(int64_t(rows) * cols, 256, 64), 256, 0, s>>>(T, ldt, r0, c0, H, ldh, rows,
+                                                                               cols, symmetric);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_inplace(double* H, const double* H2, int n, cudaStream_t s) {
+    add_inplace_kernel<<<grid_for(n, 256, 64), 256, 0, s>>>(H, H2, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace kl

@@ -1,0 +1,244 @@
+// Host set-up of the univariate factors (float64, once per handle).
+//
+// For one parametric direction this builds, from the degree and the number of uniform
+// elements of the trial space (B-splines B_i, Sec. 2.3) and of the interpolation space
+// (B~_i, Sec. 4.2):
+//   Z_k   = int B_i B_j            Gauss-Legendre, p+1 points per element (Sec. 3.5 Remark)
+//   L_k   with Z_k = L_k L_k^T     (Sec. 4.1, eq. cholesky)
+//   M_k   = int B~_i B_j           Gauss-Legendre on the merged breakpoints (Sec. 4.3)
+//   B~_k  = B~_j(xi_i)             collocation at the Greville abscissae (Sec. 4.2)
+// and folds them into the single dense factor used by the device contractions,
+//   C_k = B~_k^{-T} M_k L_k^{-T}   (n~_k x n_k),
+// so that the operator of Sec. 4.4.1 reads A~' = C^T J Gamma J C with C = C_d (x) ... (x) C_1.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "kl_internal.h"
+
+namespace kl {
+namespace {
+
+std::vector<double> open_knots(int p, int ne) {
+    std::vector<double> t;
+    for (int i = 0; i <= p; ++i) t.push_back(0.0);
+    for (int i = 1; i < ne; ++i) t.push_back(double(i) / double(ne));
+    for (int i = 0; i <= p; ++i) t.push_back(1.0);
+    return t;
+}
+
+// Knot span s with t[s] <= x < t[s+1], clamped to the last non-empty span at x = t.back().
+int find_span(const std::vector<double>& t, int p, double x) {
+    int n = int(t.size()) - p - 1;
+    if (x >= t[n]) return n - 1;
+    if (x <= t[p]) return p;
+    int lo = p, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (x < t[mid]) hi = mid; else lo = mid;
+    }
+    return lo;
+}
+
+// The p+1 non-zero B-splines N_{s-p..s}(x) on span s, by the triangular scheme of
+// "left"/"right" knot distances (de Boor's recurrence written per span).
+void nonzero_basis(const std::vector<double>& t, int p, int s, double x, double* N) {
+    std::vector<double> left(p + 1), right(p + 1);
+    N[0] = 1.0;
+    for (int j = 1; j <= p; ++j) {
+        left[j] = x - t[s + 1 - j];
+        right[j] = t[s + j] - x;
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            double denom = right[r + 1] + left[j - r];
+            double temp = denom != 0.0 ? N[r] / denom : 0.0;
+            N[r] = saved + right[r + 1] * temp;
+            saved = left[j - r] * temp;
+        }
+        N[j] = saved;
+    }
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_q (three-term recurrence).
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(q, 0.0);
+    w.assign(q, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (q + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (q + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= q; ++j) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = q * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        // refresh the derivative at the converged node
+        {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= q; ++j) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p2) / j;
+            }
+            dp = q * (z * p0 - p1) / (z * z - 1.0);
+        }
+        x[i] = -z;
+        x[q - 1 - i] = z;
+        w[i] = w[q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// G[i][j] += weight * Na[i] * Nb[j] over the non-zero functions of two spaces at x.
+struct Space {
+    std::vector<double> t;
+    int p;
+    int n;
+};
+
+Space make_space(int p, int ne) {
+    Space s;
+    s.t = open_knots(p, ne);
+    s.p = p;
+    s.n = ne + p;
+    return s;
+}
+
+// int_0^1 Ba_i Bb_j over the union of the breakpoints of both spaces, q Gauss points each.
+std::vector<double> cross_mass(const Space& a, const Space& b, int q) {
+    std::vector<double> br(a.t);
+    br.insert(br.end(), b.t.begin(), b.t.end());
+    std::sort(br.begin(), br.end());
+    br.erase(std::unique(br.begin(), br.end()), br.end());
+    std::vector<double> gx, gw;
+    gauss_legendre(q, gx, gw);
+    std::vector<double> G(size_t(a.n) * b.n, 0.0);
+    std::vector<double> Na(a.p + 1), Nb(b.p + 1);
+    for (size_t e = 0; e + 1 < br.size(); ++e) {
+        double x0 = br[e], x1 = br[e + 1], h = x1 - x0;
+        double mid = 0.5 * (x0 + x1);
+        int sa = find_span(a.t, a.p, mid), sb = find_span(b.t, b.p, mid);
+        for (int g = 0; g < q; ++g) {
+            double x = mid + 0.5 * h * gx[g], wt = 0.5 * h * gw[g];
+            nonzero_basis(a.t, a.p, sa, x, Na.data());
+            nonzero_basis(b.t, b.p, sb, x, Nb.data());
+            for (int i = 0; i <= a.p; ++i)
+                for (int j = 0; j <= b.p; ++j)
+                    G[size_t(sa - a.p + i) * b.n + (sb - b.p + j)] += wt * Na[i] * Nb[j];
+        }
+    }
+    return G;
+}
+
+// In-place inverse of an n x n row-major matrix by Gauss-Jordan with partial pivoting.
+bool invert(std::vector<double>& A, int n) {
+    std::vector<double> I(size_t(n) * n, 0.0);
+    for (int i = 0; i < n; ++i) I[size_t(i) * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[size_t(r) * n + c]) > std::fabs(A[size_t(piv) * n + c])) piv = r;
+        if (A[size_t(piv) * n + c] == 0.0) return false;
+        if (piv != c)
+            for (int j = 0; j < n; ++j) {
+                std::swap(A[size_t(c) * n + j], A[size_t(piv) * n + j]);
+                std::swap(I[size_t(c) * n + j], I[size_t(piv) * n + j]);
+            }
+        double d = 1.0 / A[size_t(c) * n + c];
+        for (int j = 0; j < n; ++j) {
+            A[size_t(c) * n + j] *= d;
+            I[size_t(c) * n + j] *= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = A[size_t(r) * n + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                A[size_t(r) * n + j] -= f * A[size_t(c) * n + j];
+                I[size_t(r) * n + j] -= f * I[size_t(c) * n + j];
+            }
+        }
+    }
+    A.swap(I);
+    return true;
+}
+
+}  // namespace
+
+kl_status build_direction(int p, int ne, int pt, int net, Direction* out) {
+    if (p < 1 || ne < 1 || pt < 1 || net < 1) return fail(KL_ERR_INVALID_ARG, "degrees and element counts must be >= 1");
+    if (ne + p > 4096 || net + pt > 4096) return fail(KL_ERR_INVALID_ARG, "more than 4096 functions in one direction");
+    Direction& d = *out;
+    d.p = p; d.ne = ne; d.pt = pt; d.net = net;
+    Space trial = make_space(p, ne), interp = make_space(pt, net);
+    d.n = trial.n;
+    d.nt = interp.n;
+    const int n = d.n, nt = d.nt;
+
+    // Greville abscissae of the interpolation space
+    d.xi.assign(nt, 0.0);
+    for (int i = 0; i < nt; ++i) {
+        double s = 0.0;
+        for (int r = 1; r <= pt; ++r) s += interp.t[i + r];
+        d.xi[i] = s / pt;
+    }
+    // Z_k (p+1 Gauss points per element) and its Cholesky factor
+    std::vector<double> Z = cross_mass(trial, trial, p + 1);
+    std::vector<double> Lk(size_t(n) * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double s = Z[size_t(j) * n + j];
+        for (int r = 0; r < j; ++r) s -= Lk[size_t(j) * n + r] * Lk[size_t(j) * n + r];
+        if (!(s > 0.0)) return fail(KL_ERR_NUMERIC, "univariate mass matrix is not positive definite");
+        double ljj = std::sqrt(s);
+        Lk[size_t(j) * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = Z[size_t(i) * n + j];
+            for (int r = 0; r < j; ++r) t -= Lk[size_t(i) * n + r] * Lk[size_t(j) * n + r];
+            Lk[size_t(i) * n + j] = t / ljj;
+        }
+    }
+    // L_k^{-1} by forward substitution on the identity
+    d.Linv.assign(size_t(n) * n, 0.0);
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < n; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int r = 0; r < i; ++r) s -= Lk[size_t(i) * n + r] * d.Linv[size_t(r) * n + c];
+            d.Linv[size_t(i) * n + c] = s / Lk[size_t(i) * n + i];
+        }
+    }
+    // M_k = int B~_i B_j (nt x n), exact for degree p + pt
+    std::vector<double> M = cross_mass(interp, trial, (p + pt) / 2 + 1);
+    // B~_k collocation (nt x nt) and its inverse
+    std::vector<double> Bt(size_t(nt) * nt, 0.0), Nv(pt + 1);
+    for (int i = 0; i < nt; ++i) {
+        int s = find_span(interp.t, pt, d.xi[i]);
+        nonzero_basis(interp.t, pt, s, d.xi[i], Nv.data());
+        for (int r = 0; r <= pt; ++r) Bt[size_t(i) * nt + (s - pt + r)] = Nv[r];
+    }
+    if (!invert(Bt, nt)) return fail(KL_ERR_NUMERIC, "collocation matrix is singular");
+    // X1 = M_k L_k^{-T}  (nt x n):  X1[i][j] = sum_r M[i][r] Linv[j][r]
+    std::vector<double> X1(size_t(nt) * n, 0.0);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int r = 0; r <= j; ++r) s += M[size_t(i) * n + r] * d.Linv[size_t(j) * n + r];
+            X1[size_t(i) * n + j] = s;
+        }
+    // C_k = B~^{-T} X1:  C[i][j] = sum_r Binv[r][i] X1[r][j]
+    d.C.assign(size_t(nt) * n, 0.0);
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int r = 0; r < nt; ++r) s += Bt[size_t(r) * nt + i] * X1[size_t(r) * n + j];
+            d.C[size_t(i) * n + j] = s;
+        }
+    return KL_OK;
+}
+
+}  // namespace kl

@@ -1,0 +1,131 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Element-by-element comparisons on seeded synthetic inputs at sizes the oracle finishes in
+seconds, spanning several 128/256-point tiles and a ragged tail; the float64 bar is the
+matvec relative error 1e-12 (max abs error / max abs value), the float32 bar 2e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import ibq
+from paper_2011_13861_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 2e-5
+
+CASES = [
+    # dim, p, ne, kernel, L, pt, net, lo, hi
+    (1, 2, 300, "exp", 0.3, None, None, None, None),
+    (2, [2, 3], [23, 17], "gauss", 0.4, None, None, [0.0, -1.0], [2.0, 0.5]),
+    (3, 2, [9, 10, 11], "exp", 0.5, None, None, None, None),
+    (3, [2, 2, 3], [6, 5, 7], "gauss", 0.3, [3, 2, 3], [8, 7, 9], None, None),
+    (2, 2, [20, 20], "exp_sep", 1.0, None, None, None, None),
+    (3, 2, [4, 5, 3], "poly", 2, None, None, [0.0, 0.0, 0.0], [1.5, 1.0, 2.0]),
+]
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def make(kl, case):
+    dim, p, ne, kern, L, pt, net, lo, hi = case
+    P = ibq.Problem(dim, p, ne, kernel=kern, L=L, pt=pt, net=net, lo=lo, hi=hi, sigma=1.3)
+    G = kl.KLProblem(dim, p, ne, kernel=kern, L=L, pt=pt, net=net, lo=lo, hi=hi, sigma=1.3)
+    return P, G
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dd-%s" % (c[0], c[3]))
+def test_setup_factors_and_points(kl, case):
+    P, G = make(kl, case)
+    assert (G.N, G.Nt) == (P.N, P.Nt)
+    for k, d in enumerate(P.dirs):
+        # C_k = B~_k^{-T} M_k L_k^{-T} composed from the oracle's univariate matrices
+        ref = np.linalg.solve(d.Bt.T, d.M @ np.linalg.inv(d.L).T)
+        assert rel(G.factor(k), ref) < 1e-13
+    X, J = G.points()
+    Xo, Jo = P.points_and_J()
+    assert np.abs(X - Xo).max() < 1e-15 * max(1.0, np.abs(Xo).max())
+    assert rel(J, Jo) < 1e-15
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dd-%s" % (c[0], c[3]))
+def test_stagewise_parity_fp64(kl, case):
+    import torch
+    P, G = make(kl, case)
+    v = inputs.random_block(P.N, 3, seed=11)
+    vd = torch.from_numpy(v.T.copy()).cuda()
+    u = G.forward(vd).cpu().numpy().T
+    assert rel(u, P.forward(v)) < 1e-13                                    # stages 1-4
+    X, _ = P.points_and_J()
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda()).cpu().numpy().T
+    assert rel(z, P.stage5(X, u)) < FP64_TOL                               # stage 5
+    y = G.backward(torch.from_numpy(z.T.copy()).cuda()).cpu().numpy().T
+    assert rel(y, P.backward(z)) < 1e-13                                   # stages 6-9
+    yf = G.apply(vd).cpu().numpy().T
+    Ap = P.dense_operator()
+    assert rel(yf, Ap @ v) < FP64_TOL                                      # all nine stages
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=lambda c: "%dd-%s" % (c[0], c[3]))
+def test_apply_fp32(kl, case):
+    import torch
+    P, G = make(kl, case)
+    v = inputs.random_block(P.N, 5, seed=12)
+    y = G.apply(torch.from_numpy(v.T.copy()).cuda(), precision=kl.KL_P_FP32).cpu().numpy().T
+    assert rel(y, P.dense_operator() @ v) < FP32_TOL
+    X, _ = P.points_and_J()
+    u = P.forward(v)
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=kl.KL_P_FP32).cpu().numpy().T
+    assert rel(z, P.stage5(X, u)) < FP32_TOL
+
+
+@pytest.mark.parametrize("nvec", [1, 2, 7, 16, 17, 33])
+def test_block_widths(kl, nvec):
+    """Vector groups of the stage-5 kernels (16 in float64, 32 in float32) and their tails."""
+    import torch
+    P, G = make(kl, CASES[2])
+    v = inputs.random_block(P.N, nvec, seed=nvec)
+    vd = torch.from_numpy(v.T.copy()).cuda()
+    ref = P.dense_operator() @ v
+    assert rel(G.apply(vd).cpu().numpy().T, ref) < FP64_TOL
+    assert rel(G.apply(vd, precision=kl.KL_P_FP32).cpu().numpy().T, ref) < FP32_TOL
+
+
+def test_deterministic(kl):
+    import torch
+    _, G = make(kl, CASES[2])
+    v = torch.from_numpy(inputs.random_block(G.N, 4, seed=5).T.copy()).cuda()
+    a = G.apply(v)
+    b = G.apply(v)
+    assert torch.equal(a, b)
+
+
+def test_invalid_arguments(kl):
+    import torch
+    with pytest.raises(kl.KLError):
+        kl.KLProblem(3, 2, 4, kernel="exp", L=-1.0)
+    with pytest.raises(kl.KLError):
+        kl.KLProblem(4, 2, 4)
+    with pytest.raises(kl.KLError):
+        kl.KLProblem(2, 0, 4)
+    _, G = make(kl, CASES[0])
+    with pytest.raises(kl.KLError):
+        G.eigs(0)
+    # an empty block is a no-op
+    e = torch.empty((0, G.N), dtype=torch.float64, device="cuda")
+    assert G.apply(e).shape == (0, G.N)
+
+
+def test_to_bspline(kl):
+    """v = L^{-T} v': the B-spline coefficients satisfy v^T Z v = v'^T v' (Sec. 4.1)."""
+    import torch
+    P, G = make(kl, CASES[1])
+    vp = inputs.random_block(P.N, 2, seed=3)
+    v = G.to_bspline(torch.from_numpy(vp.T.copy()).cuda()).cpu().numpy().T
+    Z = P.kron("Z")
+    assert np.abs(v.T @ Z @ v - vp.T @ vp).max() < 1e-12 * np.abs(vp.T @ vp).max()
