@@ -1,0 +1,44 @@
+"""Launches the stage-5 kernel product alone, for kernel profiling (ncu) and timing.
+
+  python -m paper_2011_13861_gb300.profile --workload cube-p2-32^3-exp-L0.5 --precision fp64 --nvec 1 --reps 3
+
+Builds the handle, runs stages 1-4 once to obtain u, then calls kl_covmv `reps` times on the
+current stream and prints the CUDA-event time per call.
+"""
+import argparse
+import json
+
+import torch
+
+import paper_2011_13861_gb300 as kl
+from paper_2011_13861_gb300 import inputs
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="cube-p2-32^3-exp-L0.5")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--nvec", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    w = inputs.WORKLOADS[a.workload]
+    G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32}[a.precision]
+    v = torch.from_numpy(inputs.random_block(G.N, a.nvec, seed=1).T.copy()).cuda()
+    u = G.forward(v).reshape(a.nvec, G.Nt).contiguous()
+    G.covmv(u, precision=prec)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.covmv(u, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    print(json.dumps({"workload": a.workload, "precision": a.precision, "nvec": a.nvec, "Ntilde": G.Nt,
+                      "ms": times, "pairs_per_s": G.Nt * G.Nt / (min(times) * 1e-3)}))
+
+
+if __name__ == "__main__":
+    main()
