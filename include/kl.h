@@ -91,8 +91,12 @@ typedef struct {
  *   KL_P_FP64  kernel, distance and accumulation in float64 (matvec rel. error ~1e-14).
  *   KL_P_FP32  kernel and distance in float32 (MUFU ex2 / rsqrt), float32 partial sums
  *              over column chunks combined in float64; contractions in float32.
- *              Relative error ~1e-6. */
-typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1 } kl_precision;
+ *              Relative error ~1e-6.
+ *   KL_P_DF64  kernel, distance and accumulation in double-float arithmetic (pairs of
+ *              float32, ~48 significant bits) on the float32 pipe: float64-level results
+ *              (matvec rel. error ~1e-14) at several times the float64 pipe's throughput on
+ *              GB300; contractions in float64. */
+typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1, KL_P_DF64 = 2 } kl_precision;
 
 /* Build the univariate factors, the mapped Greville grid and J on the host in
  * float64 (Sec. 3.5, 4.1-4.3), upload them, and return a handle.
@@ -156,7 +160,11 @@ typedef struct {
     uint64_t seed;
     const double* start_dev;
     double tol_low;         /* method 1: switch-over residual (0 = 1e-5) */
-    int verify;             /* 1 = finish with an explicit float64 residual A~'y - theta y */
+    int verify;             /* 1 = finish with an explicit residual A~'y - theta y applied in
+                             * `precision`; 2 = applied with the float64 kernel; 0 = report the
+                             * Lanczos estimates */
+    int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default) or KL_P_DF64;
+                             * method 0: every application, method 1: the polish */
 } kl_eig_opts;
 
 typedef struct {
@@ -169,9 +177,10 @@ typedef struct {
     double ms_total;        /* wall time of the call */
     double ms_fp32_phase;   /* method 1: time spent before the float64 polish */
     /* stage-5 launches (kernel product + split combine) timed with CUDA events on `stream` */
-    int stage5_calls_fp64, stage5_calls_fp32;
-    double ms_stage5_fp64, ms_stage5_fp32;
-    double pairs_fp64, pairs_fp32;  /* kernel evaluations performed (Ntilde^2 per launch group) */
+    int stage5_calls_fp64, stage5_calls_fp32, stage5_calls_df64;
+    double ms_stage5_fp64, ms_stage5_fp32, ms_stage5_df64;
+    double pairs_fp64, pairs_fp32, pairs_df64;  /* kernel evaluations (Ntilde^2 per launch group) */
+    int applies_df64;       /* operator applications counted per vector in KL_P_DF64 */
 } kl_eig_info;
 
 /* The k (<= 64) largest eigenvalues of A~' (descending) to relative residual tol.

@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 KL_GEOM_BOX = 0
 KL_K_EXP, KL_K_GAUSS, KL_K_EXP_SEPARABLE, KL_K_POLY_TEST = 0, 1, 2, 3
-KL_P_FP64, KL_P_FP32 = 0, 1
+KL_P_FP64, KL_P_FP32, KL_P_DF64 = 0, 1, 2
 KERNEL_KINDS = {"exp": KL_K_EXP, "gauss": KL_K_GAUSS, "exp_sep": KL_K_EXP_SEPARABLE, "poly": KL_K_POLY_TEST}
 STATUS = {0: "KL_OK", 1: "KL_ERR_INVALID_ARG", 2: "KL_ERR_CUDA", 3: "KL_ERR_OOM",
           4: "KL_ERR_NOT_CONVERGED", 5: "KL_ERR_TIMEOUT", 6: "KL_ERR_NUMERIC"}
@@ -33,7 +33,7 @@ class KLKernel(ctypes.Structure):
 class KLEigOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("block", ctypes.c_int), ("ncv", ctypes.c_int),
                 ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("start_dev", _vp),
-                ("tol_low", ctypes.c_double), ("verify", ctypes.c_int)]
+                ("tol_low", ctypes.c_double), ("verify", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class KLEigInfo(ctypes.Structure):
@@ -41,8 +41,11 @@ class KLEigInfo(ctypes.Structure):
                 ("restarts", ctypes.c_int), ("converged", ctypes.c_int), ("resid", ctypes.c_double * 64),
                 ("ms_total", ctypes.c_double), ("ms_fp32_phase", ctypes.c_double),
                 ("stage5_calls_fp64", ctypes.c_int), ("stage5_calls_fp32", ctypes.c_int),
+                ("stage5_calls_df64", ctypes.c_int),
                 ("ms_stage5_fp64", ctypes.c_double), ("ms_stage5_fp32", ctypes.c_double),
-                ("pairs_fp64", ctypes.c_double), ("pairs_fp32", ctypes.c_double)]
+                ("ms_stage5_df64", ctypes.c_double),
+                ("pairs_fp64", ctypes.c_double), ("pairs_fp32", ctypes.c_double), ("pairs_df64", ctypes.c_double),
+                ("applies_df64", ctypes.c_int)]
 
 
 SIGNATURES = {
@@ -233,12 +236,13 @@ class KLProblem:
         return X[:, :self.dim].copy(), J
 
     def eigs(self, k, tol=1e-8, method=0, block=1, ncv=0, maxiter=0, seed=1, start=None, tol_low=0.0,
-             verify=True, want_vectors=True, stream=None, raise_on_nonconv=True):
+             verify=True, want_vectors=True, stream=None, raise_on_nonconv=True, precision=KL_P_FP64):
         """The k largest eigenpairs (descending).  Returns (evals numpy, evecs (k, N) tensor or None, info dict)."""
         import numpy as np
         import torch
         opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1),
-                         _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0)
+                         _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0,
+                         int(precision))
         ev = np.zeros(k)
         vecs = None
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -254,5 +258,7 @@ class KLProblem:
              "ms_total": info.ms_total, "ms_fp32_phase": info.ms_fp32_phase, "status": st,
              "stage5_calls_fp64": info.stage5_calls_fp64, "stage5_calls_fp32": info.stage5_calls_fp32,
              "ms_stage5_fp64": info.ms_stage5_fp64, "ms_stage5_fp32": info.ms_stage5_fp32,
-             "pairs_fp64": info.pairs_fp64, "pairs_fp32": info.pairs_fp32}
+             "pairs_fp64": info.pairs_fp64, "pairs_fp32": info.pairs_fp32,
+             "stage5_calls_df64": info.stage5_calls_df64, "ms_stage5_df64": info.ms_stage5_df64,
+             "pairs_df64": info.pairs_df64, "applies_df64": info.applies_df64}
         return ev, vecs, d

@@ -85,7 +85,11 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32) {
         KL_TRY(ensure(h->w_f32b, size_t(ld) * nvec * sizeof(float)));
     }
     const int s64 = covmv_splits(h->Nt, nvec, false), s32 = covmv_splits(h->Nt, nvec, true);
-    const size_t part = size_t(h->Nt) * (size_t(s64) * 16 > size_t(s32) * 32 ? size_t(s64) * 16 : size_t(s32) * 32);
+    const int sdf = covmv_df_splits(h->Nt);
+    size_t groups = size_t(s64) * 16;
+    if (size_t(s32) * 32 > groups) groups = size_t(s32) * 32;
+    if (size_t(sdf) * 32 > groups) groups = size_t(sdf) * 32;
+    const size_t part = size_t(h->Nt) * groups;
     KL_TRY(ensure(h->w_part, part * sizeof(double)));
     return KL_OK;
 }
@@ -99,6 +103,8 @@ CovParams cov_params(kl_handle h) {
     cp.P64 = h->dP;
     cp.P32 = h->fP;
     cp.tab = h->dTab;
+    cp.Pdf = h->dfP;
+    cp.tabdf = h->dfTab;
     return cp;
 }
 
@@ -202,6 +208,9 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
     if (precision == KL_P_FP64) {
         e = launch_covmv64(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
                            covmv_splits(h->Nt, nvec, false), s);
+    } else if (precision == KL_P_DF64) {
+        e = launch_covmv_df(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
+                            covmv_df_splits(h->Nt), s);
     } else {
         float* uf = static_cast<float*>(h->w_f32a.ptr);
         const int64_t ld = stride_of(h);
@@ -233,7 +242,7 @@ kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, in
 
 // Stage-5 event timing: while kl_eigs runs, every stage-5 launch group is bracketed by a
 // pair of CUDA events on the launching stream; the pairs are read once the solve is done.
-static kl_status prof_begin(kl_handle h, bool fp64, int nvec, cudaStream_t s, int* slot) {
+static kl_status prof_begin(kl_handle h, int kind, int nvec, cudaStream_t s, int* slot) {
     *slot = -1;
     if (!h->prof_on) return KL_OK;
     const int need = int(h->prof_rec.size()) * 2 + 2;
@@ -243,7 +252,7 @@ static kl_status prof_begin(kl_handle h, bool fp64, int nvec, cudaStream_t s, in
         h->prof_ev.push_back(ev);
     }
     *slot = int(h->prof_rec.size()) * 2;
-    h->prof_rec.push_back({*slot, fp64, nvec});
+    h->prof_rec.push_back({*slot, kind, nvec});
     KL_CUDA(cudaEventRecord(h->prof_ev[*slot], s));
     return KL_OK;
 }
@@ -270,9 +279,12 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
         KL_TRY(forward_generic<double, double>(h, v, ldv, u, ld, nvec, h->dCt, h->dJ, A, B, s));
         double* z = (u == A) ? B : A;
         int slot;
-        KL_TRY(prof_begin(h, true, nvec, s, &slot));
-        cudaError_t e = launch_covmv64(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                       covmv_splits(h->Nt, nvec, false), s);
+        const bool df = (precision == KL_P_DF64);
+        KL_TRY(prof_begin(h, df ? KL_P_DF64 : KL_P_FP64, nvec, s, &slot));
+        cudaError_t e = df ? launch_covmv_df(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                                             covmv_df_splits(h->Nt), s)
+                           : launch_covmv64(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                                            covmv_splits(h->Nt, nvec, false), s);
         if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp64)");
         KL_TRY(prof_end(h, slot, s));
         double* other = (z == A) ? B : A;
@@ -285,7 +297,7 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
     KL_TRY(forward_generic<float, float>(h, v, ldv, u, ld, nvec, h->fCt, h->fJ, FA, FB, s));
     double* z = A;
     int slot;
-    KL_TRY(prof_begin(h, false, nvec, s, &slot));
+    KL_TRY(prof_begin(h, KL_P_FP32, nvec, s, &slot));
     cudaError_t e = launch_covmv32(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
                                    covmv_splits(h->Nt, nvec, true), s);
     if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp32)");
@@ -386,6 +398,20 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
             P[size_t(c) * Nt + i] = x * s64;
             Pf[size_t(c) * Nt + i] = float(x * s32);
         }
+    std::vector<float> Pdf(size_t(Nt) * 6);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t i = 0; i < Nt; ++i) {
+            const double x = P[size_t(c) * Nt + i];
+            const float xh = float(x);
+            Pdf[size_t(c) * Nt + i] = xh;
+            Pdf[size_t(3 + c) * Nt + i] = float(x - double(xh));
+        }
+    std::vector<float> tabdf(128);
+    for (int j = 0; j < 64; ++j) {
+        const double t = exp2(-double(j) / 64.0);
+        tabdf[j] = float(t);
+        tabdf[64 + j] = float(t - double(tabdf[j]));
+    }
     std::vector<double> J(size_t(Nt), h->Jval);
     std::vector<float> Jf(size_t(Nt), float(h->Jval));
     std::vector<double> tab(64);
@@ -400,6 +426,8 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     chk(upload(&h->dJ, J.data(), J.size()));
     chk(upload(&h->fJ, Jf.data(), Jf.size()));
     chk(upload(&h->dTab, tab.data(), tab.size()));
+    chk(upload(&h->dfP, Pdf.data(), Pdf.size()));
+    chk(upload(&h->dfTab, tabdf.data(), tabdf.size()));
     for (int k = 0; k < d && st == KL_OK; ++k) {
         const Direction& D = h->dir[k];
         const int n = D.n, nt = D.nt;
@@ -450,7 +478,7 @@ kl_status kl_dims(kl_handle h, int* n, int* ntilde) {
 kl_status kl_apply_prec(kl_handle h, int precision, const double* v_dev, double* y_dev, int nvec, int64_t ldv,
                         void* stream) {
     KL_TRY(check_block(h, v_dev, y_dev, nvec, ldv, h ? h->N : 0, ldv, h ? h->N : 0));
-    if (precision != KL_P_FP64 && precision != KL_P_FP32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    if (precision < KL_P_FP64 || precision > KL_P_DF64) return fail(KL_ERR_INVALID_ARG, "unknown precision");
     return apply_impl(h, precision, v_dev, ldv, y_dev, ldv, nvec, static_cast<cudaStream_t>(stream));
 }
 
@@ -468,7 +496,7 @@ kl_status kl_forward(kl_handle h, const double* v_dev, int64_t ldv, double* u_de
 kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev, int64_t ldz,
                    int nvec, void* stream) {
     KL_TRY(check_block(h, u_dev, z_dev, nvec, ldu, h ? h->Nt : 0, ldz, h ? h->Nt : 0));
-    if (precision != KL_P_FP64 && precision != KL_P_FP32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    if (precision < KL_P_FP64 || precision > KL_P_DF64) return fail(KL_ERR_INVALID_ARG, "unknown precision");
     if (nvec == 0) return KL_OK;
     return covmv_impl(h, precision, u_dev, ldu, z_dev, ldz, nvec, false, static_cast<cudaStream_t>(stream));
 }
@@ -547,6 +575,8 @@ void kl_destroy(kl_handle h) {
     if (h->dJ) cudaFree(h->dJ);
     if (h->fJ) cudaFree(h->fJ);
     if (h->dTab) cudaFree(h->dTab);
+    if (h->dfP) cudaFree(h->dfP);
+    if (h->dfTab) cudaFree(h->dfTab);
     release(h->w_a);
     release(h->w_b);
     release(h->w_f32a);

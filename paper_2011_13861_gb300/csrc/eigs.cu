@@ -56,7 +56,7 @@ struct Eig {
     int* Sweeps() { return static_cast<int*>(bSweeps.ptr); }
     int maxparts = 0;
     // statistics
-    int applies = 0, applies64 = 0, block_applies = 0;
+    int applies = 0, applies64 = 0, appliesdf = 0, block_applies = 0;
     uint64_t rng_offset = 0;
     uint64_t seed = 1;
 
@@ -96,6 +96,7 @@ struct Eig {
         KL_TRY(apply_impl(h, prec, Q, N, Wout, N, b, s));
         applies += b;
         if (prec == KL_P_FP64) applies64 += b;
+        if (prec == KL_P_DF64) appliesdf += b;
         block_applies += 1;
         return KL_OK;
     }
@@ -298,7 +299,10 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.start_dev = nullptr;
     o.tol_low = 0.0;
     o.verify = 1;
+    o.precision = KL_P_FP64;
     if (opts_in) o = *opts_in;
+    if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64)
+        return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64 or KL_P_DF64");
     const int b = std::max(1, o.block);
     if (o.method != 0 && o.method != 1) return fail(KL_ERR_INVALID_ARG, "method must be 0 or 1");
     if (b > 64) return fail(KL_ERR_INVALID_ARG, "block size above 64");
@@ -354,7 +358,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     bool conv = false;
     double ms32 = 0.0;
     if (o.method == 0) {
-        Phase P{KL_P_FP64, b, m, keep, tol, false, maxrestart, k};
+        Phase P{o.precision, b, m, keep, tol, false, maxrestart, k};
         KL_TRY(run_phase(E, P, k, b, &restarts, theta, est, &conv));
     } else {
         const double tl = o.tol_low > 0.0 ? o.tol_low : 1e-5;
@@ -365,7 +369,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
         // they form the first, wide block of a float64 block Lanczos run.
-        Phase P2{KL_P_FP64, pb, pol_m, pb, tol, true, maxrestart, k};
+        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, k};
         // the active block is V[:, 0:pb]; T is rebuilt by the first expansion
         e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
@@ -378,7 +382,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     for (int i = 0; i < k; ++i) resid[i] = est[i] / std::max(fabs(theta[i]), 1e-300);
     if (o.verify) {
         // explicit float64 residuals ||A y - theta y|| / |theta|
-        KL_TRY(E.apply(KL_P_FP64, E.V(), E.Y(), k));
+        KL_TRY(E.apply(o.verify == 2 ? KL_P_FP64 : o.precision, E.V(), E.Y(), k));
         KL_CUDA(cudaMemcpyAsync(E.Theta(), theta.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
         e = launch_ritz_resid(E.Y(), E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
         if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
@@ -394,23 +398,28 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     if (info) {
         info->applies = E.applies;
         info->applies_fp64 = E.applies64;
+        info->applies_df64 = E.appliesdf;
         info->block_applies = E.block_applies;
         info->restarts = restarts;
         info->converged = nconv;
         for (int i = 0; i < 64; ++i) info->resid[i] = i < k ? resid[i] : 0.0;
         info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         info->ms_fp32_phase = ms32;
-        info->stage5_calls_fp64 = info->stage5_calls_fp32 = 0;
-        info->ms_stage5_fp64 = info->ms_stage5_fp32 = 0.0;
-        info->pairs_fp64 = info->pairs_fp32 = 0.0;
+        info->stage5_calls_fp64 = info->stage5_calls_fp32 = info->stage5_calls_df64 = 0;
+        info->ms_stage5_fp64 = info->ms_stage5_fp32 = info->ms_stage5_df64 = 0.0;
+        info->pairs_fp64 = info->pairs_fp32 = info->pairs_df64 = 0.0;
         const double pairs = double(h->Nt) * double(h->Nt);
         for (const auto& r : h->prof_rec) {
             float ms = 0.f;
             KL_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[r.ev], h->prof_ev[r.ev + 1]));
-            if (r.fp64) {
+            if (r.kind == KL_P_FP64) {
                 info->stage5_calls_fp64 += 1;
                 info->ms_stage5_fp64 += ms;
                 info->pairs_fp64 += pairs;
+            } else if (r.kind == KL_P_DF64) {
+                info->stage5_calls_df64 += 1;
+                info->ms_stage5_df64 += ms;
+                info->pairs_df64 += pairs;
             } else {
                 info->stage5_calls_fp32 += 1;
                 info->ms_stage5_fp32 += ms;

@@ -61,6 +61,8 @@ struct CovParams {
     const double* P64;     // 3 x ldp, coordinates (pre-scaled for EXP/GAUSS/EXP_SEPARABLE)
     const float* P32;      // 3 x ldp, float coordinates pre-scaled for base-2 exponentials
     const double* tab;     // 64-entry table 2^(j/64)
+    const float* Pdf;      // 6 x ldp: x, y, z heads then x, y, z tails (double-float coordinates)
+    const float* tabdf;    // 2^(-j/64), j = 0..63: 64 heads then 64 tails
 };
 
 // Stage 5: z[:, v] = scale2 * (J .) sum_l Gamma(x_k, x_l) u[:, v]; partial sums over column
@@ -72,6 +74,10 @@ cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int
                            int64_t ldz, double scale2, const double* J, double* part, int splits,
                            cudaStream_t s);
 int covmv_splits(int64_t Nt, int nvec, bool fp32);
+cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z,
+                            int64_t ldz, double scale2, const double* J, double* part, int splits,
+                            cudaStream_t s);
+int covmv_df_splits(int64_t Nt);
 
 // dense block linear algebra (linalg.cu)
 cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
@@ -135,12 +141,14 @@ struct kl_handle_s {
     double* dJ = nullptr;     // Nt
     float* fJ = nullptr;      // Nt
     double* dTab = nullptr;   // 64
+    float* dfP = nullptr;     // 6 x Nt double-float coordinates (pre-scaled like dP)
+    float* dfTab = nullptr;   // 128: double-float 2^(-j/64)
     // workspace
     kl::DevBuf w_a, w_b, w_f32a, w_f32b, w_part;
     // stage-5 event timing (enabled by kl_eigs while it runs)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;       // pool, two per record
-    struct ProfRec { int ev; bool fp64; int nvec; };
+    struct ProfRec { int ev; int kind; int nvec; };   // kind: kl_precision
     std::vector<ProfRec> prof_rec;
 };
 

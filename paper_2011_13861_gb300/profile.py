@@ -17,13 +17,13 @@ from paper_2011_13861_gb300 import inputs
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cube-p2-32^3-exp-L0.5")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
     ap.add_argument("--nvec", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
-    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32}[a.precision]
+    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32, "df64": kl.KL_P_DF64}[a.precision]
     v = torch.from_numpy(inputs.random_block(G.N, a.nvec, seed=1).T.copy()).cuda()
     u = G.forward(v).reshape(a.nvec, G.Nt).contiguous()
     G.covmv(u, precision=prec)

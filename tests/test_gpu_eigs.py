@@ -45,13 +45,13 @@ def max_sin_angle(A, B):
     return float(np.sqrt(max(0.0, 1.0 - s.min() ** 2)))
 
 
-def check(kl, name, k, method, block, eig_tol, vec_tol=1e-6, tol=1e-8):
+def check(kl, name, k, method, block, eig_tol, vec_tol=1e-6, tol=1e-8, precision=0):
     import torch
     P, lam, Vp = oracle_pairs(name, k)
     w = inputs.WORKLOADS[name]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     start = torch.from_numpy(inputs.random_block(G.N, block, seed=1).T.copy()).cuda()
-    ev, vec, info = G.eigs(k, tol, method=method, block=block, start=start)
+    ev, vec, info = G.eigs(k, tol, method=method, block=block, start=start, precision=precision)
     assert np.abs(ev - lam[:k]).max() / lam[0] < eig_tol, (ev, lam[:k])
     assert np.abs((ev - lam[:k]) / lam[:k]).max() < eig_tol * 10
     assert max(info["resid"]) <= tol
@@ -99,3 +99,11 @@ def test_single_vector_lanczos_on_the_cube(kl):
 
 def test_reduced_cube_gaussian_mixed(kl):
     check(kl, "cube-p3-16^3-gauss-L0.3", 20, method=1, block=16, eig_tol=1e-10)
+
+
+@pytest.mark.parametrize("method,block", [(0, 4), (1, 16)])
+def test_reduced_cube_double_float(kl, method, block):
+    """Every accurate-phase application in double-float arithmetic (KL_P_DF64); the final
+    residuals are still checked with the float64 operator."""
+    info = check(kl, "cube-p2-16^3-exp-L0.5", 20, method=method, block=block, eig_tol=1e-10, precision=2)
+    assert info["applies_df64"] > 0

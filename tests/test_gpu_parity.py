@@ -71,6 +71,21 @@ def test_stagewise_parity_fp64(kl, case):
     assert rel(yf, Ap @ v) < FP64_TOL                                      # all nine stages
 
 
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dd-%s" % (c[0], c[3]))
+def test_double_float_stage5_meets_fp64_tolerance(kl, case):
+    """KL_P_DF64 (double-float arithmetic on the float32 pipe) against the float64 oracle."""
+    import torch
+    P, G = make(kl, case)
+    v = inputs.random_block(P.N, 3, seed=13)
+    vd = torch.from_numpy(v.T.copy()).cuda()
+    X, _ = P.points_and_J()
+    u = P.forward(v)
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=kl.KL_P_DF64).cpu().numpy().T
+    assert rel(z, P.stage5(X, u)) < FP64_TOL
+    y = G.apply(vd, precision=kl.KL_P_DF64).cpu().numpy().T
+    assert rel(y, P.dense_operator() @ v) < FP64_TOL
+
+
 @pytest.mark.parametrize("case", CASES[:4], ids=lambda c: "%dd-%s" % (c[0], c[3]))
 def test_apply_fp32(kl, case):
     import torch
@@ -93,6 +108,7 @@ def test_block_widths(kl, nvec):
     vd = torch.from_numpy(v.T.copy()).cuda()
     ref = P.dense_operator() @ v
     assert rel(G.apply(vd).cpu().numpy().T, ref) < FP64_TOL
+    assert rel(G.apply(vd, precision=kl.KL_P_DF64).cpu().numpy().T, ref) < FP64_TOL
     assert rel(G.apply(vd, precision=kl.KL_P_FP32).cpu().numpy().T, ref) < FP32_TOL
 
 
