@@ -131,6 +131,24 @@ kl_status kl_forward(kl_handle h, const double* v_dev, int64_t ldv, double* u_de
 kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev,
                    int64_t ldz, int nvec, void* stream);
 
+/* kl_covmv without any device allocation (the paper has no counterpart: this is a deployment
+ * convenience).  For callers that cannot call cudaMalloc when they apply the operator -- code
+ * recorded while a stream is captured into a CUDA graph, where allocation is not allowed, or
+ * programs that allocate everything up front and forbid it later.  kl_covmv may grow the
+ * handle's workspace; this call instead keeps its split partial sums in a fixed 32 MiB
+ * file-scope device array that every GPU loading the library holds until exit.
+ *   - precision must be KL_P_FP64; u, z as for kl_covmv; the handle itself comes from
+ *     kl_create, which does allocate, so create it beforehand.
+ *   - Ntilde x min(nvec, 16) must not exceed 4 Mi (4,194,304) doubles, else KL_ERR_INVALID_ARG
+ *     with nothing launched.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - All calls share the array: launches that overlap on the GPU (other streams, other host
+ *     threads) race on it, so order them.  No part of it needs clearing between calls.
+ * Results agree with kl_covmv to rounding (the split count may differ). */
+kl_status kl_covmv_noalloc(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev,
+                           int64_t ldz, int nvec, void* stream);
+
 /* Stages 6-9 of Algorithm 1: y = L^{-1} M^T B~^{-1} (J . z)   (Ntilde x nvec -> N x nvec). */
 kl_status kl_backward(kl_handle h, const double* z_dev, int64_t ldz, double* y_dev, int64_t ldy,
                       int nvec, void* stream);

@@ -57,6 +57,7 @@ SIGNATURES = {
     "kl_apply_prec": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _c_int64, _vp]),
     "kl_forward": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
     "kl_covmv": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
+    "kl_covmv_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
     "kl_backward": (ctypes.c_int, [_vp, _vp, _c_int64, _vp, _c_int64, ctypes.c_int, _vp]),
     "kl_get_factor": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "kl_get_points": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -206,6 +207,14 @@ class KLProblem:
         _check(load().kl_covmv(self._h, int(precision), _ptr(ub), self.Nt, _ptr(z), self.Nt, ub.shape[0],
                                _stream(stream)))
         return z.reshape(u.shape)
+
+    def covmv_noalloc(self, u, out, stream=None):
+        """Stage 5 into the caller's `out` through kl_covmv_noalloc (no device allocation)."""
+        ub = self._block(u, self.Nt)
+        zb = self._block(out, self.Nt)
+        _check(load().kl_covmv_noalloc(self._h, KL_P_FP64, _ptr(ub), self.Nt, _ptr(zb), self.Nt, ub.shape[0],
+                                       _stream(stream)))
+        return out
 
     def backward(self, z, stream=None):
         import torch
