@@ -54,6 +54,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -225,9 +236,7 @@ def main():
     ms_mixed = statistics.mean(t_mixed)
     ms_pdf = statistics.mean(t_pdf)
     if world > 1:
-        tt = torch.tensor([ms_plain, ms_mixed, ms_pdf], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_plain, ms_mixed, ms_pdf = tt.tolist()
+        ms_plain, ms_mixed, ms_pdf = max_over_ranks([ms_plain, ms_mixed, ms_pdf], device="cuda")
     # untimed: float64-operator residuals of the chosen form's eigenvectors
     ev_chk, vec_chk, _ = solve_mixed()
     ych = G.apply(vec_chk)

@@ -178,9 +178,11 @@ typedef struct {
     uint64_t seed;
     const double* start_dev;
     double tol_low;         /* method 1: switch-over residual (0 = 1e-5) */
-    int verify;             /* 1 = finish with an explicit residual A~'y - theta y applied in
-                             * `precision`; 2 = applied with the float64 kernel; 0 = report the
-                             * Lanczos estimates */
+    int verify;             /* final residuals ||A~'y - theta y|| / |theta|:
+                             * 1 = from the operator products of the basis, carried through every
+                             *     restart (A~'Y = (A~'V) S; no extra application);
+                             * 2 = from a fresh application with the float64 kernel;
+                             * 0 = the Lanczos estimates */
     int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default) or KL_P_DF64;
                              * method 0: every application, method 1: the polish */
 } kl_eig_opts;

@@ -89,7 +89,9 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32) {
     size_t groups = size_t(s64) * 16;
     if (size_t(s32) * 32 > groups) groups = size_t(s32) * 32;
     if (size_t(sdf) * 32 > groups) groups = size_t(sdf) * 32;
-    const size_t part = size_t(h->Nt) * groups;
+    size_t part = size_t(h->Nt) * groups;
+    const size_t dfp = covmv_df_part_doubles(h->Nt, nvec);
+    if (dfp > part) part = dfp;
     KL_TRY(ensure(h->w_part, part * sizeof(double)));
     return KL_OK;
 }
@@ -206,7 +208,7 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
     const double* J = withJ ? h->dJ : nullptr;
     cudaError_t e;
     if (precision == KL_P_FP64) {
-        e = launch_covmv64(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
+        e = launch_covmv64_sym(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
                            covmv_splits(h->Nt, nvec, false), s);
     } else if (precision == KL_P_DF64) {
         e = launch_covmv_df(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
@@ -283,7 +285,7 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
         KL_TRY(prof_begin(h, df ? KL_P_DF64 : KL_P_FP64, nvec, s, &slot));
         cudaError_t e = df ? launch_covmv_df(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
                                              covmv_df_splits(h->Nt), s)
-                           : launch_covmv64(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                           : launch_covmv64_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
                                             covmv_splits(h->Nt, nvec, false), s);
         if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp64)");
         KL_TRY(prof_end(h, slot, s));

@@ -57,7 +57,7 @@ __device__ __forceinline__ F2 kernel_df(const float* r, const float* c, int pm, 
 template <int KIND, int NV>
 __global__ void __launch_bounds__(kDfThreads)
 covmv_df_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, double* __restrict__ part,
-                int64_t cols_per_split) {
+                int64_t cols_per_split, int nv) {
     __shared__ float sp[6][kDfTile];
     __shared__ float2 su[kDfTile][NV];
     __shared__ float stab[128];
@@ -88,7 +88,7 @@ covmv_df_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, double*
             for (int k = 0; k < 6; ++k) sp[k][threadIdx.x] = cp.Pdf[k * cp.ldp + c];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const double u = U[v * ldu + c];
+                const double u = (v < nv) ? U[v * ldu + c] : 0.0;   // inactive lanes add 0
                 const float uh = __double2float_rn(u);
                 su[threadIdx.x][v] = make_float2(uh, __double2float_rn(u - double(uh)));
             }
@@ -127,7 +127,164 @@ covmv_df_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, double*
     if (valid) {
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            part[(int64_t(blockIdx.y) * NV + v) * Nt + row] = double(ah[v]) + double(al[v]);
+            if (v < nv) part[(int64_t(blockIdx.y) * nv + v) * Nt + row] = double(ah[v]) + double(al[v]);
+    }
+}
+
+// ---- symmetric tiling: Gamma(x_k, x_l) = Gamma(x_l, x_k), so each kernel value is evaluated once
+// for both products.  Points are cut into tiles of 256; CTA (I, J), I <= J, evaluates the
+// 256 x 256 block once.  Thread t owns row I*256+t.  For I < J the block is walked in 32-column
+// chunks in a rotated order: at step s lane l evaluates the pair (row l, column (l+s) mod 32) of
+// the chunk, adds g*u_col to its row accumulator and g*u_row to a travelling column accumulator
+// that is handed to lane l-1 after every step, so after 32 steps lane l holds the warp's sum
+// for column l.  The 8 warps' column sums are combined in shared memory.  Row sums go to partial
+// slot J, column sums to slot I, so every output row receives exactly one partial per tile
+// index; the diagonal block (I, I) is evaluated in full, row side only, into slot I.
+constexpr int kSymTile = 256;
+
+template <int KIND, int NV>
+__global__ void __launch_bounds__(kSymTile)
+covmv_df_sym_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, double* __restrict__ part,
+                    int nt_tiles, int nv) {
+    extern __shared__ float smem_sym[];
+    float* sc = smem_sym;                                   // [6][256] column coordinates
+    float2* su = reinterpret_cast<float2*>(smem_sym + 6 * kSymTile);   // [256][NV] column u
+    float2* cpart = su + kSymTile * NV;                     // [8 warps][32][NV] column partials
+    __shared__ float stab[128];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 128) stab[tid] = cp.tabdf[tid];
+
+    // triangular decode of the tile pair: b = J (J + 1) / 2 + I, I <= J
+    const int64_t bidx = blockIdx.x;
+    int J = int((sqrt(8.0 * double(bidx) + 1.0) - 1.0) * 0.5);
+    while (int64_t(J) * (J + 1) / 2 > bidx) --J;
+    while (int64_t(J + 1) * (J + 2) / 2 <= bidx) ++J;
+    const int I = int(bidx - int64_t(J) * (J + 1) / 2);
+    (void)nt_tiles;
+
+    const int64_t Nt = cp.Nt;
+    const int64_t row = int64_t(I) * kSymTile + tid;
+    const bool rvalid = row < Nt;
+    float rp[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) rp[k] = rvalid ? cp.Pdf[k * cp.ldp + row] : 0.f;
+    float2 ur[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double u = (rvalid && v < nv) ? U[v * ldu + row] : 0.0;
+        const float uh = __double2float_rn(u);
+        ur[v] = make_float2(uh, __double2float_rn(u - double(uh)));
+    }
+    // stage the column tile J
+    {
+        const int64_t c = int64_t(J) * kSymTile + tid;
+        const bool cvalid = c < Nt;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sc[k * kSymTile + tid] = cvalid ? cp.Pdf[k * cp.ldp + c] : 0.f;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double u = (cvalid && v < nv) ? U[v * ldu + c] : 0.0;
+            const float uh = __double2float_rn(u);
+            su[tid * NV + v] = make_float2(uh, __double2float_rn(u - double(uh)));
+        }
+    }
+    __syncthreads();
+
+    float ah[NV], al[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        ah[v] = 0.f;
+        al[v] = 0.f;
+    }
+    if (I == J) {
+#pragma unroll 1
+        for (int j = 0; j < kSymTile; ++j) {
+            float cpj[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cpj[k] = sc[k * kSymTile + j];
+            const F2 g = kernel_df<KIND>(rp, cpj, cp.poly_m, stab, stab + 64);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float2 u = su[j * NV + v];
+                const float ph = df::mul(g.h, u.x);
+                float pe = df::fma_(g.h, u.x, -ph);
+                pe = df::fma_(g.h, u.y, pe);
+                pe = df::fma_(g.l, u.x, pe);
+                const F2 s = df::two_sum(ah[v], ph);
+                ah[v] = s.h;
+                al[v] = df::add(al[v], df::add(s.l, pe));
+            }
+        }
+    } else {
+        const int64_t col0 = int64_t(J) * kSymTile;
+#pragma unroll 1
+        for (int q = 0; q < kSymTile / 32; ++q) {
+            float ch[NV], cl[NV];   // travelling column accumulator
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                ch[v] = 0.f;
+                cl[v] = 0.f;
+            }
+#pragma unroll 1
+            for (int s = 0; s < 32; ++s) {
+                const int j = q * 32 + ((lane + s) & 31);
+                float cpj[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) cpj[k] = sc[k * kSymTile + j];
+                const F2 g = kernel_df<KIND>(rp, cpj, cp.poly_m, stab, stab + 64);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    // row side: g * u_col
+                    const float2 u = su[j * NV + v];
+                    float ph = df::mul(g.h, u.x);
+                    float pe = df::fma_(g.h, u.x, -ph);
+                    pe = df::fma_(g.h, u.y, pe);
+                    pe = df::fma_(g.l, u.x, pe);
+                    F2 sm = df::two_sum(ah[v], ph);
+                    ah[v] = sm.h;
+                    al[v] = df::add(al[v], df::add(sm.l, pe));
+                    // column side: g * u_row
+                    ph = df::mul(g.h, ur[v].x);
+                    pe = df::fma_(g.h, ur[v].x, -ph);
+                    pe = df::fma_(g.h, ur[v].y, pe);
+                    pe = df::fma_(g.l, ur[v].x, pe);
+                    sm = df::two_sum(ch[v], ph);
+                    ch[v] = sm.h;
+                    cl[v] = df::add(cl[v], df::add(sm.l, pe));
+                    ch[v] = __shfl_sync(0xffffffffu, ch[v], (lane + 1) & 31);
+                    cl[v] = __shfl_sync(0xffffffffu, cl[v], (lane + 1) & 31);
+                }
+            }
+            // lane holds this warp's partial for column q*32 + lane
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const F2 r = df::fast_two_sum(ch[v], cl[v]);
+                cpart[(warp * 32 + lane) * NV + v] = make_float2(r.h, r.l);
+            }
+            __syncthreads();
+            for (int e = tid; e < 32 * NV; e += kSymTile) {
+                const int cl_ = e / NV, v = e - cl_ * NV;
+                double acc = 0.0;
+                for (int w = 0; w < kSymTile / 32; ++w) {
+                    const float2 p = cpart[(w * 32 + cl_) * NV + v];
+                    acc += double(p.x) + double(p.y);
+                }
+                const int64_t c = col0 + q * 32 + cl_;
+                if (c < Nt && v < nv) part[(int64_t(I) * nv + v) * Nt + c] = acc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const F2 r = df::fast_two_sum(ah[v], al[v]);
+                ah[v] = r.h;
+                al[v] = r.l;
+            }
+        }
+    }
+    if (rvalid) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            if (v < nv) part[(int64_t(J) * nv + v) * Nt + row] = double(ah[v]) + double(al[v]);
     }
 }
 
@@ -148,19 +305,50 @@ __global__ void covmv_df_reduce(const double* __restrict__ part, int splits, int
 
 template <int NV>
 cudaError_t dispatch_df(const CovParams& cp, const double* U, int64_t ldu, double* part, dim3 grid,
-                        int64_t cps, cudaStream_t s) {
+                        int64_t cps, int nv, cudaStream_t s) {
     switch (cp.kind) {
-        case KL_K_EXP: covmv_df_kernel<KL_K_EXP, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps); break;
-        case KL_K_GAUSS: covmv_df_kernel<KL_K_GAUSS, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps); break;
-        case KL_K_EXP_SEPARABLE: covmv_df_kernel<KL_K_EXP_SEPARABLE, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps); break;
-        default: covmv_df_kernel<KL_K_POLY_TEST, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps); break;
+        case KL_K_EXP: covmv_df_kernel<KL_K_EXP, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps, nv); break;
+        case KL_K_GAUSS: covmv_df_kernel<KL_K_GAUSS, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps, nv); break;
+        case KL_K_EXP_SEPARABLE: covmv_df_kernel<KL_K_EXP_SEPARABLE, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps, nv); break;
+        default: covmv_df_kernel<KL_K_POLY_TEST, NV><<<grid, kDfThreads, 0, s>>>(cp, U, ldu, part, cps, nv); break;
     }
     return cudaGetLastError();
 }
 
-int group_df(int left) { return left >= 32 ? 32 : left >= 16 ? 16 : left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1; }
+// instantiated block widths; a group of n active vectors runs in the smallest width >= n so
+// that the kernel value of a pair is evaluated once for the whole group
+int width_df(int n) {
+    static const int w[] = {1, 2, 4, 8, 12, 16, 20, 24, 32};
+    for (int x : w)
+        if (n <= x) return x;
+    return 32;
+}
+
+constexpr int kSymMaxNV = 8;   // widest block that takes the symmetric path
+
+template <int NV>
+cudaError_t launch_sym(const CovParams& cp, const double* U, int64_t ldu, double* part, unsigned pairs,
+                       int nt_tiles, int nv, cudaStream_t s) {
+    const size_t smem = (size_t(6) * kSymTile + 2 * size_t(kSymTile) * NV + 2 * size_t(kSymTile) * NV) * sizeof(float);
+    switch (cp.kind) {
+        case KL_K_EXP: covmv_df_sym_kernel<KL_K_EXP, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
+        case KL_K_GAUSS: covmv_df_sym_kernel<KL_K_GAUSS, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
+        case KL_K_EXP_SEPARABLE: covmv_df_sym_kernel<KL_K_EXP_SEPARABLE, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
+        default: covmv_df_sym_kernel<KL_K_POLY_TEST, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
+    }
+    return cudaGetLastError();
+}
 
 }  // namespace
+
+// partial-sum scratch (doubles) the double-float stage 5 needs for nvec vectors
+size_t covmv_df_part_doubles(int64_t Nt, int nvec) {
+    const int64_t nt_tiles = (Nt + kSymTile - 1) / kSymTile;
+    const int64_t g = nvec < kSymMaxNV ? nvec : kSymMaxNV;
+    const size_t sym = size_t(nt_tiles) * size_t(g) * size_t(Nt);
+    const size_t flat = size_t(covmv_df_splits(Nt)) * 32 * size_t(Nt);
+    return sym > flat ? sym : flat;
+}
 
 int covmv_df_splits(int64_t Nt) {
     const int64_t rowblocks = (Nt + kDfThreads - 1) / kDfThreads;
@@ -182,17 +370,42 @@ cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, i
     cps = (cps + kDfTile - 1) / kDfTile * kDfTile;
     const int used = int((Nt + cps - 1) / cps);
     dim3 grid(unsigned((Nt + kDfThreads - 1) / kDfThreads), unsigned(used));
+    const int nt_tiles = int((Nt + kSymTile - 1) / kSymTile);
     for (int v0 = 0; v0 < nvec;) {
-        const int g = group_df(nvec - v0);
+        const int g = (nvec - v0) < 32 ? (nvec - v0) : 32;   // active vectors in this launch
         cudaError_t e;
         const double* Ug = U + int64_t(v0) * ldu;
-        switch (g) {
-            case 32: e = dispatch_df<32>(cp, Ug, ldu, part, grid, cps, s); break;
-            case 16: e = dispatch_df<16>(cp, Ug, ldu, part, grid, cps, s); break;
-            case 8: e = dispatch_df<8>(cp, Ug, ldu, part, grid, cps, s); break;
-            case 4: e = dispatch_df<4>(cp, Ug, ldu, part, grid, cps, s); break;
-            case 2: e = dispatch_df<2>(cp, Ug, ldu, part, grid, cps, s); break;
-            default: e = dispatch_df<1>(cp, Ug, ldu, part, grid, cps, s); break;
+        if (g <= kSymMaxNV && nt_tiles >= 2) {
+            // narrow blocks: symmetric tiles halve the kernel evaluations
+            const int w = width_df(g);
+            const unsigned pairs = unsigned(int64_t(nt_tiles) * (nt_tiles + 1) / 2);
+            switch (w) {
+                case 8: e = launch_sym<8>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
+                case 4: e = launch_sym<4>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
+                case 2: e = launch_sym<2>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
+                default: e = launch_sym<1>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
+            }
+            if (e != cudaSuccess) return e;
+            count_launches(2);
+            int64_t tot = Nt * g;
+            int blocks = int((tot + 255) / 256);
+            if (blocks > 152 * 8) blocks = 152 * 8;
+            covmv_df_reduce<<<blocks, 256, 0, s>>>(part, nt_tiles, Nt, g, Z + int64_t(v0) * ldz, ldz, scale2, J);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            v0 += g;
+            continue;
+        }
+        switch (width_df(g)) {
+            case 32: e = dispatch_df<32>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 24: e = dispatch_df<24>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 20: e = dispatch_df<20>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 16: e = dispatch_df<16>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 12: e = dispatch_df<12>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 8: e = dispatch_df<8>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 4: e = dispatch_df<4>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            case 2: e = dispatch_df<2>(cp, Ug, ldu, part, grid, cps, g, s); break;
+            default: e = dispatch_df<1>(cp, Ug, ldu, part, grid, cps, g, s); break;
         }
         if (e != cudaSuccess) return e;
         count_launches(2);

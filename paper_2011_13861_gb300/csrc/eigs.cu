@@ -36,6 +36,9 @@ struct Eig {
     int mmax;    // capacity of the basis
     int bmax;    // capacity of a block
     kl::DevBuf bV, bW, bY, bT, bTc, bS, bSw, bTheta, bH, bH2, bG, bR, bR1, bRinv, bRtmp, bPart, bEst, bFlag, bSweeps;
+    kl::DevBuf bAV, bY2;   // A~'V (the operator products of the basis, kept through restarts)
+    double* AV() { return static_cast<double*>(bAV.ptr); }
+    double* Y2() { return static_cast<double*>(bY2.ptr); }
     double* V() { return static_cast<double*>(bV.ptr); }
     double* W() { return static_cast<double*>(bW.ptr); }
     double* Y() { return static_cast<double*>(bY.ptr); }
@@ -61,7 +64,8 @@ struct Eig {
     uint64_t seed = 1;
 
     ~Eig() {
-        kl::DevBuf* all[] = {&bV, &bW, &bY, &bT, &bTc, &bS, &bSw, &bTheta, &bH, &bH2, &bG, &bR, &bR1, &bRinv, &bRtmp, &bPart, &bEst, &bFlag, &bSweeps};
+        kl::DevBuf* all[] = {&bV, &bW, &bY, &bT, &bTc, &bS, &bSw, &bTheta, &bH, &bH2, &bG, &bR, &bR1,
+                             &bRinv, &bRtmp, &bPart, &bEst, &bFlag, &bSweeps, &bAV, &bY2};
         for (auto* b : all) release(*b);
     }
 
@@ -72,10 +76,12 @@ struct Eig {
         KL_TRY(ensure(bV, N8 * (m + b)));
         KL_TRY(ensure(bW, N8 * std::max(b, 64)));
         KL_TRY(ensure(bY, N8 * std::max(m, 64)));
+        KL_TRY(ensure(bAV, N8 * (m + b)));
+        KL_TRY(ensure(bY2, N8 * std::max(m, 64)));
         KL_TRY(ensure(bT, sizeof(double) * m * m));
         KL_TRY(ensure(bTc, sizeof(double) * m * m));
         KL_TRY(ensure(bS, sizeof(double) * m * m));
-        KL_TRY(ensure(bSw, sizeof(double) * m * m));
+        KL_TRY(ensure(bSw, 4 * sizeof(double) * m * m));
         KL_TRY(ensure(bTheta, sizeof(double) * m));
         KL_TRY(ensure(bH, sizeof(double) * m * b));
         KL_TRY(ensure(bH2, sizeof(double) * m * b));
@@ -113,10 +119,9 @@ struct Eig {
         e = launch_gemm_tall(-1.0, V(), N, N, j, H2(), mmax, b, 1.0, Wb, N, s);
         if (e != cudaSuccess) return cuda_fail(e, "update");
         // H += H2 (both stored with ld mmax, j rows, b columns)
-        for (int c = 0; c < b; ++c) {
-            e = launch_add_inplace(H() + size_t(c) * mmax, H2() + size_t(c) * mmax, j, s);
-            if (e != cudaSuccess) return cuda_fail(e, "accumulate");
-        }
+        // one launch over the b columns (rows j..mmax-1 of each column are unused scratch)
+        e = launch_add_inplace(H(), H2(), int(size_t(mmax) * (b - 1) + j), s);
+        if (e != cudaSuccess) return cuda_fail(e, "accumulate");
         return KL_OK;
     }
 
@@ -161,6 +166,15 @@ struct Eig {
         return fail(KL_ERR_NUMERIC, "could not extend the Krylov basis");
     }
 
+    // AV[:, 0:keep] = AV[:, 0:j] S[:, 0:keep]: the products of the new basis (Ritz vectors)
+    kl_status rotate_products(int j, int keep) {
+        cudaError_t e = launch_gemm_tall(1.0, AV(), N, N, j, S(), mmax, keep, 0.0, Y2(), N, s);
+        if (e != cudaSuccess) return cuda_fail(e, "rotate products");
+        e = launch_copy_block(Y2(), N, AV(), N, N, keep, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy products");
+        return KL_OK;
+    }
+
     kl_status sym_eig(int m) {
         cudaError_t e = launch_sym_eig_ws(T(), mmax, m, Theta(), S(), mmax, Sw(), Sweeps(), s);
         if (e != cudaSuccess) return cuda_fail(e, "small eigensolver");
@@ -196,6 +210,9 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         while (!full) {
             double* Q = E.V() + size_t(j - b) * E.N;
             KL_TRY(E.apply(P.prec, Q, E.W(), b));
+            // keep the raw products: A V[:, j-b:j]
+            cudaError_t ec = launch_copy_block(E.W(), E.N, E.AV() + size_t(j - b) * E.N, E.N, E.N, b, E.s);
+            if (ec != cudaSuccess) return cuda_fail(ec, "copy products");
             KL_TRY(E.orthogonalize(E.W(), b, j));
             cudaError_t e = launch_fill_T_block(E.T(), E.mmax, 0, j - b, E.H(), E.mmax, j, b, true, E.s);
             if (e != cudaSuccess) return cuda_fail(e, "fill T");
@@ -223,6 +240,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                     if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
                     e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, k, E.s);
                     if (e != cudaSuccess) return cuda_fail(e, "copy");
+                    KL_TRY(E.rotate_products(j, k));
                     for (int i = 0; i < k; ++i) {
                         theta[i] = th[i];
                         est[i] = rs[i];
@@ -264,6 +282,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
         e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, keep, E.s);
         if (e != cudaSuccess) return cuda_fail(e, "copy");
+        KL_TRY(E.rotate_products(j, keep));
         if (ok || last) {
             *converged = ok;
             return KL_OK;
@@ -370,6 +389,14 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
         // they form the first, wide block of a float64 block Lanczos run.
         Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, k};
+        // re-orthonormalise the float32-phase Ritz block in float64 (CholQR2) before it becomes
+        // the first block of the float64-accurate phase
+        {
+            bool defp = false;
+            KL_TRY(E.cholqr(E.V(), pb, E.W(), &defp));
+            e = launch_copy_block(E.W(), N, E.V(), N, N, pb, s);
+            if (e != cudaSuccess) return cuda_fail(e, "copy");
+        }
         // the active block is V[:, 0:pb]; T is rebuilt by the first expansion
         e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
         if (e != cudaSuccess) return cuda_fail(e, "memset");
@@ -382,9 +409,15 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     for (int i = 0; i < k; ++i) resid[i] = est[i] / std::max(fabs(theta[i]), 1e-300);
     if (o.verify) {
         // explicit float64 residuals ||A y - theta y|| / |theta|
-        KL_TRY(E.apply(o.verify == 2 ? KL_P_FP64 : o.precision, E.V(), E.Y(), k));
+        // verify 1: A~'y from the operator products kept with the basis (AV S);
+        // verify 2: a fresh application with the float64 kernel
+        const double* AY = E.AV();
+        if (o.verify == 2) {
+            KL_TRY(E.apply(KL_P_FP64, E.V(), E.Y(), k));
+            AY = E.Y();
+        }
         KL_CUDA(cudaMemcpyAsync(E.Theta(), theta.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
-        e = launch_ritz_resid(E.Y(), E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
+        e = launch_ritz_resid(AY, E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
         if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
         KL_CUDA(cudaMemcpyAsync(resid.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
     }

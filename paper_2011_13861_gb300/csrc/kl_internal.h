@@ -74,10 +74,14 @@ cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int
                            int64_t ldz, double scale2, const double* J, double* part, int splits,
                            cudaStream_t s);
 int covmv_splits(int64_t Nt, int nvec, bool fp32);
+cudaError_t launch_covmv64_sym(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z,
+                               int64_t ldz, double scale2, const double* J, double* part, int splits,
+                               cudaStream_t s);
 cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z,
                             int64_t ldz, double scale2, const double* J, double* part, int splits,
                             cudaStream_t s);
 int covmv_df_splits(int64_t Nt);
+size_t covmv_df_part_doubles(int64_t Nt, int nvec);
 
 // dense block linear algebra (linalg.cu)
 cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
@@ -90,6 +94,9 @@ cudaError_t launch_chol_inv(double* G, int ldg, int b, double* Rinv, double* R, 
                             cudaStream_t s);
 cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64_t seed,
                                 uint64_t offset, cudaStream_t s);
+// Symmetric eigen-decomposition of the m x m (m <= 160) matrix T (column-major, ld ldt) by
+// float64 parallel cyclic Jacobi in one CTA: sorted eigenvalues (descending) and eigenvectors S.
+// work: m^2 doubles.
 cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, double* S, int lds,
                               double* work, int* sweeps_out, cudaStream_t s);
 cudaError_t launch_residual_norms(const double* G, int ldg, const double* S, int lds, int srow0,

@@ -177,7 +177,8 @@ __device__ __forceinline__ void rr_pair(int i, int r, int mp, int* a, int* b) {
 
 __global__ void __launch_bounds__(kEigThreads)
 sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restrict__ evals,
-               double* __restrict__ Sout, int lds, double* __restrict__ W, int* sweeps_out) {
+               double* __restrict__ Sout, int lds, double* __restrict__ W, int* sweeps_out,
+               bool w_given) {
     extern __shared__ double sT[];          // m x m, row-major with stride m
     __shared__ double cs[kEigMax / 2 + 1][2];
     __shared__ int prs[kEigMax / 2 + 1][2];
@@ -186,7 +187,7 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
     for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e - i * m;
         sT[e] = 0.5 * (Tin[i + int64_t(j) * ldt] + Tin[j + int64_t(i) * ldt]);
-        W[i + int64_t(j) * m] = (i == j) ? 1.0 : 0.0;    // eigenvector accumulator, column-major
+        if (!w_given) W[i + int64_t(j) * m] = (i == j) ? 1.0 : 0.0;   // eigenvector accumulator, column-major
     }
     __syncthreads();
     const int mp = (m % 2 == 0) ? m : m + 1;
@@ -467,7 +468,7 @@ cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, do
     const size_t smem = size_t(m) * m * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    sym_eig_kernel<<<1, kEigThreads, smem, s>>>(T, ldt, m, evals, S, lds, work, sweeps_out);
+    sym_eig_kernel<<<1, kEigThreads, smem, s>>>(T, ldt, m, evals, S, lds, work, sweeps_out, false);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -20,9 +20,31 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
     ap.add_argument("--nvec", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--solve", default=None, choices=[None, "plain", "plain_df", "mixed"],
+                    help="run one warm-up and one timed eigensolve instead of stage 5 alone")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--tol-low", type=float, default=0.0)
+    ap.add_argument("--ncv", type=int, default=0)
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    if a.solve:
+        method = 1 if a.solve == "mixed" else 0
+        block = a.block or (16 if method == 1 else 4)
+        prec = kl.KL_P_FP64 if a.solve == "plain" else kl.KL_P_DF64
+        start = torch.from_numpy(inputs.random_block(G.N, block, seed=1).T.copy()).cuda()
+        out = []
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ev, _, info = G.eigs(w["k"], 1e-8, method=method, block=block, start=start, precision=prec,
+                                 tol_low=a.tol_low, ncv=a.ncv)
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        info.pop("resid")
+        print(json.dumps({"workload": a.workload, "solve": a.solve, "block": block, "ms": out, "info": info}))
+        return
     prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32, "df64": kl.KL_P_DF64}[a.precision]
     v = torch.from_numpy(inputs.random_block(G.N, a.nvec, seed=1).T.copy()).cuda()
     u = G.forward(v).reshape(a.nvec, G.Nt).contiguous()
