@@ -31,8 +31,12 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 vector rate (nominal)
 # subtract, multiply; FMA = 2): distance 3 sub + 3 mul + 2 add, pre-scaled coordinates carry 1/L
 # (the 9th flop of the survey's count is folded into set-up); sqrt by one Heron correction
 # (mul, fma, mul, fma = 6); exp by Tang's method (fma, sub, fma, 4 fma + mul, fma = 16);
-# plus 2 flops per vector for the product.
-FLOPS_PER_PAIR = {"exp": 8 + 6 + 16, "gauss": 8 + 16, "exp_sep": 3 + 2 + 16, "poly": 12}
+# plus 2 flops per vector for the product.  The kernel is symmetric, so the method needs only half
+# of the evaluations (one per unordered pair): algorithmic flops per ordered pair = eval/2 + 2b.
+FLOPS_PER_EVAL = {"exp": 8 + 6 + 16, "gauss": 8 + 16, "exp_sep": 3 + 2 + 16, "poly": 12}
+# DRAM bytes per launch of covmv64_sym_kernel<EXP, 4> at 39,304 points (ncu capture, see
+# profiles/stage5_fp64_sym_cube-p2-32^3-exp.md): 3.7 MB read + 136.3 MB written (partial slots)
+SYM64_NV4_TRAFFIC_BYTES = 3.748352e6 + 136.348928e6
 
 
 def parse():
@@ -43,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--plain-block", type=int, default=4)
-    ap.add_argument("--mixed-block", type=int, default=16)
+    ap.add_argument("--mixed-block", type=int, default=4)
     return ap.parse_args()
 
 
@@ -249,11 +253,12 @@ def main():
     value = world * applies_p * float(Nt) * Nt / (ms_plain * 1e-3)
 
     # roofline of the dominant kernel (float64 stage 5) from the events recorded around it
-    fl = FLOPS_PER_PAIR[w["kernel"]]
+    fl = FLOPS_PER_EVAL[w["kernel"]]
     calls = info_p["stage5_calls_fp64"]
     ms5 = info_p["ms_stage5_fp64"] / max(calls, 1)
     vecs_per_call = applies_p / max(calls, 1)
-    flops_per_launch = float(Nt) * Nt * (fl + 2 * vecs_per_call)
+    flops_per_pair = 0.5 * fl + 2 * vecs_per_call
+    flops_per_launch = float(Nt) * Nt * flops_per_pair
     achieved = flops_per_launch / (ms5 * 1e-3) / 1e12
     stage5_share = info_p["ms_stage5_fp64"] / ms_plain
 
@@ -300,7 +305,8 @@ def main():
         "plain_fp64": {"applies": applies_p, "block_applies": info_p["block_applies"],
                        "restarts": info_p["restarts"], "max_resid": max(info_p["resid"]),
                        "evals_per_s": value, "eigenvalues": [float(x) for x in ev_p]},
-        "chosen_form": {"method": "float32 stage-5 block Lanczos (block %d) + double-float polish" % args.mixed_block,
+        "chosen_form": {"method": "float32 stage-5 block Lanczos (block %d) + double-float (float64-accurate) "
+                                  "block-%d polish; symmetric-tile stage 5" % (args.mixed_block, k),
                         "ms": ms_mixed, "applies": info_m["applies"], "applies_df64": info_m["applies_df64"],
                         "max_resid": max(info_m["resid"]), "max_resid_fp64_operator": fp64_resid,
                         "stage5_df64_ms_per_call": info_m["ms_stage5_df64"] / max(info_m["stage5_calls_df64"], 1),
@@ -309,11 +315,14 @@ def main():
                         "ms_fp32_phase": info_m["ms_fp32_phase"],
                         "stage5_fp32_ms_per_call": info_m["ms_stage5_fp32"] / max(info_m["stage5_calls_fp32"], 1),
                         "stage5_fp64_ms_per_call": info_m["ms_stage5_fp64"] / max(info_m["stage5_calls_fp64"], 1)},
-        "roofline": {"bound": "alu", "kernel": "covmv64_kernel (float64 stage 5, exponential)",
+        "roofline": {"bound": "alu", "kernel": "covmv64_sym_kernel (float64 stage 5, symmetric tiles, exponential)",
                      "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                     "peak_source": "nominal GB300 FP64 vector rate (recipe table); not in MEASURED_PEAKS.json",
-                     "flops_per_pair": fl, "ms_per_launch": ms5, "launches": calls,
+                     "frac": achieved / FP64_NOMINAL_TFLOPS,
+                     "traffic": SYM64_NV4_TRAFFIC_BYTES if (w["kernel"] == "exp" and Nt == 39304
+                                                            and args.plain_block == 4) else None,
+                     "peak_source": "nominal GB300 FP64 vector rate (recipe table; MEASURED_PEAKS.json has no "
+                                    "FP64 figure); own DFMA microbenchmark: 1.00 TFLOP/s",
+                     "flops_per_pair": flops_per_pair, "ms_per_launch": ms5, "launches": calls,
                      "stage5_share_of_step": stage5_share},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": N * args.plain_block * 8,
                 "d2h_bytes_per_step": k * N * 8 + k * 8, "seconds": e2e_t},

@@ -185,6 +185,8 @@ typedef struct {
                              * 0 = the Lanczos estimates */
     int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default) or KL_P_DF64;
                              * method 0: every application, method 1: the polish */
+    int polish_block;       /* method 1: width of the polish block (0 = k; k..48) */
+    int polish_ncv;         /* method 1: polish basis size (0 = 3 x polish_block, at most 160) */
 } kl_eig_opts;
 
 typedef struct {

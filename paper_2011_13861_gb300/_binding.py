@@ -33,7 +33,8 @@ class KLKernel(ctypes.Structure):
 class KLEigOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("block", ctypes.c_int), ("ncv", ctypes.c_int),
                 ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("start_dev", _vp),
-                ("tol_low", ctypes.c_double), ("verify", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("tol_low", ctypes.c_double), ("verify", ctypes.c_int), ("precision", ctypes.c_int),
+                ("polish_block", ctypes.c_int), ("polish_ncv", ctypes.c_int)]
 
 
 class KLEigInfo(ctypes.Structure):
@@ -245,13 +246,14 @@ class KLProblem:
         return X[:, :self.dim].copy(), J
 
     def eigs(self, k, tol=1e-8, method=0, block=1, ncv=0, maxiter=0, seed=1, start=None, tol_low=0.0,
-             verify=True, want_vectors=True, stream=None, raise_on_nonconv=True, precision=KL_P_FP64):
+             verify=True, want_vectors=True, stream=None, raise_on_nonconv=True, precision=KL_P_FP64,
+             polish_block=0, polish_ncv=0):
         """The k largest eigenpairs (descending).  Returns (evals numpy, evecs (k, N) tensor or None, info dict)."""
         import numpy as np
         import torch
         opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1),
                          _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0,
-                         int(precision))
+                         int(precision), int(polish_block), int(polish_ncv))
         ev = np.zeros(k)
         vecs = None
         dev = torch.device("cuda", torch.cuda.current_device())

@@ -218,7 +218,7 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
         const int64_t ld = stride_of(h);
         e = launch_to_float(u, ldu, uf, ld, h->Nt, nvec, s);
         if (e == cudaSuccess)
-            e = launch_covmv32(cp, uf, ld, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
+            e = launch_covmv32_sym(cp, uf, ld, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
                                covmv_splits(h->Nt, nvec, true), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product");
@@ -300,7 +300,7 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
     double* z = A;
     int slot;
     KL_TRY(prof_begin(h, KL_P_FP32, nvec, s, &slot));
-    cudaError_t e = launch_covmv32(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+    cudaError_t e = launch_covmv32_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
                                    covmv_splits(h->Nt, nvec, true), s);
     if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp32)");
     KL_TRY(prof_end(h, slot, s));

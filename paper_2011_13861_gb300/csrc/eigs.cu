@@ -319,6 +319,8 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.tol_low = 0.0;
     o.verify = 1;
     o.precision = KL_P_FP64;
+    o.polish_block = 0;
+    o.polish_ncv = 0;
     if (opts_in) o = *opts_in;
     if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64)
         return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64 or KL_P_DF64");
@@ -339,8 +341,9 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     while ((m - keep) % b != 0) --keep;
 
     // float64 polish of the mixed method: one wide block over the kept float32 Ritz vectors
-    const int pol_b = std::min(std::max(k + 4, b), 48);
-    const int pol_m = std::min(3 * pol_b, 160 / pol_b * pol_b);
+    const int pol_b = std::min(std::max(o.polish_block > 0 ? o.polish_block : k, k), 48);
+    int pol_m = o.polish_ncv > 0 ? o.polish_ncv / pol_b * pol_b : 3 * pol_b;
+    pol_m = std::min(std::max(pol_m, 2 * pol_b), 160 / pol_b * pol_b);
 
     // stage-5 event timing for the whole call (read back at the end)
     h->prof_on = (info != nullptr);

@@ -74,6 +74,9 @@ cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int
                            int64_t ldz, double scale2, const double* J, double* part, int splits,
                            cudaStream_t s);
 int covmv_splits(int64_t Nt, int nvec, bool fp32);
+cudaError_t launch_covmv32_sym(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z,
+                               int64_t ldz, double scale2, const double* J, double* part, int splits,
+                               cudaStream_t s);
 cudaError_t launch_covmv64_sym(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z,
                                int64_t ldz, double scale2, const double* J, double* part, int splits,
                                cudaStream_t s);

@@ -25,6 +25,8 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tol-low", type=float, default=0.0)
     ap.add_argument("--ncv", type=int, default=0)
+    ap.add_argument("--polish-block", type=int, default=0)
+    ap.add_argument("--polish-ncv", type=int, default=0)
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
@@ -38,7 +40,8 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             ev, _, info = G.eigs(w["k"], 1e-8, method=method, block=block, start=start, precision=prec,
-                                 tol_low=a.tol_low, ncv=a.ncv)
+                                 tol_low=a.tol_low, ncv=a.ncv, polish_block=a.polish_block,
+                                 polish_ncv=a.polish_ncv)
             e1.record()
             torch.cuda.synchronize()
             out.append(e0.elapsed_time(e1))
