@@ -95,8 +95,13 @@ typedef struct {
  *   KL_P_DF64  kernel, distance and accumulation in double-float arithmetic (pairs of
  *              float32, ~48 significant bits) on the float32 pipe: float64-level results
  *              (matvec rel. error ~1e-14) at several times the float64 pipe's throughput on
- *              GB300; contractions in float64. */
-typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1, KL_P_DF64 = 2 } kl_precision;
+ *              GB300; contractions in float64.
+ *   KL_P_TC32  float32-accurate stage 5 on the tensor cores (tcgen05): float32 kernel values
+ *              split into three bfloat16 terms, products accumulated in float32 in tensor
+ *              memory (relative error ~1e-6, like KL_P_FP32); contractions in float32.
+ *              Calls that launch it synchronise the stream once to read a device status
+ *              word (KL_ERR_TIMEOUT if a bounded wait inside the kernel gave up). */
+typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1, KL_P_DF64 = 2, KL_P_TC32 = 3 } kl_precision;
 
 /* Build the univariate factors, the mapped Greville grid and J on the host in
  * float64 (Sec. 3.5, 4.1-4.3), upload them, and return a handle.
@@ -187,6 +192,7 @@ typedef struct {
                              * method 0: every application, method 1: the polish */
     int polish_block;       /* method 1: width of the polish block (0 = k; k..48) */
     int polish_ncv;         /* method 1: polish basis size (0 = 3 x polish_block, at most 160) */
+    int low_precision;      /* method 1: first-phase arithmetic, KL_P_FP32 (0 = default) or KL_P_TC32 */
 } kl_eig_opts;
 
 typedef struct {

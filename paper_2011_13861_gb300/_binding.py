@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 KL_GEOM_BOX = 0
 KL_K_EXP, KL_K_GAUSS, KL_K_EXP_SEPARABLE, KL_K_POLY_TEST = 0, 1, 2, 3
-KL_P_FP64, KL_P_FP32, KL_P_DF64 = 0, 1, 2
+KL_P_FP64, KL_P_FP32, KL_P_DF64, KL_P_TC32 = 0, 1, 2, 3
 KERNEL_KINDS = {"exp": KL_K_EXP, "gauss": KL_K_GAUSS, "exp_sep": KL_K_EXP_SEPARABLE, "poly": KL_K_POLY_TEST}
 STATUS = {0: "KL_OK", 1: "KL_ERR_INVALID_ARG", 2: "KL_ERR_CUDA", 3: "KL_ERR_OOM",
           4: "KL_ERR_NOT_CONVERGED", 5: "KL_ERR_TIMEOUT", 6: "KL_ERR_NUMERIC"}
@@ -34,7 +34,7 @@ class KLEigOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("block", ctypes.c_int), ("ncv", ctypes.c_int),
                 ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("start_dev", _vp),
                 ("tol_low", ctypes.c_double), ("verify", ctypes.c_int), ("precision", ctypes.c_int),
-                ("polish_block", ctypes.c_int), ("polish_ncv", ctypes.c_int)]
+                ("polish_block", ctypes.c_int), ("polish_ncv", ctypes.c_int), ("low_precision", ctypes.c_int)]
 
 
 class KLEigInfo(ctypes.Structure):
@@ -247,13 +247,13 @@ class KLProblem:
 
     def eigs(self, k, tol=1e-8, method=0, block=1, ncv=0, maxiter=0, seed=1, start=None, tol_low=0.0,
              verify=True, want_vectors=True, stream=None, raise_on_nonconv=True, precision=KL_P_FP64,
-             polish_block=0, polish_ncv=0):
+             polish_block=0, polish_ncv=0, low_precision=KL_P_FP32):
         """The k largest eigenpairs (descending).  Returns (evals numpy, evecs (k, N) tensor or None, info dict)."""
         import numpy as np
         import torch
         opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1),
                          _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0,
-                         int(precision), int(polish_block), int(polish_ncv))
+                         int(precision), int(polish_block), int(polish_ncv), int(low_precision))
         ev = np.zeros(k)
         vecs = None
         dev = torch.device("cuda", torch.cuda.current_device())

@@ -89,6 +89,7 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32) {
     size_t groups = size_t(s64) * 16;
     if (size_t(s32) * 32 > groups) groups = size_t(s32) * 32;
     if (size_t(sdf) * 32 > groups) groups = size_t(sdf) * 32;
+    if (size_t(covmv_tc_splits(h->Nt)) * 16 > groups) groups = size_t(covmv_tc_splits(h->Nt)) * 16;
     size_t part = size_t(h->Nt) * groups;
     const size_t dfp = covmv_df_part_doubles(h->Nt, nvec);
     if (dfp > part) part = dfp;
@@ -111,6 +112,18 @@ CovParams cov_params(kl_handle h) {
 }
 
 }  // namespace
+
+// Reads (and clears) the device status word written by kernels with bounded waits.
+kl_status check_device_status(kl_handle h, cudaStream_t s) {
+    int st = 0;
+    KL_CUDA(cudaMemcpyAsync(&st, h->dStatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KL_CUDA(cudaStreamSynchronize(s));
+    if (st != 0) {
+        KL_CUDA(cudaMemsetAsync(h->dStatus, 0, sizeof(int), s));
+        return fail(KL_ERR_TIMEOUT, "a bounded wait in the tensor-core stage-5 kernel gave up");
+    }
+    return KL_OK;
+}
 
 // ---- stages 1-4: u = J . C v  (C = C_d (x) ... (x) C_1) ----------------------------------
 template <typename Tc, typename Tout>
@@ -202,11 +215,21 @@ kl_status forward_impl(kl_handle h, const double* v, int64_t ldv, double* u, int
 
 kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, double* z, int64_t ldz,
                      int nvec, bool withJ, cudaStream_t s) {
-    KL_TRY(ensure_apply_ws(h, nvec, precision == KL_P_FP32));
+    KL_TRY(ensure_apply_ws(h, nvec, precision == KL_P_FP32 || precision == KL_P_TC32));
     CovParams cp = cov_params(h);
     const double s2 = h->kernel.sigma * h->kernel.sigma;
     const double* J = withJ ? h->dJ : nullptr;
     cudaError_t e;
+    if (precision == KL_P_TC32) {
+        float* uf = static_cast<float*>(h->w_f32a.ptr);
+        const int64_t ld = stride_of(h);
+        e = launch_to_float(u, ldu, uf, ld, h->Nt, nvec, s);
+        if (e == cudaSuccess)
+            e = launch_covmv_tc(cp, uf, ld, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
+                                covmv_tc_splits(h->Nt), h->dStatus, s);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (tensor cores)");
+        return KL_OK;
+    }
     if (precision == KL_P_FP64) {
         e = launch_covmv64_sym(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
                            covmv_splits(h->Nt, nvec, false), s);
@@ -268,7 +291,7 @@ static kl_status prof_end(kl_handle h, int slot, cudaStream_t s) {
 kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, double* y, int64_t ldy, int nvec,
                      cudaStream_t s) {
     if (nvec == 0) return KL_OK;
-    const bool fp32 = (precision == KL_P_FP32);
+    const bool fp32 = (precision == KL_P_FP32 || precision == KL_P_TC32);
     KL_TRY(ensure_apply_ws(h, nvec, fp32));
     const int64_t ld = stride_of(h);
     double* A = static_cast<double*>(h->w_a.ptr);
@@ -300,8 +323,11 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
     double* z = A;
     int slot;
     KL_TRY(prof_begin(h, KL_P_FP32, nvec, s, &slot));
-    cudaError_t e = launch_covmv32_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                   covmv_splits(h->Nt, nvec, true), s);
+    cudaError_t e = (precision == KL_P_TC32)
+                        ? launch_covmv_tc(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                                          covmv_tc_splits(h->Nt), h->dStatus, s)
+                        : launch_covmv32_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
+                                             covmv_splits(h->Nt, nvec, true), s);
     if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp32)");
     KL_TRY(prof_end(h, slot, s));
     return backward_generic<float>(h, z, ld, y, ldy, nvec, h->fC, FA, FB, s);
@@ -430,6 +456,8 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     chk(upload(&h->dTab, tab.data(), tab.size()));
     chk(upload(&h->dfP, Pdf.data(), Pdf.size()));
     chk(upload(&h->dfTab, tabdf.data(), tabdf.size()));
+    const int zero = 0;
+    chk(upload(&h->dStatus, &zero, 1));
     for (int k = 0; k < d && st == KL_OK; ++k) {
         const Direction& D = h->dir[k];
         const int n = D.n, nt = D.nt;
@@ -480,8 +508,10 @@ kl_status kl_dims(kl_handle h, int* n, int* ntilde) {
 kl_status kl_apply_prec(kl_handle h, int precision, const double* v_dev, double* y_dev, int nvec, int64_t ldv,
                         void* stream) {
     KL_TRY(check_block(h, v_dev, y_dev, nvec, ldv, h ? h->N : 0, ldv, h ? h->N : 0));
-    if (precision < KL_P_FP64 || precision > KL_P_DF64) return fail(KL_ERR_INVALID_ARG, "unknown precision");
-    return apply_impl(h, precision, v_dev, ldv, y_dev, ldv, nvec, static_cast<cudaStream_t>(stream));
+    if (precision < KL_P_FP64 || precision > KL_P_TC32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    KL_TRY(apply_impl(h, precision, v_dev, ldv, y_dev, ldv, nvec, static_cast<cudaStream_t>(stream)));
+    if (precision == KL_P_TC32) return check_device_status(h, static_cast<cudaStream_t>(stream));
+    return KL_OK;
 }
 
 kl_status kl_apply(kl_handle h, const double* v_dev, double* y_dev, int nvec, int64_t ldv, void* stream) {
@@ -498,9 +528,11 @@ kl_status kl_forward(kl_handle h, const double* v_dev, int64_t ldv, double* u_de
 kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev, int64_t ldz,
                    int nvec, void* stream) {
     KL_TRY(check_block(h, u_dev, z_dev, nvec, ldu, h ? h->Nt : 0, ldz, h ? h->Nt : 0));
-    if (precision < KL_P_FP64 || precision > KL_P_DF64) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    if (precision < KL_P_FP64 || precision > KL_P_TC32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
     if (nvec == 0) return KL_OK;
-    return covmv_impl(h, precision, u_dev, ldu, z_dev, ldz, nvec, false, static_cast<cudaStream_t>(stream));
+    KL_TRY(covmv_impl(h, precision, u_dev, ldu, z_dev, ldz, nvec, false, static_cast<cudaStream_t>(stream)));
+    if (precision == KL_P_TC32) return check_device_status(h, static_cast<cudaStream_t>(stream));
+    return KL_OK;
 }
 
 kl_status kl_backward(kl_handle h, const double* z_dev, int64_t ldz, double* y_dev, int64_t ldy, int nvec,
@@ -579,6 +611,7 @@ void kl_destroy(kl_handle h) {
     if (h->dTab) cudaFree(h->dTab);
     if (h->dfP) cudaFree(h->dfP);
     if (h->dfTab) cudaFree(h->dfTab);
+    if (h->dStatus) cudaFree(h->dStatus);
     release(h->w_a);
     release(h->w_b);
     release(h->w_f32a);

@@ -321,6 +321,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.precision = KL_P_FP64;
     o.polish_block = 0;
     o.polish_ncv = 0;
+    o.low_precision = KL_P_FP32;
     if (opts_in) o = *opts_in;
     if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64)
         return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64 or KL_P_DF64");
@@ -385,8 +386,10 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     } else {
         const double tl = o.tol_low > 0.0 ? o.tol_low : 1e-5;
         const int pb = std::min(pol_b, m);
-        Phase P1{KL_P_FP32, b, m, keep, std::max(tl, tol), false, maxrestart, pb};
+        const int lowp = (o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32;
+        Phase P1{lowp, b, m, keep, std::max(tl, tol), false, maxrestart, pb};
         KL_TRY(run_phase(E, P1, k, b, &restarts, theta, est, &conv));
+        if (lowp == KL_P_TC32) KL_TRY(check_device_status(h, s));
         KL_CUDA(cudaStreamSynchronize(s));
         ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);

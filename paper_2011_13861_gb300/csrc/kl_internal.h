@@ -74,6 +74,12 @@ cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int
                            int64_t ldz, double scale2, const double* J, double* part, int splits,
                            cudaStream_t s);
 int covmv_splits(int64_t Nt, int nvec, bool fp32);
+// tensor-core (tcgen05) float32-accurate stage 5 for blocks of 16; `status` is a device int that
+// a CTA sets to KL_ERR_TIMEOUT when a bounded wait gives up
+cudaError_t launch_covmv_tc(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
+                            double scale2, const double* J, double* part, int splits, int* status,
+                            cudaStream_t s);
+int covmv_tc_splits(int64_t Nt);
 cudaError_t launch_covmv32_sym(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z,
                                int64_t ldz, double scale2, const double* J, double* part, int splits,
                                cudaStream_t s);
@@ -153,6 +159,7 @@ struct kl_handle_s {
     double* dTab = nullptr;   // 64
     float* dfP = nullptr;     // 6 x Nt double-float coordinates (pre-scaled like dP)
     float* dfTab = nullptr;   // 128: double-float 2^(-j/64)
+    int* dStatus = nullptr;   // device status word of the kernels with bounded waits (0 = ok)
     // workspace
     kl::DevBuf w_a, w_b, w_f32a, w_f32b, w_part;
     // stage-5 event timing (enabled by kl_eigs while it runs)
@@ -171,6 +178,7 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
                      int64_t ldz, int nvec, bool withJ, cudaStream_t s);
 kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, int64_t ldy,
                         int nvec, bool zHasJ, cudaStream_t s);
+kl_status check_device_status(kl_handle h, cudaStream_t s);
 kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host,
                     double* evecs_dev, int64_t ldv, kl_eig_info* info, cudaStream_t s);
 }  // namespace kl

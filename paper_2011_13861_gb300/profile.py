@@ -17,7 +17,7 @@ from paper_2011_13861_gb300 import inputs
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cube-p2-32^3-exp-L0.5")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64", "tc32"])
     ap.add_argument("--nvec", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--solve", default=None, choices=[None, "plain", "plain_df", "mixed"],
@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--ncv", type=int, default=0)
     ap.add_argument("--polish-block", type=int, default=0)
     ap.add_argument("--polish-ncv", type=int, default=0)
+    ap.add_argument("--low", default="fp32", choices=["fp32", "tc32"])
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
@@ -41,14 +42,15 @@ def main():
             e0.record()
             ev, _, info = G.eigs(w["k"], 1e-8, method=method, block=block, start=start, precision=prec,
                                  tol_low=a.tol_low, ncv=a.ncv, polish_block=a.polish_block,
-                                 polish_ncv=a.polish_ncv)
+                                 polish_ncv=a.polish_ncv,
+                                 low_precision=kl.KL_P_TC32 if a.low == "tc32" else kl.KL_P_FP32)
             e1.record()
             torch.cuda.synchronize()
             out.append(e0.elapsed_time(e1))
         info.pop("resid")
         print(json.dumps({"workload": a.workload, "solve": a.solve, "block": block, "ms": out, "info": info}))
         return
-    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32, "df64": kl.KL_P_DF64}[a.precision]
+    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32, "df64": kl.KL_P_DF64, "tc32": kl.KL_P_TC32}[a.precision]
     v = torch.from_numpy(inputs.random_block(G.N, a.nvec, seed=1).T.copy()).cuda()
     u = G.forward(v).reshape(a.nvec, G.Nt).contiguous()
     G.covmv(u, precision=prec)

@@ -99,6 +99,22 @@ def test_apply_fp32(kl, case):
     assert rel(z, P.stage5(X, u)) < FP32_TOL
 
 
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dd-%s" % (c[0], c[3]))
+@pytest.mark.parametrize("nvec", [16, 3, 17])
+def test_tensor_core_stage5(kl, case, nvec):
+    """KL_P_TC32: float32 kernel values split into three bfloat16 terms, tcgen05 MMA with float32
+    accumulation in tensor memory; float32-level agreement with the float64 oracle."""
+    import torch
+    P, G = make(kl, case)
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, nvec, seed=31)
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=kl.KL_P_TC32).cpu().numpy().T
+    assert rel(z, P.stage5(X, u)) < FP32_TOL
+    v = inputs.random_block(P.N, nvec, seed=32)
+    y = G.apply(torch.from_numpy(v.T.copy()).cuda(), precision=kl.KL_P_TC32).cpu().numpy().T
+    assert rel(y, P.dense_operator() @ v) < FP32_TOL
+
+
 @pytest.mark.parametrize("nvec", [1, 2, 7, 16, 17, 33])
 def test_block_widths(kl, nvec):
     """Vector groups of the stage-5 kernels (16 in float64, 32 in float32) and their tails."""
