@@ -100,8 +100,15 @@ typedef struct {
  *              split into three bfloat16 terms, products accumulated in float32 in tensor
  *              memory (relative error ~1e-6, like KL_P_FP32); contractions in float32.
  *              Calls that launch it synchronise the stream once to read a device status
- *              word (KL_ERR_TIMEOUT if a bounded wait inside the kernel gave up). */
-typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1, KL_P_DF64 = 2, KL_P_TC32 = 3 } kl_precision;
+ *              word (KL_ERR_TIMEOUT if a bounded wait inside the kernel gave up).
+ *   KL_P_TC64  float64-class stage 5 on the tensor cores: double-float kernel values and the
+ *              float64 u (scaled per vector by a power of two) cut into six exact 8-bit
+ *              bfloat16 slices each; the 21 slice products of weight >= 2^-48 are summed in
+ *              tensor memory, the three leading levels exactly (drained every 128 columns),
+ *              so the product matches KL_P_DF64 (matvec rel. error ~1e-14); contractions in
+ *              float64.  Same status-word synchronisation as KL_P_TC32.  No counterpart in
+ *              the paper, which evaluates the kernel and sums in float64 (Sec. 4.4). */
+typedef enum { KL_P_FP64 = 0, KL_P_FP32 = 1, KL_P_DF64 = 2, KL_P_TC32 = 3, KL_P_TC64 = 4 } kl_precision;
 
 /* Build the univariate factors, the mapped Greville grid and J on the host in
  * float64 (Sec. 3.5, 4.1-4.3), upload them, and return a handle.
@@ -188,7 +195,7 @@ typedef struct {
                              *     restart (A~'Y = (A~'V) S; no extra application);
                              * 2 = from a fresh application with the float64 kernel;
                              * 0 = the Lanczos estimates */
-    int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default) or KL_P_DF64;
+    int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default), KL_P_DF64 or KL_P_TC64;
                              * method 0: every application, method 1: the polish */
     int polish_block;       /* method 1: width of the polish block (0 = k; k..48) */
     int polish_ncv;         /* method 1: polish basis size (0 = 3 x polish_block, at most 160) */
@@ -209,6 +216,9 @@ typedef struct {
     double ms_stage5_fp64, ms_stage5_fp32, ms_stage5_df64;
     double pairs_fp64, pairs_fp32, pairs_df64;  /* kernel evaluations (Ntilde^2 per launch group) */
     int applies_df64;       /* operator applications counted per vector in KL_P_DF64 */
+    int stage5_calls_tc64;  /* stage-5 launch groups, time and kernel evaluations in KL_P_TC64 */
+    double ms_stage5_tc64, pairs_tc64;
+    int applies_tc64;       /* operator applications counted per vector in KL_P_TC64 */
 } kl_eig_info;
 
 /* The k (<= 64) largest eigenvalues of A~' (descending) to relative residual tol.

@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 KL_GEOM_BOX = 0
 KL_K_EXP, KL_K_GAUSS, KL_K_EXP_SEPARABLE, KL_K_POLY_TEST = 0, 1, 2, 3
-KL_P_FP64, KL_P_FP32, KL_P_DF64, KL_P_TC32 = 0, 1, 2, 3
+KL_P_FP64, KL_P_FP32, KL_P_DF64, KL_P_TC32, KL_P_TC64 = 0, 1, 2, 3, 4
 KERNEL_KINDS = {"exp": KL_K_EXP, "gauss": KL_K_GAUSS, "exp_sep": KL_K_EXP_SEPARABLE, "poly": KL_K_POLY_TEST}
 STATUS = {0: "KL_OK", 1: "KL_ERR_INVALID_ARG", 2: "KL_ERR_CUDA", 3: "KL_ERR_OOM",
           4: "KL_ERR_NOT_CONVERGED", 5: "KL_ERR_TIMEOUT", 6: "KL_ERR_NUMERIC"}
@@ -46,7 +46,9 @@ class KLEigInfo(ctypes.Structure):
                 ("ms_stage5_fp64", ctypes.c_double), ("ms_stage5_fp32", ctypes.c_double),
                 ("ms_stage5_df64", ctypes.c_double),
                 ("pairs_fp64", ctypes.c_double), ("pairs_fp32", ctypes.c_double), ("pairs_df64", ctypes.c_double),
-                ("applies_df64", ctypes.c_int)]
+                ("applies_df64", ctypes.c_int),
+                ("stage5_calls_tc64", ctypes.c_int), ("ms_stage5_tc64", ctypes.c_double),
+                ("pairs_tc64", ctypes.c_double), ("applies_tc64", ctypes.c_int)]
 
 
 SIGNATURES = {
@@ -271,5 +273,7 @@ class KLProblem:
              "ms_stage5_fp64": info.ms_stage5_fp64, "ms_stage5_fp32": info.ms_stage5_fp32,
              "pairs_fp64": info.pairs_fp64, "pairs_fp32": info.pairs_fp32,
              "stage5_calls_df64": info.stage5_calls_df64, "ms_stage5_df64": info.ms_stage5_df64,
-             "pairs_df64": info.pairs_df64, "applies_df64": info.applies_df64}
+             "pairs_df64": info.pairs_df64, "applies_df64": info.applies_df64,
+             "stage5_calls_tc64": info.stage5_calls_tc64, "ms_stage5_tc64": info.ms_stage5_tc64,
+             "pairs_tc64": info.pairs_tc64, "applies_tc64": info.applies_tc64}
         return ev, vecs, d

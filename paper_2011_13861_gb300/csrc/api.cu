@@ -76,7 +76,7 @@ kl_status check_block(kl_handle h, const void* a, const void* b, int nvec, int64
 }
 
 // workspace for nvec columns of the intermediate tensors
-kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32) {
+kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32, bool tc64 = false) {
     const int64_t ld = stride_of(h);
     KL_TRY(ensure(h->w_a, size_t(ld) * nvec * sizeof(double)));
     KL_TRY(ensure(h->w_b, size_t(ld) * nvec * sizeof(double)));
@@ -89,10 +89,19 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32) {
     size_t groups = size_t(s64) * 16;
     if (size_t(s32) * 32 > groups) groups = size_t(s32) * 32;
     if (size_t(sdf) * 32 > groups) groups = size_t(sdf) * 32;
-    if (size_t(covmv_tc_splits(h->Nt)) * 16 > groups) groups = size_t(covmv_tc_splits(h->Nt)) * 16;
     size_t part = size_t(h->Nt) * groups;
     const size_t dfp = covmv_df_part_doubles(h->Nt, nvec);
     if (dfp > part) part = dfp;
+    if (fp32) {
+        const size_t tcp = covmv_tc_part_doubles(h->Nt);
+        if (tcp > part) part = tcp;
+        KL_TRY(ensure(h->w_tcimg, covmv_tc_image_bytes(h->Nt)));
+    }
+    if (tc64) {
+        const size_t tcp = covmv_tc64_part_doubles(h->Nt);
+        if (tcp > part) part = tcp;
+        KL_TRY(ensure(h->w_tcimg, covmv_tc64_image_bytes(h->Nt)));
+    }
     KL_TRY(ensure(h->w_part, part * sizeof(double)));
     return KL_OK;
 }
@@ -108,6 +117,7 @@ CovParams cov_params(kl_handle h) {
     cp.tab = h->dTab;
     cp.Pdf = h->dfP;
     cp.tabdf = h->dfTab;
+    cp.gscale = h->gscale;
     return cp;
 }
 
@@ -215,18 +225,24 @@ kl_status forward_impl(kl_handle h, const double* v, int64_t ldv, double* u, int
 
 kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, double* z, int64_t ldz,
                      int nvec, bool withJ, cudaStream_t s) {
-    KL_TRY(ensure_apply_ws(h, nvec, precision == KL_P_FP32 || precision == KL_P_TC32));
+    KL_TRY(ensure_apply_ws(h, nvec, precision == KL_P_FP32 || precision == KL_P_TC32, precision == KL_P_TC64));
     CovParams cp = cov_params(h);
     const double s2 = h->kernel.sigma * h->kernel.sigma;
     const double* J = withJ ? h->dJ : nullptr;
     cudaError_t e;
+    if (precision == KL_P_TC64) {
+        e = launch_covmv_tc64(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr), h->w_tcimg.ptr,
+                              h->dStatus, s);
+        if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (tensor cores, float64 class)");
+        return KL_OK;
+    }
     if (precision == KL_P_TC32) {
         float* uf = static_cast<float*>(h->w_f32a.ptr);
         const int64_t ld = stride_of(h);
         e = launch_to_float(u, ldu, uf, ld, h->Nt, nvec, s);
         if (e == cudaSuccess)
             e = launch_covmv_tc(cp, uf, ld, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr),
-                                covmv_tc_splits(h->Nt), h->dStatus, s);
+                                h->w_tcimg.ptr, h->dStatus, s);
         if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (tensor cores)");
         return KL_OK;
     }
@@ -292,7 +308,7 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
                      cudaStream_t s) {
     if (nvec == 0) return KL_OK;
     const bool fp32 = (precision == KL_P_FP32 || precision == KL_P_TC32);
-    KL_TRY(ensure_apply_ws(h, nvec, fp32));
+    KL_TRY(ensure_apply_ws(h, nvec, fp32, precision == KL_P_TC64));
     const int64_t ld = stride_of(h);
     double* A = static_cast<double*>(h->w_a.ptr);
     double* B = static_cast<double*>(h->w_b.ptr);
@@ -304,12 +320,14 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
         KL_TRY(forward_generic<double, double>(h, v, ldv, u, ld, nvec, h->dCt, h->dJ, A, B, s));
         double* z = (u == A) ? B : A;
         int slot;
-        const bool df = (precision == KL_P_DF64);
-        KL_TRY(prof_begin(h, df ? KL_P_DF64 : KL_P_FP64, nvec, s, &slot));
-        cudaError_t e = df ? launch_covmv_df(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                             covmv_df_splits(h->Nt), s)
-                           : launch_covmv64_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                            covmv_splits(h->Nt, nvec, false), s);
+        KL_TRY(prof_begin(h, precision, nvec, s, &slot));
+        double* part = static_cast<double*>(h->w_part.ptr);
+        cudaError_t e =
+            (precision == KL_P_DF64)   ? launch_covmv_df(cp, u, ld, nvec, z, ld, s2, h->dJ, part, covmv_df_splits(h->Nt), s)
+            : (precision == KL_P_TC64) ? launch_covmv_tc64(cp, u, ld, nvec, z, ld, s2, h->dJ, part, h->w_tcimg.ptr,
+                                                           h->dStatus, s)
+                                       : launch_covmv64_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, part,
+                                                            covmv_splits(h->Nt, nvec, false), s);
         if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp64)");
         KL_TRY(prof_end(h, slot, s));
         double* other = (z == A) ? B : A;
@@ -325,7 +343,7 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
     KL_TRY(prof_begin(h, KL_P_FP32, nvec, s, &slot));
     cudaError_t e = (precision == KL_P_TC32)
                         ? launch_covmv_tc(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                          covmv_tc_splits(h->Nt), h->dStatus, s)
+                                          h->w_tcimg.ptr, h->dStatus, s)
                         : launch_covmv32_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
                                              covmv_splits(h->Nt, nvec, true), s);
     if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp32)");
@@ -418,6 +436,20 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         s64 = 1.0 / L;
         s32 = sqrt(log2e) / L;
     }
+    // power of two bounding |Gamma| for the slicing of the tensor-core float64-class path:
+    // |prod_d (1 + x_d x'_d)^m| <= prod_d (1 + max x_d^2)^m; the other kernels are <= 1
+    h->gscale = 1.f;
+    if (kind == KL_K_POLY_TEST) {
+        double bound = 1.0;
+        for (int c = 0; c < 3; ++c) {
+            double mx = 0.0;
+            for (int64_t i = 0; i < Nt; ++i) mx = fmax(mx, fabs(h->X_host[size_t(i) * 3 + c]));
+            bound *= pow(1.0 + mx * mx, double(int(L)));
+        }
+        int e = 0;
+        frexp(bound, &e);
+        h->gscale = float(ldexp(1.0, -e));
+    }
     std::vector<double> P(size_t(Nt) * 3);
     std::vector<float> Pf(size_t(Nt) * 3);
     for (int c = 0; c < 3; ++c)
@@ -508,9 +540,9 @@ kl_status kl_dims(kl_handle h, int* n, int* ntilde) {
 kl_status kl_apply_prec(kl_handle h, int precision, const double* v_dev, double* y_dev, int nvec, int64_t ldv,
                         void* stream) {
     KL_TRY(check_block(h, v_dev, y_dev, nvec, ldv, h ? h->N : 0, ldv, h ? h->N : 0));
-    if (precision < KL_P_FP64 || precision > KL_P_TC32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    if (precision < KL_P_FP64 || precision > KL_P_TC64) return fail(KL_ERR_INVALID_ARG, "unknown precision");
     KL_TRY(apply_impl(h, precision, v_dev, ldv, y_dev, ldv, nvec, static_cast<cudaStream_t>(stream)));
-    if (precision == KL_P_TC32) return check_device_status(h, static_cast<cudaStream_t>(stream));
+    if (precision == KL_P_TC32 || precision == KL_P_TC64) return check_device_status(h, static_cast<cudaStream_t>(stream));
     return KL_OK;
 }
 
@@ -528,10 +560,10 @@ kl_status kl_forward(kl_handle h, const double* v_dev, int64_t ldv, double* u_de
 kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu, double* z_dev, int64_t ldz,
                    int nvec, void* stream) {
     KL_TRY(check_block(h, u_dev, z_dev, nvec, ldu, h ? h->Nt : 0, ldz, h ? h->Nt : 0));
-    if (precision < KL_P_FP64 || precision > KL_P_TC32) return fail(KL_ERR_INVALID_ARG, "unknown precision");
+    if (precision < KL_P_FP64 || precision > KL_P_TC64) return fail(KL_ERR_INVALID_ARG, "unknown precision");
     if (nvec == 0) return KL_OK;
     KL_TRY(covmv_impl(h, precision, u_dev, ldu, z_dev, ldz, nvec, false, static_cast<cudaStream_t>(stream)));
-    if (precision == KL_P_TC32) return check_device_status(h, static_cast<cudaStream_t>(stream));
+    if (precision == KL_P_TC32 || precision == KL_P_TC64) return check_device_status(h, static_cast<cudaStream_t>(stream));
     return KL_OK;
 }
 
@@ -617,6 +649,7 @@ void kl_destroy(kl_handle h) {
     release(h->w_f32a);
     release(h->w_f32b);
     release(h->w_part);
+    release(h->w_tcimg);
     for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
     delete h;
 }

@@ -20,39 +20,7 @@ constexpr int kDfTile = 128;
 
 using df::F2;
 
-__device__ __forceinline__ F2 diff(float ah, float al, float bh, float bl) {
-    F2 s = df::two_sum(ah, -bh);
-    float e = df::add(s.l, df::sub(al, bl));
-    return df::fast_two_sum(s.h, e);
-}
-
-template <int KIND>
-__device__ __forceinline__ F2 kernel_df(const float* r, const float* c, int pm, const float* th,
-                                        const float* tl) {
-    // r, c: {xh, yh, zh, xl, yl, zl} of the row and column point
-    if (KIND == KL_K_POLY_TEST) {
-        F2 f{1.f, 0.f};
-        for (int k = 0; k < 3; ++k) {
-            F2 p = df::mul(F2{r[k], r[3 + k]}, F2{c[k], c[3 + k]});
-            f = df::mul(f, df::add(p, F2{1.f, 0.f}));
-        }
-        F2 g{1.f, 0.f};
-        for (int i = 0; i < pm; ++i) g = df::mul(g, f);
-        return g;
-    }
-    const F2 dx = diff(r[0], r[3], c[0], c[3]);
-    const F2 dy = diff(r[1], r[4], c[1], c[4]);
-    const F2 dz = diff(r[2], r[5], c[2], c[5]);
-    if (KIND == KL_K_EXP_SEPARABLE) {
-        F2 s = df::add(df::add(df::abs(dx), df::abs(dy)), df::abs(dz));
-        return df::exp_neg(s, th, tl);
-    }
-    F2 s = df::add(df::add(df::sqr(dx), df::sqr(dy)), df::sqr(dz));
-    if (KIND == KL_K_GAUSS) return df::exp_neg(s, th, tl);
-    float seed;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(seed) : "f"(fmaxf(s.h, 1e-30f)));
-    return df::exp_neg(df::sqrt(s, seed), th, tl);
-}
+using df::kernel_df;
 
 template <int KIND, int NV>
 __global__ void __launch_bounds__(kDfThreads)

@@ -19,103 +19,87 @@
 // reports KL_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 
+#include "tc_common.cuh"
+
+// Stage 5 of Algorithm 1 as a tensor-core block contraction (tcgen05, sm_103a) for groups of up
+// to 32 right-hand sides: z = Gamma u, with Gamma generated tile by tile in registers and never
+// stored in global memory.
+//
+// Work decomposition.  Rows come in blocks of 128 (the MMA M dimension), columns in chunks of 32;
+// a (row block, column chunk) pair is a tile.  The tiles, ordered row block by row block, are cut
+// into one contiguous range per CTA (persistent grid of resident CTAs), so every CTA does the same
+// number of tiles; a range covers at most a few row blocks ("segments").  Each segment's sums go
+// to a partial slot, and a fixed-order reduction adds the slots of a row block.
+//
+// Per CTA, three roles run as a pipeline over shared-memory stages, synchronised by mbarriers:
+//   * loader (one thread): one bulk copy per chunk of a pre-staged image holding the 32 column
+//     coordinates and the u chunk already split into bfloat16 terms (written by tc_image_kernel);
+//   * producers (eight warps, two threads per row, 16 columns each): evaluate float32 kernel
+//     values (MUFU rsqrt/ex2, as in the scalar float32 kernel), split each into three bfloat16
+//     terms by truncation (g = g1 + g2 + g3 exactly), and write them K-major to shared memory;
+//   * MMA issuer (one thread): six tcgen05.mma per 16 columns (kind::f16, bf16 x bf16, float32
+//     accumulation in tensor memory) for the term products g_a u_b with a + b <= 4 (1-based),
+//     which reproduce float32 products to ~2^-24, then tcgen05.commit to free the stage.
+// At a segment end the producers read their accumulator lanes with tcgen05.ld; tensor memory holds
+// four accumulator buffers so the next segment starts without waiting for that read.
+//
+// Every wait is bounded: after ~2 s of spinning a role records an error in a device status word,
+// drains the asynchronous operations it started (again bounded), and the CTA releases its tensor
+// memory and returns; the launcher's caller reports KL_ERR_TIMEOUT.
 #include "kl_internal.h"
 
 namespace kl {
 namespace {
 
-constexpr int kTcRows = 128;     // MMA M
-constexpr int kTcN = 16;         // MMA N: vectors per launch group
-constexpr int kTcK = 16;         // MMA K for 16-bit inputs
-constexpr int kTcChunk = 32;     // columns per pipeline stage (2 MMA K-steps)
-constexpr int kTcThreads = 128;
-constexpr int kTcPieces = 3;     // bfloat16 terms per float32 value
-constexpr int kTcTmemCols = 32;  // allocation granule (>= N)
+using namespace tc;
 
-// shared-memory layout (bytes), canonical K-major, no swizzle: core matrices of 8 rows x 16 bytes
-constexpr int kASub = kTcRows * kTcK * 2;                 // one 128 x 16 bf16 sub-tile: 4 KB
-constexpr int kAPiece = kASub * (kTcChunk / kTcK);        // one piece of a chunk: 8 KB
-constexpr int kAStage = kAPiece * kTcPieces;              // 24 KB
-constexpr int kBSub = kTcN * kTcK * 2;                    // 16 x 16 bf16: 512 B
-constexpr int kBPiece = kBSub * (kTcChunk / kTcK);        // 1 KB
-constexpr int kBStage = kBPiece * kTcPieces;              // 3 KB
+constexpr int kTcRows = 128;                      // MMA M (rows per block)
+constexpr int kTcK = 16;                          // MMA K for 16-bit inputs
+constexpr int kTcChunk = 32;                      // columns per pipeline stage (2 K-steps)
+constexpr int kTcStages = 3;                      // shared-memory stages
+constexpr int kTcNB = 32;                         // MMA N: vectors per group
+constexpr int kTcNBuf = 4;                        // accumulator buffers in tensor memory
+constexpr int kTcTmemCols = kTcNB * kTcNBuf;      // 128 columns (power of two >= 32)
+constexpr int kTcProducers = 256;                 // warps 0-7: two threads per row, 16 columns each
+constexpr int kTcThreads = kTcProducers + 64;     // + loader warp 8 + MMA warp 9
+constexpr int kTcLoaderWarp = kTcProducers / 32;
+constexpr int kTcMmaWarp = kTcLoaderWarp + 1;
+constexpr int kTcPieces = 3;                      // bfloat16 terms per float32 value
+
+// shared-memory layout (bytes); operand tiles are canonical K-major without swizzle: core
+// matrices of 8 rows x 16 bytes, 256 bytes between 8-row groups, 128 bytes between 8-column halves
+constexpr int kASub = kTcRows * kTcK * 2;                  // 128 x 16 bf16: 4 KB
+constexpr int kAPiece = kASub * (kTcChunk / kTcK);         // 8 KB
+constexpr int kAStage = kAPiece * kTcPieces;               // 24 KB
+constexpr int kBSub = kTcNB * kTcK * 2;                    // 32 x 16 bf16: 1 KB
+constexpr int kBPiece = kBSub * (kTcChunk / kTcK);         // 2 KB
+constexpr int kCoordBytes = 3 * kTcChunk * 4;              // x[32], y[32], z[32] floats
+constexpr int kImg = kCoordBytes + kBPiece * kTcPieces;    // one chunk image: 6528 B
 constexpr int kOffA = 0;
-constexpr int kOffB = 2 * kAStage;                        // 48 KB
-constexpr int kOffC = kOffB + 2 * kBStage;                // column points: 2 stages x 32 float4
-constexpr int kOffBar = kOffC + 2 * kTcChunk * 16;        // 2 mbarriers
-constexpr int kOffTmem = kOffBar + 16;
+constexpr int kOffImg = kOffA + kTcStages * kAStage;
+constexpr int kOffBar = kOffImg + kTcStages * kImg;
+constexpr int kBarLoaded = 0;                              // per stage: image copy landed (tx count)
+constexpr int kBarFull = kTcStages;                        // per stage: one arrival per producer
+constexpr int kBarEmpty = 2 * kTcStages;                   // per stage: MMAs done reading (commit)
+constexpr int kBarSegDone = 3 * kTcStages;                 // per buffer: segment accumulated (commit)
+constexpr int kBarTmemFree = 3 * kTcStages + kTcNBuf;      // per buffer: every producer read it
+constexpr int kNumBars = 3 * kTcStages + 2 * kTcNBuf;
+constexpr int kOffTmem = kOffBar + 8 * kNumBars;
 constexpr int kSmemBytes = kOffTmem + 16;
+constexpr uint32_t kIdesc = idesc_bf16(kTcRows, kTcNB);
+static_assert(kImg % 16 == 0 && kOffImg % 16 == 0 && kOffBar % 8 == 0, "bulk-copy and mbarrier alignment");
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+// g = hi + mid + lo exactly, each term a bfloat16 (the upper 16 bits of the returned words):
+// truncation keeps the leading 8 significant bits, and both subtractions are exact
+__device__ __forceinline__ void split3(float g, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+    w0 = __float_as_uint(g) & 0xFFFF0000u;
+    const float r1 = g - __uint_as_float(w0);
+    w1 = __float_as_uint(r1) & 0xFFFF0000u;
+    w2 = __float_as_uint(r1 - __uint_as_float(w1));
 }
 
-// byte offset of element (row r, k) inside a K-major no-swizzle tile of 16-column sub-tiles
-__device__ __forceinline__ int kmajor_offset(int r, int k, int sub_bytes) {
-    const int t = k / kTcK, kk = k % kTcK;
-    return t * sub_bytes + (r >> 3) * 256 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2;
-}
-
-// tcgen05 shared-memory matrix descriptor: start address, leading (K-direction) and stride
-// (M/N-direction) byte offsets between core matrices, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= uint64_t((saddr >> 4) & 0x3FFF);
-    d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
-    d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
-    d |= uint64_t(1) << 46;
-    return d;
-}
-
-// instruction descriptor, kind::f16: D float32, A and B bfloat16, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTcN >> 3) << 17) |
-                            (uint32_t(kTcRows >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        :
-        : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait for the phase with the given parity; false on timeout (~2 s at 2 GHz)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 4000000000ll) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void split3(float x, __nv_bfloat16* p) {
-    const __nv_bfloat16 a = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(a);
-    const __nv_bfloat16 b = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(b);
-    p[0] = a;
-    p[1] = b;
-    p[2] = __float2bfloat16_rn(r2);
-}
+// two bfloat16 (upper halves of a and b) packed as elements (k, k+1)
+__device__ __forceinline__ uint32_t pack_bf16(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
 
 template <int KIND>
 __device__ __forceinline__ float kernel_tc(float dx, float dy, float dz, float x0, float y0, float z0, float x1,
@@ -141,217 +125,314 @@ __device__ __forceinline__ float kernel_tc(float dx, float dy, float dz, float x
     }
 }
 
+// The image of column chunk ch: the chunk's coordinates (x[32], y[32], z[32], zero past Ntilde)
+// and the group's u values split into three bfloat16 terms, in the K-major operand layout the
+// MMA reads (rows = vectors, zero past nv and past Ntilde).  128 threads per chunk.
+__global__ void tc_image_kernel(const float* __restrict__ P, int64_t ldp, int64_t Nt, const float* __restrict__ U,
+                                int64_t ldu, int nv, unsigned char* __restrict__ img, int64_t nchunks) {
+    const int t = threadIdx.x;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        unsigned char* base = img + ch * kImg;
+        const int64_t c0 = ch * kTcChunk;
+        if (t < 3 * kTcChunk) {
+            const int64_t c = c0 + (t % kTcChunk);
+            reinterpret_cast<float*>(base)[t] = c < Nt ? P[int64_t(t / kTcChunk) * ldp + c] : 0.f;
+        }
+        const int v = t / (kTcChunk / 8), g8 = t % (kTcChunk / 8);
+        uint32_t w[kTcPieces][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const int64_t ca = c0 + g8 * 8 + e, cb = ca + 1;
+            const float ua = (v < nv && ca < Nt) ? U[v * ldu + ca] : 0.f;
+            const float ub = (v < nv && cb < Nt) ? U[v * ldu + cb] : 0.f;
+            uint32_t a0, a1, a2, b0, b1, b2;
+            split3(ua, a0, a1, a2);
+            split3(ub, b0, b1, b2);
+            w[0][e / 2] = pack_bf16(a0, b0);
+            w[1][e / 2] = pack_bf16(a1, b1);
+            w[2][e / 2] = pack_bf16(a2, b2);
+        }
+#pragma unroll
+        for (int q = 0; q < kTcPieces; ++q)
+            *reinterpret_cast<uint4*>(base + kCoordBytes + q * kBPiece + kmajor_offset(v, g8 * 8, kBSub)) =
+                make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+    }
+}
+
+// Persistent tile-range kernel (see the file comment).  len = column chunks per row block,
+// T = row blocks x len; the partial sums of segment `seg` of CTA b go to slot b * maxseg + seg as
+// [kTcNB][128] doubles (only v < nv and rows < Ntilde written).
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads)
-covmv_tc_kernel(CovParams cp, const float* __restrict__ U, int64_t ldu, int nv, double* __restrict__ part,
-                int64_t cols_per_split, int* __restrict__ status) {
+covmv_tc_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, double* __restrict__ part, int64_t len,
+                int64_t T, int maxseg, int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + kOffBar, bar1 = sbase + kOffBar + 8;
+    const uint32_t bar0 = sbase + kOffBar;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffTmem);
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+        for (int st = 0; st < kTcStages; ++st) {
+            mbar_init(bar0 + 8 * (kBarLoaded + st), 1);
+            mbar_init(bar0 + 8 * (kBarFull + st), kTcProducers);
+            mbar_init(bar0 + 8 * (kBarEmpty + st), 1);
+        }
+        for (int bf = 0; bf < kTcNBuf; ++bf) {
+            mbar_init(bar0 + 8 * (kBarSegDone + bf), 1);
+            mbar_init(bar0 + 8 * (kBarTmemFree + bf), kTcProducers);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTcTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    if (warp == kTcMmaWarp) {
+        tmem_alloc(smem_u32(tmem_slot), kTcTmemCols);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
+    const int64_t G = gridDim.x;
+    const int64_t t0 = tile_begin(blockIdx.x, T, G);
+    const int ntiles = int(tile_begin(int64_t(blockIdx.x) + 1, T, G) - t0);
     const int64_t Nt = cp.Nt;
-    const float* P = cp.P32;
-    const int64_t row = int64_t(blockIdx.x) * kTcRows + tid;
-    const bool rvalid = row < Nt;
-    const float x0 = rvalid ? P[row] : 0.f, y0 = rvalid ? P[cp.ldp + row] : 0.f, z0 = rvalid ? P[2 * cp.ldp + row] : 0.f;
-
-    const int64_t c_begin = int64_t(blockIdx.y) * cols_per_split;
-    int64_t c_end = c_begin + cols_per_split;
-    if (c_end > Nt) c_end = Nt;
-    const int nchunks = int((c_end - c_begin + kTcChunk - 1) / kTcChunk);
-
     bool ok = true;
-    for (int it = 0; it < nchunks; ++it) {
-        const int s = it & 1;
-        const uint32_t bar = s ? bar1 : bar0;
-        if (it >= 2 && ok) ok = mbar_wait(bar, uint32_t(((it - 2) >> 1) & 1));
-        const int64_t c0 = c_begin + int64_t(it) * kTcChunk;
-        float4* cst = reinterpret_cast<float4*>(smem + kOffC) + s * kTcChunk;
-        if (tid < kTcChunk) {
-            const int64_t c = c0 + tid;
-            cst[tid] = (c < c_end) ? make_float4(P[c], P[cp.ldp + c], P[2 * cp.ldp + c], 0.f)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        // u chunk -> B pieces: thread t handles vector v = t / 8 and the 8-column group t % 8 ... but
-        // the chunk has 32 columns = 4 groups of 8 for each of 16 vectors = 64 items for 128 threads
-        unsigned char* Bst = smem + kOffB + s * kBStage;
-        if (tid < kTcN * (kTcChunk / 8)) {
-            const int v = tid / (kTcChunk / 8), g8 = tid % (kTcChunk / 8);
-            __align__(16) __nv_bfloat16 pc[kTcPieces][8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int64_t c = c0 + g8 * 8 + e;
-                const float u = (v < nv && c < c_end) ? U[v * ldu + c] : 0.f;
-                __nv_bfloat16 t3[3];
-                split3(u, t3);
-                pc[0][e] = t3[0];
-                pc[1][e] = t3[1];
-                pc[2][e] = t3[2];
+
+    if (warp < kTcLoaderWarp) {
+        // ------------------------------ producers ------------------------------
+        const int r = tid & (kTcRows - 1), half = tid / kTcRows;   // row in block, column half
+        int seg = 0;
+        int64_t rb = -1;
+        float x0 = 0.f, y0 = 0.f, z0 = 0.f;
+        for (int i = 0; i < ntiles; ++i) {
+            const int64_t t = t0 + i;
+            if (t / len != rb) {
+                rb = t / len;
+                const int64_t row = rb * kTcRows + r;
+                const bool rv = row < Nt;
+                x0 = rv ? cp.P32[row] : 0.f;
+                y0 = rv ? cp.P32[cp.ldp + row] : 0.f;
+                z0 = rv ? cp.P32[2 * cp.ldp + row] : 0.f;
             }
+            const int st = i % kTcStages;
+            ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarLoaded + st), uint32_t((i / kTcStages) & 1)));
+            if (!ok) break;
+            const float* cx = reinterpret_cast<const float*>(smem + kOffImg + st * kImg);
+            unsigned char* As = smem + kOffA + st * kAStage;
 #pragma unroll
-            for (int q = 0; q < kTcPieces; ++q)
-                *reinterpret_cast<uint4*>(Bst + q * kBPiece + kmajor_offset(v, g8 * 8, kBSub)) =
-                    *reinterpret_cast<const uint4*>(pc[q]);
-        }
-        __syncthreads();
-        // kernel values of this thread's row for the 32 columns -> A pieces
-        unsigned char* Ast = smem + kOffA + s * kAStage;
-#pragma unroll 1
-        for (int g8 = 0; g8 < kTcChunk / 8; ++g8) {
-            __align__(16) __nv_bfloat16 pc[kTcPieces][8];
+            for (int gg = 0; gg < 2; ++gg) {
+                const int g8 = half * 2 + gg;
+                const float4 xa = *reinterpret_cast<const float4*>(cx + g8 * 8);
+                const float4 xb = *reinterpret_cast<const float4*>(cx + g8 * 8 + 4);
+                const float4 ya = *reinterpret_cast<const float4*>(cx + kTcChunk + g8 * 8);
+                const float4 yb = *reinterpret_cast<const float4*>(cx + kTcChunk + g8 * 8 + 4);
+                const float4 za = *reinterpret_cast<const float4*>(cx + 2 * kTcChunk + g8 * 8);
+                const float4 zb = *reinterpret_cast<const float4*>(cx + 2 * kTcChunk + g8 * 8 + 4);
+                const float xs[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+                const float ys[8] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+                const float zs[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+                uint32_t w[kTcPieces][4];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float4 q = cst[g8 * 8 + e];
-                const float g = kernel_tc<KIND>(x0 - q.x, y0 - q.y, z0 - q.z, x0, y0, z0, q.x, q.y, q.z, cp.poly_m);
-                __nv_bfloat16 t3[3];
-                split3(g, t3);
-                pc[0][e] = t3[0];
-                pc[1][e] = t3[1];
-                pc[2][e] = t3[2];
+                for (int e = 0; e < 8; e += 2) {
+                    const float ga = kernel_tc<KIND>(x0 - xs[e], y0 - ys[e], z0 - zs[e], x0, y0, z0, xs[e], ys[e],
+                                                     zs[e], cp.poly_m);
+                    const float gb = kernel_tc<KIND>(x0 - xs[e + 1], y0 - ys[e + 1], z0 - zs[e + 1], x0, y0, z0,
+                                                     xs[e + 1], ys[e + 1], zs[e + 1], cp.poly_m);
+                    uint32_t a0, a1, a2, b0, b1, b2;
+                    split3(ga, a0, a1, a2);
+                    split3(gb, b0, b1, b2);
+                    w[0][e / 2] = pack_bf16(a0, b0);
+                    w[1][e / 2] = pack_bf16(a1, b1);
+                    w[2][e / 2] = pack_bf16(a2, b2);
+                }
+#pragma unroll
+                for (int q = 0; q < kTcPieces; ++q)
+                    *reinterpret_cast<uint4*>(As + q * kAPiece + kmajor_offset(r, g8 * 8, kASub)) =
+                        make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
             }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(bar0 + 8 * (kBarFull + st));
+            if (i == ntiles - 1 || (t + 1) % len == 0) {
+                // segment end: read this row's accumulators (vectors half*16 .. half*16+15)
+                const int bf = seg % kTcNBuf;
+                ok = __all_sync(0xffffffffu,
+                                mbar_wait(bar0 + 8 * (kBarSegDone + bf), uint32_t((seg / kTcNBuf) & 1)));
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                uint32_t d[16];
+                const uint32_t taddr =
+                    tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(bf * kTcNB + half * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];\n"
+                    : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+                      "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]),
+                      "=r"(d[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                mbar_arrive(bar0 + 8 * (kBarTmemFree + bf));
+                if (rb * kTcRows + r < Nt) {
+                    double* slot = part + (int64_t(blockIdx.x) * maxseg + seg) * (int64_t(kTcNB) * kTcRows) + r;
 #pragma unroll
-            for (int q = 0; q < kTcPieces; ++q)
-                *reinterpret_cast<uint4*>(Ast + q * kAPiece + kmajor_offset(tid, g8 * 8, kASub)) =
-                    *reinterpret_cast<const uint4*>(pc[q]);
+                    for (int j = 0; j < 16; ++j)
+                        if (half * 16 + j < nv) slot[(half * 16 + j) * kTcRows] = double(__uint_as_float(d[j]));
+                }
+                ++seg;
+            }
         }
-        // make the generic-proxy shared-memory writes visible to the tensor core (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0 && ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = sbase + kOffA + s * kAStage, b0 = sbase + kOffB + s * kBStage;
-            // products of pieces (a, b) with a + b <= 2 (0-based): g1u1, g1u2, g2u1, g1u3, g2u2, g3u1
-            const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+    } else if (warp == kTcLoaderWarp) {
+        // ------------------------------ loader ------------------------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < ntiles; ++i) {
+                const int st = i % kTcStages;
+                if (i >= kTcStages) {
+                    ok = mbar_wait(bar0 + 8 * (kBarEmpty + st), uint32_t(((i / kTcStages) - 1) & 1));
+                    if (!ok) break;
+                }
+                const int64_t ch = (t0 + i) % len;
+                bulk_load(sbase + kOffImg + st * kImg, img + ch * kImg, kImg, bar0 + 8 * (kBarLoaded + st));
+                issued = i + 1;
+            }
+            if (!ok) {
+                // drain: the last copy issued into each stage must land before the CTA exits
+                for (int i = issued - kTcStages; i < issued; ++i)
+                    if (i >= 0) mbar_wait(bar0 + 8 * (kBarLoaded + i % kTcStages), uint32_t((i / kTcStages) & 1));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            int seg = 0, committed = 0;
+            for (int i = 0; i < ntiles; ++i) {
+                const int64_t t = t0 + i;
+                const int st = i % kTcStages;
+                const uint32_t ph = uint32_t((i / kTcStages) & 1);
+                const bool seg_begin = (i == 0) || (t % len == 0);
+                const bool seg_end = (i == ntiles - 1) || ((t + 1) % len == 0);
+                const int bf = seg % kTcNBuf;
+                if (seg_begin && seg >= kTcNBuf) {
+                    ok = mbar_wait(bar0 + 8 * (kBarTmemFree + bf), uint32_t(((seg / kTcNBuf) - 1) & 1));
+                    if (!ok) break;
+                }
+                ok = mbar_wait(bar0 + 8 * (kBarFull + st), ph);
+                if (!ok) break;
+                ok = mbar_wait(bar0 + 8 * (kBarLoaded + st), ph);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = sbase + kOffA + st * kAStage;
+                const uint32_t b0 = sbase + kOffImg + st * kImg + kCoordBytes;
+                const uint32_t dcol = tmem + uint32_t(bf * kTcNB);
+                // term products (a, b), 0-based, with a + b <= 2
+                const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
-            for (int ks = 0; ks < kTcChunk / kTcK; ++ks) {
+                for (int ks = 0; ks < kTcChunk / kTcK; ++ks) {
 #pragma unroll
-                for (int p = 0; p < 6; ++p) {
-                    const uint64_t ad = make_desc(a0 + pa[p] * kAPiece + ks * kASub, 128, 256);
-                    const uint64_t bd = make_desc(b0 + pb[p] * kBPiece + ks * kBSub, 128, 256);
-                    mma_bf16(tmem, ad, bd, (it > 0 || ks > 0 || p > 0) ? 1u : 0u);
+                    for (int q = 0; q < 6; ++q) {
+                        const uint64_t ad = make_desc(a0 + pa[q] * kAPiece + ks * kASub, 128, 256);
+                        const uint64_t bd = make_desc(b0 + pb[q] * kBPiece + ks * kBSub, 128, 256);
+                        mma_bf16(dcol, ad, bd, kIdesc, (seg_begin && ks == 0 && q == 0) ? 0u : 1u);
+                    }
+                }
+                mma_commit(bar0 + 8 * (kBarEmpty + st));
+                committed = i + 1;
+                if (seg_end) {
+                    mma_commit(bar0 + 8 * (kBarSegDone + bf));
+                    ++seg;
                 }
             }
-            mma_commit(bar);
+            if (!ok && committed > 0) {
+                // drain: a commit tracks every earlier MMA of this thread
+                const int last = committed - 1;
+                mbar_wait(bar0 + 8 * (kBarEmpty + last % kTcStages), uint32_t((last / kTcStages) & 1));
+            }
         }
-    }
-    // wait for the last chunk's MMAs (a commit covers every earlier MMA of the issuing thread)
-    if (nchunks > 0) {
-        const int last = nchunks - 1;
-        const bool done = mbar_wait((last & 1) ? bar1 : bar0, uint32_t((last >> 1) & 1));
-        ok = ok && done;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!ok) {
-        if (lane == 0) atomicExch(status, int(KL_ERR_TIMEOUT));
-    } else if (nchunks > 0) {
-        uint32_t d[16];
-        const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
-            : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
-              "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]), "=r"(d[15])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (rvalid) {
-#pragma unroll
-            for (int v = 0; v < kTcN; ++v)
-                if (v < nv) part[(int64_t(blockIdx.y) * nv + v) * Nt + row] = double(__uint_as_float(d[v]));
-        }
-    } else if (rvalid) {
-        for (int v = 0; v < nv; ++v) part[(int64_t(blockIdx.y) * nv + v) * Nt + row] = 0.0;
+        __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok && tid == 0) atomicExch(status, int(KL_ERR_TIMEOUT));
+    if (warp == kTcMmaWarp)
+        tmem_dealloc(tmem, kTcTmemCols);
 }
 
-__global__ void tc_reduce(const double* __restrict__ part, int splits, int64_t Nt, int nv, double* __restrict__ Z,
-                          int64_t ldz, double scale2, const double* __restrict__ J) {
-    const int64_t total = Nt * nv;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t v = idx / Nt, r = idx - v * Nt;
-        double s = 0.0;
-        for (int sp = 0; sp < splits; ++sp) s += part[(int64_t(sp) * nv + v) * Nt + r];
-        s *= scale2;
-        if (J) s *= J[r];
-        Z[v * ldz + r] = s;
+cudaError_t set_smem_attr(int kind) {
+    switch (kind) {
+        case KL_K_EXP:
+            return cudaFuncSetAttribute(covmv_tc_kernel<KL_K_EXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemBytes);
+        case KL_K_GAUSS:
+            return cudaFuncSetAttribute(covmv_tc_kernel<KL_K_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemBytes);
+        case KL_K_EXP_SEPARABLE:
+            return cudaFuncSetAttribute(covmv_tc_kernel<KL_K_EXP_SEPARABLE>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        default:
+            return cudaFuncSetAttribute(covmv_tc_kernel<KL_K_POLY_TEST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kSmemBytes);
     }
 }
 
 }  // namespace
 
-int covmv_tc_splits(int64_t Nt) {
-    const int64_t rowblocks = (Nt + kTcRows - 1) / kTcRows;
-    int64_t splits = (152 * 3 * 2 + rowblocks - 1) / rowblocks;
-    int64_t maxs = Nt / (8 * kTcChunk);
-    if (maxs < 1) maxs = 1;
-    if (splits > maxs) splits = maxs;
-    if (splits > 64) splits = 64;
-    if (splits < 1) splits = 1;
-    return int(splits);
+size_t covmv_tc_part_doubles(int64_t Nt) {
+    Schedule sc;
+    if (Nt <= 0 || make_schedule(Nt, kTcRows, kTcChunk, 2, &sc) != cudaSuccess) return 0;
+    return size_t(sc.G) * size_t(sc.maxseg) * kTcNB * kTcRows;
 }
 
+size_t covmv_tc_image_bytes(int64_t Nt) { return size_t((Nt + kTcChunk - 1) / kTcChunk) * kImg; }
+
 cudaError_t launch_covmv_tc(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
-                            double scale2, const double* J, double* part, int splits, int* status,
-                            cudaStream_t s) {
+                            double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s) {
     const int64_t Nt = cp.Nt;
     if (Nt == 0 || nvec == 0) return cudaSuccess;
-    int64_t cps = (Nt + splits - 1) / splits;
-    cps = (cps + kTcChunk - 1) / kTcChunk * kTcChunk;
-    const int used = int((Nt + cps - 1) / cps);
-    dim3 grid(unsigned((Nt + kTcRows - 1) / kTcRows), unsigned(used));
-    static bool attr_done[4] = {false, false, false, false};
-    for (int v0 = 0; v0 < nvec; v0 += kTcN) {
-        const int g = (nvec - v0) < kTcN ? (nvec - v0) : kTcN;
-        const float* Ug = U + int64_t(v0) * ldu;
-        cudaError_t e = cudaSuccess;
-#define KL_TC_CASE(K)                                                                                         \
-    case K:                                                                                                   \
-        if (!attr_done[K]) {                                                                                  \
-            e = cudaFuncSetAttribute(covmv_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes); \
-            if (e != cudaSuccess) return e;                                                                   \
-            attr_done[K] = true;                                                                              \
-        }                                                                                                     \
-        covmv_tc_kernel<K><<<grid, kTcThreads, kSmemBytes, s>>>(cp, Ug, ldu, g, part, cps, status);           \
-        break;
-        switch (cp.kind) {
-            KL_TC_CASE(KL_K_EXP)
-            KL_TC_CASE(KL_K_GAUSS)
-            KL_TC_CASE(KL_K_EXP_SEPARABLE)
-            default:
-                KL_TC_CASE(KL_K_POLY_TEST)
-        }
-#undef KL_TC_CASE
+    Schedule sc;
+    cudaError_t e = make_schedule(Nt, kTcRows, kTcChunk, 2, &sc);
+    if (e != cudaSuccess) return e;
+    e = set_smem_attr(cp.kind);
+    if (e != cudaSuccess) return e;
+    unsigned char* im = static_cast<unsigned char*>(img);
+    const int64_t nchunks = sc.len;
+    const int img_blocks = int(nchunks < 152 * 8 ? nchunks : 152 * 8);
+    for (int v0 = 0; v0 < nvec; v0 += kTcNB) {
+        const int g = (nvec - v0) < kTcNB ? (nvec - v0) : kTcNB;
+        tc_image_kernel<<<img_blocks, 128, 0, s>>>(cp.P32, cp.ldp, Nt, U + int64_t(v0) * ldu, ldu, g, im, nchunks);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        count_launches(2);
-        int64_t tot = Nt * g;
+        const dim3 grid(unsigned(sc.G));
+        switch (cp.kind) {
+            case KL_K_EXP:
+                covmv_tc_kernel<KL_K_EXP><<<grid, kTcThreads, kSmemBytes, s>>>(cp, im, g, part, sc.len, sc.T,
+                                                                               sc.maxseg, status);
+                break;
+            case KL_K_GAUSS:
+                covmv_tc_kernel<KL_K_GAUSS><<<grid, kTcThreads, kSmemBytes, s>>>(cp, im, g, part, sc.len, sc.T,
+                                                                                 sc.maxseg, status);
+                break;
+            case KL_K_EXP_SEPARABLE:
+                covmv_tc_kernel<KL_K_EXP_SEPARABLE><<<grid, kTcThreads, kSmemBytes, s>>>(cp, im, g, part, sc.len,
+                                                                                         sc.T, sc.maxseg, status);
+                break;
+            default:
+                covmv_tc_kernel<KL_K_POLY_TEST><<<grid, kTcThreads, kSmemBytes, s>>>(cp, im, g, part, sc.len, sc.T,
+                                                                                     sc.maxseg, status);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t tot = Nt * g;
         int blocks = int((tot + 255) / 256);
         if (blocks > 152 * 8) blocks = 152 * 8;
-        tc_reduce<<<blocks, 256, 0, s>>>(part, used, Nt, g, Z + int64_t(v0) * ldz, ldz, scale2, J);
+        slot_reduce<kTcRows, kTcNB><<<blocks, 256, 0, s>>>(part, Nt, g, sc.len, sc.T, sc.G, sc.maxseg,
+                                                           Z + int64_t(v0) * ldz, ldz,
+                                         scale2, J);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        count_launches(3);
     }
     return cudaSuccess;
 }

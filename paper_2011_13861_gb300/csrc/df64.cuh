@@ -11,6 +11,8 @@
 
 #if defined(__CUDACC__)
 #include <cuda_runtime.h>
+
+#include "kl.h"
 #else
 #include <cmath>
 #endif
@@ -154,6 +156,44 @@ KL_HD F2 exp_neg(F2 x, const float* tab_h, const float* tab_l) {
 #endif
     return F2{mul(R.h, scale), mul(R.l, scale)};
 }
+
+#if defined(__CUDACC__)
+// ---- kernel values Gamma(x_k, x_l) in double-float (device only) ----
+
+__device__ __forceinline__ F2 diff(float ah, float al, float bh, float bl) {
+    F2 s = two_sum(ah, -bh);
+    float e = add(s.l, sub(al, bl));
+    return fast_two_sum(s.h, e);
+}
+
+template <int KIND>
+__device__ __forceinline__ F2 kernel_df(const float* r, const float* c, int pm, const float* th,
+                                        const float* tl) {
+    // r, c: {xh, yh, zh, xl, yl, zl} of the row and column point
+    if (KIND == KL_K_POLY_TEST) {
+        F2 f{1.f, 0.f};
+        for (int k = 0; k < 3; ++k) {
+            F2 p = mul(F2{r[k], r[3 + k]}, F2{c[k], c[3 + k]});
+            f = mul(f, add(p, F2{1.f, 0.f}));
+        }
+        F2 g{1.f, 0.f};
+        for (int i = 0; i < pm; ++i) g = mul(g, f);
+        return g;
+    }
+    const F2 dx = diff(r[0], r[3], c[0], c[3]);
+    const F2 dy = diff(r[1], r[4], c[1], c[4]);
+    const F2 dz = diff(r[2], r[5], c[2], c[5]);
+    if (KIND == KL_K_EXP_SEPARABLE) {
+        F2 s = add(add(abs(dx), abs(dy)), abs(dz));
+        return exp_neg(s, th, tl);
+    }
+    F2 s = add(add(sqr(dx), sqr(dy)), sqr(dz));
+    if (KIND == KL_K_GAUSS) return exp_neg(s, th, tl);
+    float seed;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(seed) : "f"(fmaxf(s.h, 1e-30f)));
+    return exp_neg(sqrt(s, seed), th, tl);
+}
+#endif
 
 }  // namespace df
 }  // namespace kl

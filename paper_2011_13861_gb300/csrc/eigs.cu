@@ -59,7 +59,7 @@ struct Eig {
     int* Sweeps() { return static_cast<int*>(bSweeps.ptr); }
     int maxparts = 0;
     // statistics
-    int applies = 0, applies64 = 0, appliesdf = 0, block_applies = 0;
+    int applies = 0, applies64 = 0, appliesdf = 0, appliestc64 = 0, block_applies = 0;
     uint64_t rng_offset = 0;
     uint64_t seed = 1;
 
@@ -103,6 +103,7 @@ struct Eig {
         applies += b;
         if (prec == KL_P_FP64) applies64 += b;
         if (prec == KL_P_DF64) appliesdf += b;
+        if (prec == KL_P_TC64) appliestc64 += b;
         block_applies += 1;
         return KL_OK;
     }
@@ -323,8 +324,8 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.polish_ncv = 0;
     o.low_precision = KL_P_FP32;
     if (opts_in) o = *opts_in;
-    if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64)
-        return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64 or KL_P_DF64");
+    if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64 && o.precision != KL_P_TC64)
+        return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64, KL_P_DF64 or KL_P_TC64");
     const int b = std::max(1, o.block);
     if (o.method != 0 && o.method != 1) return fail(KL_ERR_INVALID_ARG, "method must be 0 or 1");
     if (b > 64) return fail(KL_ERR_INVALID_ARG, "block size above 64");
@@ -409,6 +410,9 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
     }
 
+    // a bounded wait that gave up inside a tensor-core kernel invalidates the solve
+    if (o.precision == KL_P_TC64) KL_TRY(check_device_status(h, s));
+
     // ---- outputs ----
     for (int i = 0; i < k; ++i) evals_host[i] = theta[i];
     std::vector<double> resid(k, 0.0);
@@ -438,6 +442,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         info->applies = E.applies;
         info->applies_fp64 = E.applies64;
         info->applies_df64 = E.appliesdf;
+        info->applies_tc64 = E.appliestc64;
         info->block_applies = E.block_applies;
         info->restarts = restarts;
         info->converged = nconv;
@@ -447,6 +452,8 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         info->stage5_calls_fp64 = info->stage5_calls_fp32 = info->stage5_calls_df64 = 0;
         info->ms_stage5_fp64 = info->ms_stage5_fp32 = info->ms_stage5_df64 = 0.0;
         info->pairs_fp64 = info->pairs_fp32 = info->pairs_df64 = 0.0;
+        info->stage5_calls_tc64 = 0;
+        info->ms_stage5_tc64 = info->pairs_tc64 = 0.0;
         const double pairs = double(h->Nt) * double(h->Nt);
         for (const auto& r : h->prof_rec) {
             float ms = 0.f;
@@ -459,6 +466,10 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
                 info->stage5_calls_df64 += 1;
                 info->ms_stage5_df64 += ms;
                 info->pairs_df64 += pairs;
+            } else if (r.kind == KL_P_TC64) {
+                info->stage5_calls_tc64 += 1;
+                info->ms_stage5_tc64 += ms;
+                info->pairs_tc64 += pairs;
             } else {
                 info->stage5_calls_fp32 += 1;
                 info->ms_stage5_fp32 += ms;

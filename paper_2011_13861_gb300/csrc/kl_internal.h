@@ -63,6 +63,7 @@ struct CovParams {
     const double* tab;     // 64-entry table 2^(j/64)
     const float* Pdf;      // 6 x ldp: x, y, z heads then x, y, z tails (double-float coordinates)
     const float* tabdf;    // 2^(-j/64), j = 0..63: 64 heads then 64 tails
+    float gscale = 1.f;    // power of two with gscale * |Gamma| <= 1 (tensor-core float64-class path)
 };
 
 // Stage 5: z[:, v] = scale2 * (J .) sum_l Gamma(x_k, x_l) u[:, v]; partial sums over column
@@ -74,12 +75,19 @@ cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int
                            int64_t ldz, double scale2, const double* J, double* part, int splits,
                            cudaStream_t s);
 int covmv_splits(int64_t Nt, int nvec, bool fp32);
-// tensor-core (tcgen05) float32-accurate stage 5 for blocks of 16; `status` is a device int that
+// tensor-core (tcgen05) float32-accurate stage 5 for groups of 32 vectors; `part` holds
+// covmv_tc_part_doubles doubles, `img` covmv_tc_image_bytes bytes; `status` is a device int that
 // a CTA sets to KL_ERR_TIMEOUT when a bounded wait gives up
 cudaError_t launch_covmv_tc(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
-                            double scale2, const double* J, double* part, int splits, int* status,
-                            cudaStream_t s);
-int covmv_tc_splits(int64_t Nt);
+                            double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
+size_t covmv_tc_part_doubles(int64_t Nt);
+size_t covmv_tc_image_bytes(int64_t Nt);
+// tensor-core float64-class stage 5 (exact bfloat16 slicing, see covmv_tc64.cu) for groups of
+// 32 vectors; `part` holds covmv_tc64_part_doubles doubles, `img` covmv_tc64_image_bytes bytes
+cudaError_t launch_covmv_tc64(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
+                              double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
+size_t covmv_tc64_part_doubles(int64_t Nt);
+size_t covmv_tc64_image_bytes(int64_t Nt);
 cudaError_t launch_covmv32_sym(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z,
                                int64_t ldz, double scale2, const double* J, double* part, int splits,
                                cudaStream_t s);
@@ -145,6 +153,7 @@ struct kl_handle_s {
     int64_t ldw = 0;              // leading dimension of the intermediate tensors (largest stage size)
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     double Jval = 1.0;
+    float gscale = 1.f;       // see CovParams::gscale
     std::vector<double> X_host;  // Nt x 3 row-major physical points
     // device set-up data
     double* dCt[3] = {nullptr, nullptr, nullptr};   // forward operator of mode k, layout n_k x nt_k
@@ -161,7 +170,7 @@ struct kl_handle_s {
     float* dfTab = nullptr;   // 128: double-float 2^(-j/64)
     int* dStatus = nullptr;   // device status word of the kernels with bounded waits (0 = ok)
     // workspace
-    kl::DevBuf w_a, w_b, w_f32a, w_f32b, w_part;
+    kl::DevBuf w_a, w_b, w_f32a, w_f32b, w_part, w_tcimg;
     // stage-5 event timing (enabled by kl_eigs while it runs)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;       // pool, two per record

@@ -17,7 +17,7 @@ from paper_2011_13861_gb300 import inputs
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cube-p2-32^3-exp-L0.5")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64", "tc32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64", "tc32", "tc64"])
     ap.add_argument("--nvec", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--solve", default=None, choices=[None, "plain", "plain_df", "mixed"],
@@ -28,13 +28,16 @@ def main():
     ap.add_argument("--polish-block", type=int, default=0)
     ap.add_argument("--polish-ncv", type=int, default=0)
     ap.add_argument("--low", default="fp32", choices=["fp32", "tc32"])
+    ap.add_argument("--accurate", default="df64", choices=["fp64", "df64", "tc64"],
+                    help="accurate-phase arithmetic of --solve plain_df / mixed")
     a = ap.parse_args()
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     if a.solve:
         method = 1 if a.solve == "mixed" else 0
         block = a.block or (16 if method == 1 else 4)
-        prec = kl.KL_P_FP64 if a.solve == "plain" else kl.KL_P_DF64
+        prec = kl.KL_P_FP64 if a.solve == "plain" else \
+            {"fp64": kl.KL_P_FP64, "df64": kl.KL_P_DF64, "tc64": kl.KL_P_TC64}[a.accurate]
         start = torch.from_numpy(inputs.random_block(G.N, block, seed=1).T.copy()).cuda()
         out = []
         for _ in range(2):
@@ -48,9 +51,11 @@ def main():
             torch.cuda.synchronize()
             out.append(e0.elapsed_time(e1))
         info.pop("resid")
-        print(json.dumps({"workload": a.workload, "solve": a.solve, "block": block, "ms": out, "info": info}))
+        print(json.dumps({"workload": a.workload, "solve": a.solve, "block": block, "accurate": a.accurate,
+                          "ms": out, "info": info}))
         return
-    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32, "df64": kl.KL_P_DF64, "tc32": kl.KL_P_TC32}[a.precision]
+    prec = {"fp64": kl.KL_P_FP64, "fp32": kl.KL_P_FP32, "df64": kl.KL_P_DF64, "tc32": kl.KL_P_TC32,
+            "tc64": kl.KL_P_TC64}[a.precision]
     v = torch.from_numpy(inputs.random_block(G.N, a.nvec, seed=1).T.copy()).cuda()
     u = G.forward(v).reshape(a.nvec, G.Nt).contiguous()
     G.covmv(u, precision=prec)

@@ -45,13 +45,14 @@ def max_sin_angle(A, B):
     return float(np.sqrt(max(0.0, 1.0 - s.min() ** 2)))
 
 
-def check(kl, name, k, method, block, eig_tol, vec_tol=1e-6, tol=1e-8, precision=0):
+def check(kl, name, k, method, block, eig_tol, vec_tol=1e-6, tol=1e-8, precision=0, low_precision=1):
     import torch
     P, lam, Vp = oracle_pairs(name, k)
     w = inputs.WORKLOADS[name]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     start = torch.from_numpy(inputs.random_block(G.N, block, seed=1).T.copy()).cuda()
-    ev, vec, info = G.eigs(k, tol, method=method, block=block, start=start, precision=precision)
+    ev, vec, info = G.eigs(k, tol, method=method, block=block, start=start, precision=precision,
+                           low_precision=low_precision)
     assert np.abs(ev - lam[:k]).max() / lam[0] < eig_tol, (ev, lam[:k])
     assert np.abs((ev - lam[:k]) / lam[:k]).max() < eig_tol * 10
     assert max(info["resid"]) <= tol
@@ -107,3 +108,18 @@ def test_reduced_cube_double_float(kl, method, block):
     residuals are still checked with the float64 operator."""
     info = check(kl, "cube-p2-16^3-exp-L0.5", 20, method=method, block=block, eig_tol=1e-10, precision=2)
     assert info["applies_df64"] > 0
+
+
+@pytest.mark.parametrize("method,block", [(0, 4), (1, 16)])
+def test_reduced_cube_tensor_core_fp64_class(kl, method, block):
+    """Every accurate-phase application on the tensor cores with exact slicing (KL_P_TC64);
+    eigenpairs checked against the oracle and the final residuals with the float64 operator."""
+    info = check(kl, "cube-p2-16^3-exp-L0.5", 20, method=method, block=block, eig_tol=1e-10, precision=4)
+    assert info["applies_tc64"] > 0
+
+
+def test_reduced_cube_all_tensor_core(kl):
+    """Float32 phase and polish both on the tensor cores (KL_P_TC32 then KL_P_TC64)."""
+    info = check(kl, "cube-p2-16^3-exp-L0.5", 20, method=1, block=16, eig_tol=1e-10, precision=4,
+                 low_precision=3)
+    assert info["applies_tc64"] > 0

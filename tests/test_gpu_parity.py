@@ -115,9 +115,45 @@ def test_tensor_core_stage5(kl, case, nvec):
     assert rel(y, P.dense_operator() @ v) < FP32_TOL
 
 
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%dd-%s" % (c[0], c[3]))
+@pytest.mark.parametrize("nvec", [32, 3, 33])
+def test_tensor_core_fp64_class_stage5(kl, case, nvec):
+    """KL_P_TC64: double-float kernel values and float64 u cut into exact bfloat16 slices, slice
+    products summed on the tensor cores; float64 tolerance against the float64 oracle."""
+    import torch
+    P, G = make(kl, case)
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, nvec, seed=41)
+    # one vector with a large dynamic range (per-vector power-of-two scaling)
+    u[:, 0] *= np.exp(np.linspace(-20.0, 5.0, P.Nt))
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=kl.KL_P_TC64).cpu().numpy().T
+    zo = P.stage5(X, u)
+    for v in range(nvec):
+        assert rel(z[:, v], zo[:, v]) < FP64_TOL, v
+    v = inputs.random_block(P.N, nvec, seed=42)
+    y = G.apply(torch.from_numpy(v.T.copy()).cuda(), precision=kl.KL_P_TC64).cpu().numpy().T
+    assert rel(y, P.dense_operator() @ v) < FP64_TOL
+
+
+def test_tensor_core_fp64_class_zero_and_tiny_vectors(kl):
+    """A zero vector gives zero; a vector scaled by 2^-900 gives the scaled product."""
+    import torch
+    P, G = make(kl, CASES[2])
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, 3, seed=43)
+    u[:, 1] = 0.0
+    u[:, 2] *= 2.0 ** -900
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=kl.KL_P_TC64).cpu().numpy().T
+    zo = P.stage5(X, u)
+    assert np.all(z[:, 1] == 0.0)
+    assert rel(z[:, 0], zo[:, 0]) < FP64_TOL
+    assert rel(z[:, 2], zo[:, 2]) < FP64_TOL
+
+
 @pytest.mark.parametrize("nvec", [1, 2, 7, 16, 17, 33])
 def test_block_widths(kl, nvec):
-    """Vector groups of the stage-5 kernels (16 in float64, 32 in float32) and their tails."""
+    """Vector groups of the stage-5 kernels (16 in float64, 32 in float32 and on the tensor cores)
+    and their tails."""
     import torch
     P, G = make(kl, CASES[2])
     v = inputs.random_block(P.N, nvec, seed=nvec)
@@ -125,7 +161,9 @@ def test_block_widths(kl, nvec):
     ref = P.dense_operator() @ v
     assert rel(G.apply(vd).cpu().numpy().T, ref) < FP64_TOL
     assert rel(G.apply(vd, precision=kl.KL_P_DF64).cpu().numpy().T, ref) < FP64_TOL
+    assert rel(G.apply(vd, precision=kl.KL_P_TC64).cpu().numpy().T, ref) < FP64_TOL
     assert rel(G.apply(vd, precision=kl.KL_P_FP32).cpu().numpy().T, ref) < FP32_TOL
+    assert rel(G.apply(vd, precision=kl.KL_P_TC32).cpu().numpy().T, ref) < FP32_TOL
 
 
 def test_deterministic(kl):
