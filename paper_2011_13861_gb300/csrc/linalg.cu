@@ -4,22 +4,30 @@
 // two-stage with a fixed combination order, so repeated runs are bit-identical.
 #include <math.h>
 
+#include "df64.cuh"
 #include "kl_internal.h"
 
 namespace kl {
 namespace {
 
 constexpr int kGramThreads = 256;
-constexpr int kGramRows = 16;
+constexpr int kGramRows = 32;
 constexpr int kGramMaxP = 192;
 constexpr int kGramMaxQ = 32;
 
-// part[g][i*q + j] = sum over this CTA's rows r of A[r, i] * B[r, j]
+// shared-memory row stride for a staged chunk of c columns: odd, so that the rows of a warp's
+// coalesced stores fall into distinct banks
+__host__ __device__ constexpr int gram_ld(int c) { return c | 1; }
+
+// part[g][i*q + j] = sum over this CTA's rows r of A[r, i] * B[r, j]; rows are staged 32 at a
+// time (coalesced along r) and every thread accumulates up to 24 of the p*q outputs
 __global__ void __launch_bounds__(kGramThreads)
 gram_partial(const double* __restrict__ A, int64_t lda, int p, const double* __restrict__ B,
              int64_t ldb, int q, int64_t N, int64_t rows_per_part, double* __restrict__ part) {
-    __shared__ double sA[kGramRows][kGramMaxP + 1];
-    __shared__ double sB[kGramRows][kGramMaxQ + 1];
+    extern __shared__ double sgram[];
+    const int la = gram_ld(p), lb = gram_ld(q);
+    double* sA = sgram;                       // [kGramRows][la]
+    double* sB = sgram + kGramRows * la;      // [kGramRows][lb]
     const int outs = p * q;
     constexpr int kMaxPer = (kGramMaxP * kGramMaxQ + kGramThreads - 1) / kGramThreads;
     double acc[kMaxPer];
@@ -30,12 +38,16 @@ gram_partial(const double* __restrict__ A, int64_t lda, int p, const double* __r
     if (r_end > N) r_end = N;
     for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramRows) {
         __syncthreads();
-        const int rl = threadIdx.x % kGramRows;
-        const int64_t r = r0 + rl;
-        for (int c = threadIdx.x / kGramRows; c < p; c += kGramThreads / kGramRows)
-            sA[rl][c] = (r < r_end) ? A[c * lda + r] : 0.0;
-        for (int c = threadIdx.x / kGramRows; c < q; c += kGramThreads / kGramRows)
-            sB[rl][c] = (r < r_end) ? B[c * ldb + r] : 0.0;
+        for (int e = threadIdx.x; e < kGramRows * p; e += kGramThreads) {
+            const int c = e / kGramRows, rl = e - c * kGramRows;
+            const int64_t r = r0 + rl;
+            sA[rl * la + c] = (r < r_end) ? A[c * lda + r] : 0.0;
+        }
+        for (int e = threadIdx.x; e < kGramRows * q; e += kGramThreads) {
+            const int c = e / kGramRows, rl = e - c * kGramRows;
+            const int64_t r = r0 + rl;
+            sB[rl * lb + c] = (r < r_end) ? B[c * ldb + r] : 0.0;
+        }
         __syncthreads();
 #pragma unroll
         for (int t = 0; t < kMaxPer; ++t) {
@@ -44,7 +56,7 @@ gram_partial(const double* __restrict__ A, int64_t lda, int p, const double* __r
                 const int i = e / q, j = e - i * q;
                 double s = acc[t];
 #pragma unroll 8
-                for (int rr = 0; rr < kGramRows; ++rr) s = fma(sA[rr][i], sB[rr][j], s);
+                for (int rr = 0; rr < kGramRows; ++rr) s = fma(sA[rr * la + i], sB[rr * lb + j], s);
                 acc[t] = s;
             }
         }
@@ -56,43 +68,59 @@ gram_partial(const double* __restrict__ A, int64_t lda, int p, const double* __r
     }
 }
 
-__global__ void gram_reduce(const double* __restrict__ part, int parts, int p, int q,
-                            double* __restrict__ out, int ldo) {
+// out = sum over the parts, 32 outputs per CTA: thread (g, o) adds parts g, g+8, ... of output o
+// (coalesced along o), then the 8 group sums are added in a fixed order
+__global__ void __launch_bounds__(256) gram_reduce(const double* __restrict__ part, int parts, int p, int q,
+                                                   double* __restrict__ out, int ldo) {
+    __shared__ double red[8][33];
     const int outs = p * q;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < outs; e += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int g = 0; g < parts; ++g) s += part[int64_t(g) * outs + e];
+    const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + o;
+    double s = 0.0;
+    if (e < outs)
+        for (int k = g; k < parts; k += 8) s += part[int64_t(k) * outs + e];
+    red[g][o] = s;
+    __syncthreads();
+    if (g == 0 && e < outs) {
+        double t = red[0][o];
+        for (int k = 1; k < 8; ++k) t += red[k][o];
         const int i = e / q, j = e - i * q;
-        out[i + int64_t(j) * ldo] = s;
+        out[i + int64_t(j) * ldo] = t;
     }
 }
 
-// C[r, 0:q] = alpha * A[r, 0:p] B + beta * C[r, 0:q], one row per thread, B in shared memory
+// C[r, j0:j0+QB] = alpha * A[r, 0:p] B[:, j0:j0+QB] + beta * C[r, j0:j0+QB] for every row r and
+// column group j0 (QB columns, the last group zero-padded); items (row, group) with the row
+// fastest, so a warp reads 32 consecutive entries of each column of A; B in shared memory
 template <int QB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 gemm_tall_kernel(double alpha, const double* __restrict__ A, int64_t lda, int64_t N, int p,
                  const double* __restrict__ B, int ldb, int q, double beta, double* __restrict__ C,
                  int64_t ldc) {
-    extern __shared__ double sBm[];   // p x QB
-    for (int e = threadIdx.x; e < p * QB; e += blockDim.x) {
-        const int i = e / QB, j = e - i * QB;
+    extern __shared__ double sBm[];   // p x (ng * QB), row-major
+    const int ng = (q + QB - 1) / QB, lq = ng * QB;
+    for (int e = threadIdx.x; e < p * lq; e += blockDim.x) {
+        const int i = e / lq, j = e - i * lq;
         sBm[e] = (j < q) ? B[i + int64_t(j) * ldb] : 0.0;
     }
     __syncthreads();
-    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < N;
-         r += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t items = N * ng;
+    for (int64_t it = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; it < items;
+         it += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t g = it / N, r = it - g * N;
+        const int j0 = int(g) * QB;
         double acc[QB];
 #pragma unroll
         for (int j = 0; j < QB; ++j) acc[j] = 0.0;
         for (int i = 0; i < p; ++i) {
             const double a = A[i * lda + r];
 #pragma unroll
-            for (int j = 0; j < QB; ++j) acc[j] = fma(a, sBm[i * QB + j], acc[j]);
+            for (int j = 0; j < QB; ++j) acc[j] = fma(a, sBm[i * lq + j0 + j], acc[j]);
         }
 #pragma unroll
         for (int j = 0; j < QB; ++j) {
-            if (j < q) {
-                double* c = C + j * ldc + r;
+            if (j0 + j < q) {
+                double* c = C + (j0 + j) * ldc + r;
                 *c = (beta == 0.0) ? alpha * acc[j] : fma(alpha, acc[j], beta * (*c));
             }
         }
@@ -270,6 +298,136 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
     if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
+// ---- the same parallel cyclic Jacobi in double-float arithmetic (float32 pipe) ----
+// GB300's float64 pipe issues about 1.6 FMAs per clock per SM against ~113 float32 FMAs, so
+// the rotations are applied to double-float (hi + lo) copies of T and of the eigenvector
+// accumulator.  The rotation for a pair comes from a float32 tangent t (the textbook formula),
+// with c = 1/sqrt(1 + t^2) and s = t c formed in double-float so that c^2 + s^2 = 1 to ~2^-48:
+// every rotation is orthogonal to double-float accuracy, and an off-diagonal entry that a
+// rotation leaves at ~2^-24 of its size is removed by the next sweep.  Sweeps stop when no
+// off-diagonal entry exceeds 1e-14 sqrt(|T_aa T_bb|).
+constexpr int kEigDfThreads = 512;
+constexpr int kEigDfMax = 112;
+
+__device__ __forceinline__ df::F2 df_from_double(double x) {
+    const float h = float(x);
+    return df::F2{h, float(x - double(h))};
+}
+
+// (c x - s y, s x + c y) for double-float c, s, x, y
+__device__ __forceinline__ void df_rotate(df::F2 c, df::F2 sn, float& xh, float& xl, float& yh, float& yl) {
+    const df::F2 x{xh, xl}, y{yh, yl};
+    const df::F2 nx = df::sub(df::mul(c, x), df::mul(sn, y));
+    const df::F2 ny = df::add(df::mul(sn, x), df::mul(c, y));
+    xh = nx.h;
+    xl = nx.l;
+    yh = ny.h;
+    yl = ny.l;
+}
+
+__global__ void __launch_bounds__(kEigDfThreads)
+sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restrict__ evals,
+                  double* __restrict__ Sout, int lds, int* sweeps_out) {
+    extern __shared__ float sdf[];
+    const int ld = m | 1;                       // odd stride: column accesses spread over banks
+    float* Th = sdf;                            // T, row-major [m][ld]
+    float* Tl = Th + m * ld;
+    float* Wh = Tl + m * ld;                    // eigenvectors, column-major [m][ld]
+    float* Wl = Wh + m * ld;
+    __shared__ df::F2 cs[kEigDfMax / 2 + 1][2];
+    __shared__ int prs[kEigDfMax / 2 + 1][2];
+    __shared__ int rotated;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e - i * m;
+        const df::F2 v = df_from_double(0.5 * (Tin[i + int64_t(j) * ldt] + Tin[j + int64_t(i) * ldt]));
+        Th[i * ld + j] = v.h;
+        Tl[i * ld + j] = v.l;
+        Wh[j * ld + i] = (i == j) ? 1.f : 0.f;
+        Wl[j * ld + i] = 0.f;
+    }
+    __syncthreads();
+    const int mp = (m % 2 == 0) ? m : m + 1;
+    const int npairs = mp / 2;
+    int sweep = 0;
+    for (; sweep < 40; ++sweep) {
+        if (tid == 0) rotated = 0;
+        __syncthreads();
+        for (int r = 0; r < mp - 1; ++r) {
+            for (int i = tid; i < npairs; i += blockDim.x) {
+                int a, b;
+                rr_pair(i, r, mp, &a, &b);
+                if (a > b) { int t = a; a = b; b = t; }
+                df::F2 c{1.f, 0.f}, sn{0.f, 0.f};
+                if (b < m) {
+                    const float apq = Th[a * ld + b];
+                    const float app = Th[a * ld + a], aqq = Th[b * ld + b];
+                    if (apq != 0.f && fabsf(apq) > 1e-14f * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+                        const df::F2 d = df::sub(df::F2{Th[b * ld + b], Tl[b * ld + b]},
+                                                 df::F2{Th[a * ld + a], Tl[a * ld + a]});
+                        const float theta = d.h / (2.f * apq);
+                        float t;
+                        if (fabsf(theta) > 1e18f) {
+                            t = 0.5f / theta;
+                        } else {
+                            t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f)));
+                        }
+                        // u = 1 + t^2 (|t| <= 1) in double-float; c = 1/sqrt(u); s = t c
+                        const df::F2 t2 = df::two_prod(t, t);
+                        df::F2 u = df::fast_two_sum(1.f, t2.h);
+                        u = df::fast_two_sum(u.h, df::add(u.l, t2.l));
+                        float seed;
+                        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(seed) : "f"(u.h));
+                        const df::F2 su = df::sqrt(u, seed);
+                        const float r0 = 1.f / su.h;
+                        const df::F2 p = df::mul(su, df::F2{r0, 0.f});
+                        const df::F2 e1 = df::sub(df::F2{1.f, 0.f}, p);
+                        c = df::fast_two_sum(r0, r0 * e1.h);
+                        sn = df::mul(df::F2{t, 0.f}, c);
+                        rotated = 1;
+                    }
+                }
+                prs[i][0] = a;
+                prs[i][1] = b;
+                cs[i][0] = c;
+                cs[i][1] = sn;
+            }
+            __syncthreads();
+            // rows: T <- J^T T
+            for (int e = tid; e < npairs * m; e += blockDim.x) {
+                const int i = e / m, j = e - i * m;
+                const int a = prs[i][0], b = prs[i][1];
+                if (b >= m || cs[i][1].h == 0.f) continue;
+                df_rotate(cs[i][0], cs[i][1], Th[a * ld + j], Tl[a * ld + j], Th[b * ld + j], Tl[b * ld + j]);
+            }
+            __syncthreads();
+            // columns: T <- T J ; eigenvectors W <- W J
+            for (int e = tid; e < npairs * m; e += blockDim.x) {
+                const int i = e / m, j = e - i * m;
+                const int a = prs[i][0], b = prs[i][1];
+                if (b >= m || cs[i][1].h == 0.f) continue;
+                df_rotate(cs[i][0], cs[i][1], Th[j * ld + a], Tl[j * ld + a], Th[j * ld + b], Tl[j * ld + b]);
+                df_rotate(cs[i][0], cs[i][1], Wh[a * ld + j], Wl[a * ld + j], Wh[b * ld + j], Wl[b * ld + j]);
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!rotated) break;
+    }
+    // sort descending: rank by (value desc, index asc)
+    for (int i = tid; i < m; i += blockDim.x) {
+        const double di = double(Th[i * ld + i]) + double(Tl[i * ld + i]);
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+            const double dj = double(Th[j * ld + j]) + double(Tl[j * ld + j]);
+            if (dj > di || (dj == di && j < i)) ++rank;
+        }
+        evals[rank] = di;
+        for (int r = 0; r < m; ++r) Sout[r + int64_t(rank) * lds] = double(Wh[i * ld + r]) + double(Wl[i * ld + r]);
+    }
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
 // out[i] = sqrt(s_i^T G s_i), s_i = S[srow0 : srow0 + b, i]
 __global__ void residual_norms_kernel(const double* __restrict__ G, int ldg, const double* __restrict__ S,
                                       int lds, int srow0, int b, int ncols, double* __restrict__ out) {
@@ -380,9 +538,24 @@ int grid_for(int64_t work, int threads, int cap) {
 
 }  // namespace
 
+int num_sms() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) ==
+                                                       cudaSuccess && n > 0)
+            cached = n;
+        else
+            return 152;
+    }
+    return cached;
+}
+
+// two CTAs per SM (all resident at once), at least 64 rows each
 int gram_parts(int64_t N) {
-    int64_t parts = (N + 255) / 256;
-    if (parts > 152 * 2) parts = 152 * 2;
+    int64_t parts = (N + 63) / 64;
+    const int64_t cap = int64_t(num_sms()) * 2;
+    if (parts > cap) parts = cap;
     if (parts < 1) parts = 1;
     return int(parts);
 }
@@ -390,6 +563,7 @@ int gram_parts(int64_t N) {
 cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
                         int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s) {
     if (p > kGramMaxP) return cudaErrorInvalidValue;
+    if (p == 0 || q == 0) return cudaSuccess;
     int parts = gram_parts(N);
     if (parts > maxparts) parts = maxparts;
     int64_t rpp = (N + parts - 1) / parts;
@@ -398,12 +572,16 @@ cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, in
     if (parts < 1) parts = 1;
     for (int j0 = 0; j0 < q; j0 += kGramMaxQ) {
         const int qq = (q - j0 < kGramMaxQ) ? q - j0 : kGramMaxQ;
+        const size_t smem = size_t(kGramRows) * (gram_ld(p) + gram_ld(qq)) * sizeof(double);
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+        }
         count_launches(2);
-        gram_partial<<<parts, kGramThreads, 0, s>>>(A, lda, p, B + int64_t(j0) * ldb, ldb, qq, N, rpp, part);
+        gram_partial<<<parts, kGramThreads, smem, s>>>(A, lda, p, B + int64_t(j0) * ldb, ldb, qq, N, rpp, part);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        gram_reduce<<<grid_for(int64_t(p) * qq, 256, 64), 256, 0, s>>>(part, parts, p, qq,
-                                                                      out + int64_t(j0) * ldo, ldo);
+        gram_reduce<<<(p * qq + 31) / 32, 256, 0, s>>>(part, parts, p, qq, out + int64_t(j0) * ldo, ldo);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -420,28 +598,25 @@ cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t
     }
     for (int j0 = 0; j0 < q; j0 += 32) {
         const int qq = (q - j0 < 32) ? q - j0 : 32;
-        const int QB = qq <= 1 ? 1 : qq <= 4 ? 4 : qq <= 8 ? 8 : qq <= 16 ? 16 : 32;
-        const size_t smem = size_t(p) * QB * sizeof(double);
-        const int blocks = grid_for(N, 256, 152 * 8);
+        const int QB = qq == 1 ? 1 : 4;
+        const int ng = (qq + QB - 1) / QB;
+        const size_t smem = size_t(p) * ng * QB * sizeof(double);
+        const int blocks = grid_for(N * ng, 128, num_sms() * 16);
         const double* Bj = B + int64_t(j0) * ldb;
         count_launches(1);
         double* Cj = C + int64_t(j0) * ldc;
         cudaError_t e = cudaSuccess;
-#define KL_GEMM_CASE(QQ)                                                                        \
-    case QQ:                                                                                    \
-        if (smem > 48 * 1024)                                                                   \
-            e = cudaFuncSetAttribute(gemm_tall_kernel<QQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-        if (e != cudaSuccess) return e;                                                         \
-        gemm_tall_kernel<QQ><<<blocks, 256, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc); \
-        break;
-        switch (QB) {
-            KL_GEMM_CASE(1)
-            KL_GEMM_CASE(4)
-            KL_GEMM_CASE(8)
-            KL_GEMM_CASE(16)
-            KL_GEMM_CASE(32)
+        if (QB == 1) {
+            if (smem > 48 * 1024)
+                e = cudaFuncSetAttribute(gemm_tall_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+            gemm_tall_kernel<1><<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
+        } else {
+            if (smem > 48 * 1024)
+                e = cudaFuncSetAttribute(gemm_tall_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+            gemm_tall_kernel<4><<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
         }
-#undef KL_GEMM_CASE
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -465,6 +640,14 @@ cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64
 cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, double* S, int lds,
                               double* work, int* sweeps_out, cudaStream_t s) {
     if (m > kEigMax || m < 1) return cudaErrorInvalidValue;
+    if (m <= kEigDfMax) {
+        const size_t smem = size_t(4) * m * (m | 1) * sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(sym_eig_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        sym_eig_df_kernel<<<1, kEigDfThreads, smem, s>>>(T, ldt, m, evals, S, lds, sweeps_out);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const size_t smem = size_t(m) * m * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
