@@ -63,16 +63,53 @@ def test_eigenpairs_at_39k_points_against_oracle_operator(kl, cube_exp):
     assert np.abs(ev - ev64).max() / ev64[0] < 1e-10
 
 
+def kronecker_reference(w, k, extra=12):
+    """Top eigenpairs of the separable Gaussian cube from the 1D dense oracle: values mu_a mu_b mu_c
+    and vectors u_c (x) u_b (x) u_a (direction 1 fastest), a few beyond k to close clusters."""
+    P1 = ibq.Problem(1, w["p"], w["ne"], kernel="gauss", L=w["L"])
+    mu, U = np.linalg.eigh(P1.dense_operator())
+    mu, U = mu[::-1], U[:, ::-1]
+    r = 10
+    trip = sorted(((mu[a] * mu[b] * mu[c], a, b, c) for a in range(r) for b in range(r) for c in range(r)),
+                  key=lambda t: -t[0])[:k + extra]
+    vals = np.array([t[0] for t in trip])
+    return vals, trip, U
+
+
+def cluster_angles(vals, trip, U, ev, V, k, rtol=1e-9):
+    """Largest principal-angle sine between each GPU eigenvector cluster and the full oracle
+    eigenspace of that eigenvalue (clusters may extend past index k)."""
+    out = []
+    i = 0
+    while i < k:
+        j = i
+        while j + 1 < k and abs(vals[j + 1] - vals[i]) <= rtol * vals[0]:
+            j += 1
+        members = [t for t in trip if abs(t[0] - vals[i]) <= rtol * vals[0]]
+        Q = np.stack([np.kron(U[:, c], np.kron(U[:, b], U[:, a])) for _, a, b, c in members], axis=1)
+        Q, _ = np.linalg.qr(Q)
+        Vc = V[:, i:j + 1]
+        out.append(float(np.linalg.norm(Vc - Q @ (Q.T @ Vc), 2)))
+        i = j + 1
+    return out
+
+
 def test_gaussian_cube_at_133k_points_kronecker_spectrum(kl):
-    """Unit cube, p=3, 48^3 elements (132,651 points), Gaussian kernel L=0.3: the kernel is a
-    product over coordinates and the map is the identity, so A~' = A~'_3 (x) A~'_2 (x) A~'_1 and the
-    spectrum is every product of three 1D eigenvalues (1D operator from the dense oracle)."""
+    """Unit cube, p=3, 48^3 elements (132,651 points), Gaussian kernel L=0.3, block 16, float32
+    phase then the tensor-core float64-class polish: the kernel is a product over coordinates
+    and the map is the identity, so A~' = A~'_3 (x) A~'_2 (x) A~'_1 and the eigenpairs are products
+    of 1D eigenpairs (1D operator from the dense oracle).  Eigenvalues per mode and principal
+    angles per eigenvalue cluster against that reference."""
     import torch
     w = inputs.WORKLOADS["cube-p3-48^3-gauss-L0.3"]
-    mu = np.linalg.eigvalsh(ibq.Problem(1, w["p"], w["ne"], kernel="gauss", L=w["L"]).dense_operator())[::-1][:20]
-    ref = np.sort(np.einsum("i,j,k->ijk", mu, mu, mu).ravel())[::-1][:20]
+    vals, trip, U = kronecker_reference(w, 20)
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     start = torch.from_numpy(inputs.random_block(G.N, 16, seed=1).T.copy()).cuda()
-    ev, _, info = G.eigs(20, 1e-8, method=1, block=16, start=start, precision=2, want_vectors=False)
+    ev, vec, info = G.eigs(20, 1e-8, method=1, block=16, start=start, precision=kl.KL_P_TC64)
     assert max(info["resid"]) <= 1e-8
-    assert np.abs(ev - ref).max() / ref[0] < 1e-10
+    assert np.abs(ev - vals[:20]).max() / vals[0] < 1e-10
+    angles = cluster_angles(vals, trip, U, ev, vec.cpu().numpy().T, 20)
+    assert max(angles) < 1e-6, angles
+    # the same problem with the double-float polish agrees
+    ev2, _, _ = G.eigs(20, 1e-8, method=1, block=16, start=start, precision=kl.KL_P_DF64, want_vectors=False)
+    assert np.abs(ev2 - vals[:20]).max() / vals[0] < 1e-10
