@@ -57,7 +57,7 @@ class Problem:
     """One discretised KL problem: directions, geometry map and covariance kernel."""
 
     def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None,
-                 lo=None, hi=None):
+                 lo=None, hi=None, geom=None):
         def per_dir(v):
             return list(v) if np.ndim(v) else [v] * dim
         p, ne = per_dir(p), per_dir(ne)
@@ -65,7 +65,10 @@ class Problem:
         net = per_dir(net) if net is not None else [None] * dim
         self.dim = dim
         self.dirs = [Direction(p[k], ne[k], pt[k], net[k]) for k in range(dim)]
-        self.geom = BoxMap(lo if lo is not None else [0.0] * dim, hi if hi is not None else [1.0] * dim)
+        # geometry map F: the affine box map by default, or any object with F(xh) and detDF(xh)
+        # (e.g. a NURBS map, oracle.nurbs.NURBSMap)
+        self.geom = geom if geom is not None else BoxMap(lo if lo is not None else [0.0] * dim,
+                                                         hi if hi is not None else [1.0] * dim)
         self.kernel, self.sigma, self.L = kernel, float(sigma), float(L)
         self.N = int(np.prod([d.n for d in self.dirs]))
         self.Nt = int(np.prod([d.nt for d in self.dirs]))

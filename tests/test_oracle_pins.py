@@ -262,3 +262,98 @@ def test_cube_symmetry_multiplicities():
     P = ibq.Problem(3, 2, 3, kernel="exp", L=0.5)
     w = np.linalg.eigvalsh(P.dense_operator())[::-1][:10]
     assert abs(w[1] - w[2]) / w[0] < 1e-13 and abs(w[2] - w[3]) / w[0] < 1e-13
+
+
+# ---------------------------------------------------------------------------------------------
+# NURBS geometry map (Sec. 2.4) used for the quarter-annulus instances
+# ---------------------------------------------------------------------------------------------
+
+def test_nurbs_basis_derivative_bernstein_closed_form():
+    """On one element (knots 0^{p+1} 1^{p+1}) the B-splines are the Bernstein polynomials and
+    d/dx b_{i,p} = p (b_{i-1,p-1} - b_{i,p-1}); checked against that closed form and against
+    the zero sum of derivatives (partition of unity)."""
+    from math import comb
+    from oracle import nurbs
+    x = np.linspace(0.0, 1.0, 41)
+    for p in (1, 2, 3, 4):
+        t = np.array([0.0] * (p + 1) + [1.0] * (p + 1))
+        dB = nurbs.basis_derivative_matrix(t, p, x)
+
+        def b(i, q):
+            if i < 0 or i > q:
+                return np.zeros_like(x)
+            return comb(q, i) * x ** i * (1 - x) ** (q - i)
+        ref = np.stack([p * (b(i - 1, p - 1) - b(i, p - 1)) for i in range(p + 1)], axis=1)
+        assert np.abs(dB - ref).max() < 1e-12
+        assert np.abs(dB.sum(axis=1)).max() < 1e-12
+
+
+def test_nurbs_basis_derivative_finite_differences_multi_element():
+    from oracle import nurbs
+    t = bspline.open_uniform_knots(3, 5)
+    x = np.linspace(0.013, 0.987, 57)
+    h = 1e-6
+    fd = (bspline.basis_matrix(t, 3, x + h) - bspline.basis_matrix(t, 3, x - h)) / (2 * h)
+    assert np.abs(nurbs.basis_derivative_matrix(t, 3, x) - fd).max() < 1e-6
+
+
+def test_quarter_annulus_exact_geometry_and_volume():
+    """The rational quadratic quarter circle is exact: |(x, y)| = 1 + xh_1 and z = xh_3 to
+    rounding, the angle runs monotonically from 0 to pi/2; DF agrees with central differences
+    and the integral of det DF is the volume 3 pi / 4 (area 3 pi / 4 in 2D)."""
+    from oracle import nurbs
+    rng = np.random.default_rng(7)
+    F = nurbs.quarter_annulus()
+    xh = rng.random((200, 3))
+    X = F(xh)
+    assert np.abs(np.hypot(X[:, 0], X[:, 1]) - (1.0 + xh[:, 0])).max() < 1e-14
+    assert np.abs(X[:, 2] - xh[:, 2]).max() < 1e-14
+    s = np.linspace(0.0, 1.0, 101)
+    ang = np.arctan2(*F(np.stack([0.5 + 0 * s, s, 0 * s], axis=1))[:, 1::-1].T)
+    assert abs(ang[0]) < 1e-14 and abs(ang[-1] - np.pi / 2) < 1e-14 and np.all(np.diff(ang) > 0)
+    h = 1e-6
+    J = F.jacobian(xh)
+    Jfd = np.stack([(F(xh + h * np.eye(3)[j]) - F(xh - h * np.eye(3)[j])) / (2 * h) for j in range(3)], axis=2)
+    assert np.abs(J - Jfd).max() < 1e-8
+    x, w = bspline.gauss_legendre(24)
+    g = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3)
+    ww = np.einsum("i,j,k->ijk", w, w, w).ravel()
+    assert abs((F.detDF(g) * ww).sum() - 0.75 * np.pi) < 1e-12
+    F2 = nurbs.quarter_annulus(dim=2)
+    g2 = np.stack(np.meshgrid(x, x, indexing="ij"), -1).reshape(-1, 2)
+    assert abs((F2.detDF(g2) * np.outer(w, w).ravel()).sum() - 0.75 * np.pi) < 1e-12
+
+
+def test_nurbs_identity_equals_box_map():
+    """A NURBS map whose control net is the degree-1 tensor grid of a box with unit weights is
+    the affine box map: same points, same det DF, same IBQ operator."""
+    from oracle import nurbs
+    lo, hi = np.array([0.0, -1.0]), np.array([2.0, 0.5])
+    t = np.array([0.0, 0.0, 1.0, 1.0])
+    ctrl = np.zeros((2, 2, 2))
+    for j in range(2):
+        for i in range(2):
+            ctrl[j, i] = [lo[0] + (hi[0] - lo[0]) * i, lo[1] + (hi[1] - lo[1]) * j]
+    F = nurbs.NURBSMap([1, 1], [t, t], ctrl, np.ones((2, 2)))
+    Pb = ibq.Problem(2, 2, [5, 4], kernel="gauss", L=0.4, lo=lo, hi=hi)
+    Pn = ibq.Problem(2, 2, [5, 4], kernel="gauss", L=0.4, geom=F)
+    Xb, Jb = Pb.points_and_J()
+    Xn, Jn = Pn.points_and_J()
+    assert np.abs(Xb - Xn).max() < 1e-14 and np.abs(Jb - Jn).max() < 1e-14
+    assert np.abs(Pb.dense_operator() - Pn.dense_operator()).max() < 1e-14
+
+
+def test_ibq_on_quarter_annulus_converges_to_galerkin():
+    """On the curved 2D quarter annulus (J varies from point to point) the IBQ eigenvalues
+    approach the brute-force Galerkin eigenvalues of the same space as the mesh is refined."""
+    from oracle import nurbs
+    F = nurbs.quarter_annulus(dim=2)
+    errs = []
+    for ne in (6, 12):
+        P = ibq.Problem(2, 2, ne, kernel="gauss", L=0.7, geom=F)
+        A, Z = galerkin.galerkin_matrices(P, 6)
+        lg = sla.eigh(A, Z, eigvals_only=True)[::-1][:6]
+        li = np.linalg.eigvalsh(P.dense_operator())[::-1][:6]
+        errs.append(np.abs(li - lg).max() / lg[0])
+    assert errs[1] < errs[0] / 4
+    assert errs[1] < 1e-3
