@@ -53,14 +53,24 @@ typedef enum {
 } kl_status;
 
 /* Geometry map F of the parametric cube [0,1]^d onto the physical domain (Sec. 2.4).
- * KL_GEOM_BOX is the affine map F(x^) = lo + (hi - lo) * x^ (det DF constant). */
-typedef enum { KL_GEOM_BOX = 0 } kl_geom_kind;
+ * KL_GEOM_BOX is the affine map F(x^) = lo + (hi - lo) * x^ (det DF constant).
+ * KL_GEOM_NURBS is a tensor-product NURBS map (Sec. 2.4): F = sum_I N_I w_I P_I / sum_I N_I w_I
+ * over the control records P_I = (x, y, z), weight w_I; the knot vectors must be open on
+ * [0, 1] (the parametric domain of the spline spaces), degree 1..15, weights positive, and
+ * det DF > 0 at every Greville point (KL_ERR_INVALID_ARG otherwise).  The points and
+ * J = sqrt(det DF) are evaluated once on the host in float64; knots and ctrl are host
+ * pointers read during kl_create only. */
+typedef enum { KL_GEOM_BOX = 0, KL_GEOM_NURBS = 1 } kl_geom_kind;
 
 typedef struct {
-    int dim;        /* d = 1, 2 or 3 */
-    int kind;       /* kl_geom_kind */
-    double lo[3];   /* box corner, hi[k] > lo[k] */
+    int dim;                /* d = 1, 2 or 3 */
+    int kind;               /* kl_geom_kind */
+    double lo[3];           /* BOX: corner, hi[k] > lo[k] */
     double hi[3];
+    int deg[3];             /* NURBS: degree per parametric direction k < dim */
+    int nctrl[3];           /* NURBS: control points per direction */
+    const double* knots[3]; /* NURBS: nctrl[k] + deg[k] + 1 knots each */
+    const double* ctrl;     /* NURBS: prod nctrl[k<dim] records (x, y, z, w), direction 1 fastest */
 } kl_geometry;
 
 /* Trial space B_h (degree deg[k], elems[k] uniform elements, C^{deg-1}, Sec. 2.3)

@@ -4,7 +4,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-KL_GEOM_BOX = 0
+KL_GEOM_BOX, KL_GEOM_NURBS = 0, 1
 KL_K_EXP, KL_K_GAUSS, KL_K_EXP_SEPARABLE, KL_K_POLY_TEST = 0, 1, 2, 3
 KL_P_FP64, KL_P_FP32, KL_P_DF64, KL_P_TC32, KL_P_TC64 = 0, 1, 2, 3, 4
 KERNEL_KINDS = {"exp": KL_K_EXP, "gauss": KL_K_GAUSS, "exp_sep": KL_K_EXP_SEPARABLE, "poly": KL_K_POLY_TEST}
@@ -18,7 +18,8 @@ _vp = ctypes.c_void_p
 
 class KLGeometry(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("kind", ctypes.c_int), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3)]
+                ("hi", ctypes.c_double * 3), ("deg", ctypes.c_int * 3), ("nctrl", ctypes.c_int * 3),
+                ("knots", _vp * 3), ("ctrl", _vp)]
 
 
 class KLSpace(ctypes.Structure):
@@ -146,10 +147,30 @@ class KLProblem:
     (column-major blocks are handled by passing the transposed storage, see _block).
     """
 
-    def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None, lo=None, hi=None):
+    def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None, lo=None, hi=None,
+                 nurbs=None):
         lib = load()
         g = KLGeometry(dim, KL_GEOM_BOX, (ctypes.c_double * 3)(*_per_dir(lo, dim, 0.0)),
                        (ctypes.c_double * 3)(*_per_dir(hi, dim, 1.0)))
+        keep = []
+        if nurbs is not None:
+            import numpy as np
+            # nurbs: dict(deg=[...], knots=[...], ctrl=array (n_d, ..., n_1, dim), weights=array (n_d, ..., n_1))
+            g.kind = KL_GEOM_NURBS
+            deg = [int(x) for x in nurbs["deg"]]
+            knots = [np.ascontiguousarray(t, dtype=np.float64) for t in nurbs["knots"]]
+            ctrl = np.asarray(nurbs["ctrl"], dtype=np.float64)
+            wts = np.asarray(nurbs["weights"], dtype=np.float64)
+            rec = np.zeros(wts.shape + (4,))
+            rec[..., :ctrl.shape[-1]] = ctrl
+            rec[..., 3] = wts
+            rec = np.ascontiguousarray(rec.reshape(-1, 4))
+            keep += knots + [rec]
+            for k in range(dim):
+                g.deg[k] = deg[k]
+                g.nctrl[k] = len(knots[k]) - deg[k] - 1
+                g.knots[k] = knots[k].ctypes.data
+            g.ctrl = rec.ctypes.data
         sp = KLSpace((ctypes.c_int * 3)(*_per_dir(p, dim)), (ctypes.c_int * 3)(*_per_dir(ne, dim)),
                      (ctypes.c_int * 3)(*_per_dir(pt, dim)), (ctypes.c_int * 3)(*_per_dir(net, dim)))
         kk = KLKernel(KERNEL_KINDS[kernel] if isinstance(kernel, str) else int(kernel), float(sigma), float(L))

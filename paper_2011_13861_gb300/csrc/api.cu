@@ -362,15 +362,45 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     *out = nullptr;
     const int d = geom->dim;
     if (d < 1 || d > 3) return fail(KL_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
-    if (geom->kind != KL_GEOM_BOX) return fail(KL_ERR_INVALID_ARG, "unsupported geometry kind");
+    if (geom->kind != KL_GEOM_BOX && geom->kind != KL_GEOM_NURBS) return fail(KL_ERR_INVALID_ARG, "unsupported geometry kind");
     if (kernel->kind < KL_K_EXP || kernel->kind > KL_K_POLY_TEST) return fail(KL_ERR_INVALID_ARG, "unknown kernel kind");
     if (!(kernel->sigma > 0.0) || !(kernel->L > 0.0) || !isfinite(kernel->sigma) || !isfinite(kernel->L))
         return fail(KL_ERR_INVALID_ARG, "sigma and L must be positive and finite");
     if (kernel->kind == KL_K_POLY_TEST && (kernel->L < 1.0 || kernel->L > 8.0))
         return fail(KL_ERR_INVALID_ARG, "polynomial test kernel needs 1 <= m = L <= 8");
-    for (int k = 0; k < d; ++k)
-        if (!(geom->hi[k] > geom->lo[k]) || !isfinite(geom->lo[k]) || !isfinite(geom->hi[k]))
-            return fail(KL_ERR_INVALID_ARG, "box extent must be positive");
+    NurbsMap nm;
+    if (geom->kind == KL_GEOM_BOX) {
+        for (int k = 0; k < d; ++k)
+            if (!(geom->hi[k] > geom->lo[k]) || !isfinite(geom->lo[k]) || !isfinite(geom->hi[k]))
+                return fail(KL_ERR_INVALID_ARG, "box extent must be positive");
+    } else {
+        // NURBS map: open knot vectors on [0, 1], positive weights (host data, copied here)
+        nm.dim = d;
+        size_t nrec = 1;
+        for (int k = 0; k < d; ++k) {
+            const int p = geom->deg[k], n = geom->nctrl[k];
+            if (p < 1 || p > 15 || n < p + 1 || n > 4096 || !geom->knots[k])
+                return fail(KL_ERR_INVALID_ARG, "NURBS map: need 1 <= deg <= 15, nctrl >= deg + 1, knots");
+            nm.deg[k] = p;
+            nm.n[k] = n;
+            nm.knots[k].assign(geom->knots[k], geom->knots[k] + n + p + 1);
+            const std::vector<double>& t = nm.knots[k];
+            for (size_t i = 0; i + 1 < t.size(); ++i)
+                if (!(t[i] <= t[i + 1]) || !isfinite(t[i]))
+                    return fail(KL_ERR_INVALID_ARG, "NURBS map: knots must be finite and non-decreasing");
+            for (int i = 0; i <= p; ++i)
+                if (t[size_t(i)] != 0.0 || t[t.size() - 1 - size_t(i)] != 1.0)
+                    return fail(KL_ERR_INVALID_ARG, "NURBS map: knot vectors must be open on [0, 1]");
+            nrec *= size_t(n);
+        }
+        if (!geom->ctrl) return fail(KL_ERR_INVALID_ARG, "NURBS map: null control points");
+        nm.ctrl.assign(geom->ctrl, geom->ctrl + 4 * nrec);
+        for (size_t i = 0; i < nrec; ++i) {
+            for (int r = 0; r < 4; ++r)
+                if (!isfinite(nm.ctrl[4 * i + r])) return fail(KL_ERR_INVALID_ARG, "NURBS map: non-finite control data");
+            if (!(nm.ctrl[4 * i + 3] > 0.0)) return fail(KL_ERR_INVALID_ARG, "NURBS map: weights must be positive");
+        }
+    }
 
     kl_handle h = new (std::nothrow) kl_handle_s();
     if (!h) return fail(KL_ERR_OOM, "host allocation failed");
@@ -392,15 +422,16 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         h->nt[k] = h->dir[k].nt;
         h->N *= h->n[k];
         h->Nt *= h->nt[k];
-        h->lo[k] = geom->lo[k];
-        h->hi[k] = geom->hi[k];
-        det *= geom->hi[k] - geom->lo[k];
+        if (geom->kind == KL_GEOM_BOX) {
+            h->lo[k] = geom->lo[k];
+            h->hi[k] = geom->hi[k];
+            det *= geom->hi[k] - geom->lo[k];
+        }
     }
     if (h->Nt > 2147483647LL || h->N > 2147483647LL) {
         delete h;
         return fail(KL_ERR_INVALID_ARG, "problem too large (more than 2^31-1 points)");
     }
-    h->Jval = sqrt(det);
     // largest intermediate tensor of the forward (n -> n~) and backward (n~ -> n) mode passes
     h->ldw = h->N > h->Nt ? h->N : h->Nt;
     for (int k = 0; k < d; ++k) {
@@ -413,15 +444,29 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         if (b > h->ldw) h->ldw = b;
     }
 
-    // mapped Greville points in vec order (direction 1 fastest) and J
+    // mapped Greville points X = F(xh) in vec order (direction 1 fastest) and J = sqrt(det DF)
     const int64_t Nt = h->Nt;
     h->X_host.assign(size_t(Nt) * 3, 0.0);
+    h->J_host.assign(size_t(Nt), sqrt(det));
     for (int64_t idx = 0; idx < Nt; ++idx) {
         int64_t r = idx;
+        double xh[3] = {0.0, 0.0, 0.0};
         for (int k = 0; k < d; ++k) {
             const int64_t ik = r % h->nt[k];
             r /= h->nt[k];
-            h->X_host[size_t(idx) * 3 + k] = h->lo[k] + (h->hi[k] - h->lo[k]) * h->dir[k].xi[size_t(ik)];
+            xh[k] = h->dir[k].xi[size_t(ik)];
+        }
+        if (geom->kind == KL_GEOM_BOX) {
+            for (int k = 0; k < d; ++k) h->X_host[size_t(idx) * 3 + k] = h->lo[k] + (h->hi[k] - h->lo[k]) * xh[k];
+        } else {
+            double X[3], detDF;
+            nurbs_map_point(nm, xh, X, &detDF);
+            if (!(detDF > 0.0) || !isfinite(detDF)) {
+                delete h;
+                return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");
+            }
+            for (int k = 0; k < 3; ++k) h->X_host[size_t(idx) * 3 + k] = X[k];
+            h->J_host[size_t(idx)] = sqrt(detDF);
         }
     }
     // device copies: coordinates scaled per kernel kind
@@ -472,8 +517,9 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         tabdf[j] = float(t);
         tabdf[64 + j] = float(t - double(tabdf[j]));
     }
-    std::vector<double> J(size_t(Nt), h->Jval);
-    std::vector<float> Jf(size_t(Nt), float(h->Jval));
+    const std::vector<double>& J = h->J_host;
+    std::vector<float> Jf(static_cast<size_t>(Nt));
+    for (int64_t i = 0; i < Nt; ++i) Jf[size_t(i)] = float(J[size_t(i)]);
     std::vector<double> tab(64);
     for (int j = 0; j < 64; ++j) tab[j] = exp2(double(j) / 64.0);
 
@@ -585,7 +631,7 @@ kl_status kl_get_points(kl_handle h, double* X_host, double* J_host) {
     if (!h) return fail(KL_ERR_INVALID_ARG, "null handle");
     if (X_host) std::memcpy(X_host, h->X_host.data(), h->X_host.size() * sizeof(double));
     if (J_host)
-        for (int64_t i = 0; i < h->Nt; ++i) J_host[i] = h->Jval;
+        std::memcpy(J_host, h->J_host.data(), h->J_host.size() * sizeof(double));
     return KL_OK;
 }
 

@@ -44,6 +44,17 @@ struct Direction {
 
 kl_status build_direction(int p, int ne, int pt, int net, Direction* out);
 
+// tensor-product NURBS geometry map: knots per direction, control records (x, y, z, w),
+// direction 1 fastest; directions >= dim have one control point
+struct NurbsMap {
+    int dim = 0;
+    int deg[3] = {0, 0, 0};
+    int n[3] = {1, 1, 1};
+    std::vector<double> knots[3];
+    std::vector<double> ctrl;
+};
+void nurbs_map_point(const NurbsMap& m, const double* xh, double* X, double* detDF);
+
 // ----------------------------------------------------------------------------------------
 // device kernels (launchers)
 // ----------------------------------------------------------------------------------------
@@ -152,9 +163,9 @@ struct kl_handle_s {
     int64_t N = 0, Nt = 0;
     int64_t ldw = 0;              // leading dimension of the intermediate tensors (largest stage size)
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-    double Jval = 1.0;
     float gscale = 1.f;       // see CovParams::gscale
     std::vector<double> X_host;  // Nt x 3 row-major physical points
+    std::vector<double> J_host;  // Nt: J = sqrt(det DF) at the Greville points
     // device set-up data
     double* dCt[3] = {nullptr, nullptr, nullptr};   // forward operator of mode k, layout n_k x nt_k
     double* dC[3] = {nullptr, nullptr, nullptr};    // backward operator of mode k, layout nt_k x n_k

@@ -59,6 +59,30 @@ void nonzero_basis(const std::vector<double>& t, int p, int s, double x, double*
     }
 }
 
+// Derivatives of the p+1 non-zero B-splines N_{s-p..s} at x from the degree p-1 functions
+// of the same span: d/dx N_{i,p} = p N_{i,p-1}/(t_{i+p} - t_i) - p N_{i+1,p-1}/(t_{i+p+1} - t_{i+1}).
+void nonzero_basis_derivative(const std::vector<double>& t, int p, int s, double x, double* dN) {
+    if (p == 0) {
+        dN[0] = 0.0;
+        return;
+    }
+    std::vector<double> Nm(p);
+    nonzero_basis(t, p - 1, s, x, Nm.data());   // N_{s-p+1..s, p-1}
+    for (int r = 0; r <= p; ++r) {
+        const int i = s - p + r;
+        double v = 0.0;
+        if (r >= 1) {
+            const double den = t[i + p] - t[i];
+            if (den > 0.0) v += p * Nm[r - 1] / den;
+        }
+        if (r <= p - 1) {
+            const double den = t[i + p + 1] - t[i + 1];
+            if (den > 0.0) v -= p * Nm[r] / den;
+        }
+        dN[r] = v;
+    }
+}
+
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_q (three-term recurrence).
 void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
     x.assign(q, 0.0);
@@ -239,6 +263,58 @@ kl_status build_direction(int p, int ne, int pt, int net, Direction* out) {
             d.C[size_t(i) * n + j] = s;
         }
     return KL_OK;
+}
+
+
+// F(xh) and det DF(xh) of a tensor-product NURBS map (Sec. 2.4): F = P / W with
+// P = sum_I N_I(xh) w_I P_I and W = sum_I N_I(xh) w_I; column j of DF is
+// (dP/dxh_j W - P dW/dxh_j) / W^2.  Directions beyond dim have one control point.
+void nurbs_map_point(const NurbsMap& m, const double* xh, double* X, double* detDF) {
+    int span[3] = {0, 0, 0};
+    double N[3][16], dN[3][16];
+    for (int k = 0; k < 3; ++k) {
+        if (k < m.dim) {
+            span[k] = find_span(m.knots[k], m.deg[k], xh[k]);
+            nonzero_basis(m.knots[k], m.deg[k], span[k], xh[k], N[k]);
+            nonzero_basis_derivative(m.knots[k], m.deg[k], span[k], xh[k], dN[k]);
+        } else {
+            N[k][0] = 1.0;
+            dN[k][0] = 0.0;
+        }
+    }
+    const int q0 = m.dim > 0 ? m.deg[0] : 0, q1 = m.dim > 1 ? m.deg[1] : 0, q2 = m.dim > 2 ? m.deg[2] : 0;
+    double P[3] = {0, 0, 0}, W = 0.0, dP[3][3] = {{0}}, dW[3] = {0, 0, 0};
+    for (int c = 0; c <= q2; ++c)
+        for (int b = 0; b <= q1; ++b)
+            for (int a = 0; a <= q0; ++a) {
+                const int i0 = (m.dim > 0 ? span[0] - q0 : 0) + a;
+                const int i1 = (m.dim > 1 ? span[1] - q1 : 0) + b;
+                const int i2 = (m.dim > 2 ? span[2] - q2 : 0) + c;
+                const double* cp = &m.ctrl[4 * ((size_t(i2) * m.n[1] + i1) * m.n[0] + i0)];
+                const double w = cp[3];
+                const double val = N[0][a] * N[1][b] * N[2][c] * w;
+                const double der[3] = {dN[0][a] * N[1][b] * N[2][c] * w, N[0][a] * dN[1][b] * N[2][c] * w,
+                                       N[0][a] * N[1][b] * dN[2][c] * w};
+                W += val;
+                for (int r = 0; r < 3; ++r) P[r] += val * cp[r];
+                for (int j = 0; j < 3; ++j) {
+                    dW[j] += der[j];
+                    for (int r = 0; r < 3; ++r) dP[r][j] += der[j] * cp[r];
+                }
+            }
+    double D[3][3];
+    for (int r = 0; r < 3; ++r) {
+        X[r] = P[r] / W;
+        for (int j = 0; j < 3; ++j) D[r][j] = (dP[r][j] * W - P[r] * dW[j]) / (W * W);
+    }
+    if (m.dim == 1) {
+        *detDF = D[0][0];
+    } else if (m.dim == 2) {
+        *detDF = D[0][0] * D[1][1] - D[0][1] * D[1][0];
+    } else {
+        *detDF = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) - D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                 D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+    }
 }
 
 }  // namespace kl

@@ -22,3 +22,27 @@ WORKLOADS = {
     "cube-p2-16^3-exp-L0.5": dict(dim=3, p=2, ne=16, kernel="exp", sigma=1.0, L=0.5, k=20),
     "cube-p3-16^3-gauss-L0.3": dict(dim=3, p=3, ne=16, kernel="gauss", sigma=1.0, L=0.3, k=20),
 }
+
+
+def quarter_annulus_net(r_in=1.0, r_out=2.0, height=1.0, dim=3):
+    """Control net of the quarter-annulus geometry (radius r_in..r_out, angle 0..pi/2, extruded
+    to height for dim = 3): degree 2 per direction, one element, equally spaced radii and
+    heights, the three angular control directions (1,0), (1,1), (0,1) with weights 1, sqrt(1/2),
+    1.  Geometry data only (the input both sides evaluate): dict(deg, knots, ctrl, weights) with
+    ctrl of shape (n_d, ..., n_1, dim), direction 1 (radius) fastest."""
+    knots = [np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0]) for _ in range(dim)]
+    radii = [r_in, 0.5 * (r_in + r_out), r_out]
+    dirs = [(1.0, 0.0), (1.0, 1.0), (0.0, 1.0)]
+    wang = [1.0, float(np.sqrt(0.5)), 1.0]
+    zs = [0.0, 0.5 * height, height]
+    shape = (3,) * dim
+    ctrl = np.zeros(shape + (dim,))
+    wts = np.zeros(shape)
+    for idx in np.ndindex(*shape):
+        i, j = idx[-1], idx[-2]              # radius (direction 1), angle (direction 2)
+        pt = [radii[i] * dirs[j][0], radii[i] * dirs[j][1]]
+        if dim == 3:
+            pt.append(zs[idx[0]])
+        ctrl[idx] = pt
+        wts[idx] = wang[j]
+    return {"deg": [2] * dim, "knots": knots, "ctrl": ctrl, "weights": wts}
