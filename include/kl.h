@@ -231,6 +231,38 @@ typedef struct {
     int applies_tc64;       /* operator applications counted per vector in KL_P_TC64 */
 } kl_eig_info;
 
+/* ---- Many independent problems at once (no counterpart in the paper) ----------------
+ * The instances (each its own kl_handle: size, degree, kernel, geometry may all differ) share
+ * one persistent launch of stage 5 per step: items of 128 rows x a column range of every
+ * instance are taken from a global work counter, the kernel kind is read per item, and the
+ * launch sequence is replayed from a captured CUDA graph; the column-range size is chosen by
+ * timing candidates on the first batch.  Arithmetic as in KL_P_FP32 / KL_P_DF64. */
+
+/* y_i = A~'_i v_i for i < count, on `stream`: stages 1-4 of every instance, one batched stage 5,
+ * stages 6-9.  precision: KL_P_FP32 or KL_P_DF64.  v_dev, y_dev: count device pointers
+ * (N_i x nvec[i], leading dimension ldv[i], or N_i when ldv is NULL), 0 <= nvec[i] <= 32.
+ * A handle may appear once.  Asynchronous on `stream`. */
+kl_status kl_apply_batched(kl_handle* handles, int count, int precision, const double* const* v_dev,
+                           double* const* y_dev, const int* nvec, const int64_t* ldv, void* stream);
+
+typedef struct {
+    int rounds;             /* batched stage-5 launches (one per solver step of the instances) */
+    int cols_per_split;     /* column range chosen by the timing of the first batch */
+    double ms_total;        /* wall time of the call */
+} kl_batch_info;
+
+/* kl_eigs for count instances with the same k, tol and options (opts may be NULL): one host
+ * thread and one CUDA stream per instance run the solver of kl_eigs; every KL_P_FP32 and
+ * KL_P_DF64 operator application of every instance joins a rendezvous, and the last instance
+ * to arrive launches the batched stage 5 for all of them (instances that finish leave the
+ * rendezvous).  evals_host: count x k (row i = instance i); evecs_dev: NULL or count device
+ * pointers (NULL entries allowed), leading dimensions ldv (NULL: N_i); infos, statuses,
+ * binfo may be NULL.  Synchronous.  Returns the first non-KL_OK instance status (statuses[i]
+ * holds every instance's), e.g. KL_ERR_NOT_CONVERGED. */
+kl_status kl_eigs_batched(kl_handle* handles, int count, int k, double tol, const kl_eig_opts* opts,
+                          double* evals_host, double* const* evecs_dev, const int64_t* ldv, kl_eig_info* infos,
+                          kl_status* statuses, kl_batch_info* binfo);
+
 /* The k (<= 64) largest eigenvalues of A~' (descending) to relative residual tol.
  * evals_host: k values (host).  evecs_dev: N x k orthonormal eigenvectors in standard
  * form (v'^T v' = I), leading dimension ldv (may be NULL).  info may be NULL.

@@ -52,6 +52,10 @@ class KLEigInfo(ctypes.Structure):
                 ("pairs_tc64", ctypes.c_double), ("applies_tc64", ctypes.c_int)]
 
 
+class KLBatchInfo(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("cols_per_split", ctypes.c_int), ("ms_total", ctypes.c_double)]
+
+
 SIGNATURES = {
     "kl_create": (ctypes.c_int, [ctypes.POINTER(KLGeometry), ctypes.POINTER(KLSpace), ctypes.POINTER(KLKernel),
                                  ctypes.POINTER(_vp)]),
@@ -68,6 +72,13 @@ SIGNATURES = {
     "kl_eigs": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(KLEigOpts), _vp, _vp, _c_int64,
                                ctypes.POINTER(KLEigInfo), _vp]),
     "kl_to_bspline": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _c_int64, _vp]),
+    "kl_apply_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp),
+                                        ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_c_int64),
+                                        _vp]),
+    "kl_eigs_batched": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(KLEigOpts), _vp, ctypes.POINTER(_vp), ctypes.POINTER(_c_int64),
+                                       ctypes.POINTER(KLEigInfo), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(KLBatchInfo)]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
     "kl_destroy": (None, [_vp]),
@@ -112,6 +123,19 @@ def exported_symbols(path=None):
 def kernel_launches():
     """Kernels launched by libkl since it was loaded."""
     return int(load().kl_kernel_launches())
+
+
+def _info_dict(info, k, st):
+    return {"applies": info.applies, "applies_fp64": info.applies_fp64, "block_applies": info.block_applies,
+            "restarts": info.restarts, "converged": info.converged, "resid": list(info.resid[:k]),
+            "ms_total": info.ms_total, "ms_fp32_phase": info.ms_fp32_phase, "status": st,
+            "stage5_calls_fp64": info.stage5_calls_fp64, "stage5_calls_fp32": info.stage5_calls_fp32,
+            "ms_stage5_fp64": info.ms_stage5_fp64, "ms_stage5_fp32": info.ms_stage5_fp32,
+            "pairs_fp64": info.pairs_fp64, "pairs_fp32": info.pairs_fp32,
+            "stage5_calls_df64": info.stage5_calls_df64, "ms_stage5_df64": info.ms_stage5_df64,
+            "pairs_df64": info.pairs_df64, "applies_df64": info.applies_df64,
+            "stage5_calls_tc64": info.stage5_calls_tc64, "ms_stage5_tc64": info.ms_stage5_tc64,
+            "pairs_tc64": info.pairs_tc64, "applies_tc64": info.applies_tc64}
 
 
 def _check(status):
@@ -287,14 +311,47 @@ class KLProblem:
                             _ptr(vecs), self.N, ctypes.byref(info), _stream(stream))
         if st != 0 and (raise_on_nonconv or st != 4):
             _check(st)
-        d = {"applies": info.applies, "applies_fp64": info.applies_fp64, "block_applies": info.block_applies,
-             "restarts": info.restarts, "converged": info.converged, "resid": list(info.resid[:k]),
-             "ms_total": info.ms_total, "ms_fp32_phase": info.ms_fp32_phase, "status": st,
-             "stage5_calls_fp64": info.stage5_calls_fp64, "stage5_calls_fp32": info.stage5_calls_fp32,
-             "ms_stage5_fp64": info.ms_stage5_fp64, "ms_stage5_fp32": info.ms_stage5_fp32,
-             "pairs_fp64": info.pairs_fp64, "pairs_fp32": info.pairs_fp32,
-             "stage5_calls_df64": info.stage5_calls_df64, "ms_stage5_df64": info.ms_stage5_df64,
-             "pairs_df64": info.pairs_df64, "applies_df64": info.applies_df64,
-             "stage5_calls_tc64": info.stage5_calls_tc64, "ms_stage5_tc64": info.ms_stage5_tc64,
-             "pairs_tc64": info.pairs_tc64, "applies_tc64": info.applies_tc64}
-        return ev, vecs, d
+        return ev, vecs, _info_dict(info, k, st)
+
+
+def apply_batched(problems, vs, precision=KL_P_DF64, stream=None):
+    """y_i = A~'_i v_i for every problem with one batched stage-5 launch (kl_apply_batched).
+    vs: float64 CUDA tensors of shape (nvec_i, N_i) (or (N_i,)); returns the outputs alike."""
+    import torch
+    n = len(problems)
+    hs = (_vp * n)(*[p._h.value for p in problems])
+    blocks = [KLProblem._block(v, p.N) for v, p in zip(vs, problems)]
+    outs = [torch.empty_like(b) for b in blocks]
+    vp = (_vp * n)(*[_ptr(b) for b in blocks])
+    yp = (_vp * n)(*[_ptr(o) for o in outs])
+    nv = (ctypes.c_int * n)(*[b.shape[0] for b in blocks])
+    ld = (_c_int64 * n)(*[p.N for p in problems])
+    _check(load().kl_apply_batched(hs, n, int(precision), vp, yp, nv, ld, _stream(stream)))
+    return [o.reshape(v.shape) for o, v in zip(outs, vs)]
+
+
+def eigs_batched(problems, k, tol=1e-8, method=0, block=4, ncv=0, maxiter=0, seed=1, tol_low=0.0, verify=True,
+                 want_vectors=True, precision=KL_P_DF64, polish_block=0, polish_ncv=0, low_precision=KL_P_FP32):
+    """kl_eigs_batched: the k largest eigenpairs of every problem, solved together.  Returns
+    (evals (count, k) numpy, list of (k, N_i) tensors or None, list of info dicts, statuses, batch info)."""
+    import numpy as np
+    import torch
+    n = len(problems)
+    opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1), None,
+                     float(tol_low), 1 if verify else 0, int(precision), int(polish_block), int(polish_ncv),
+                     int(low_precision))
+    ev = np.zeros((n, k))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vecs = [torch.empty((k, p.N), dtype=torch.float64, device=dev) for p in problems] if want_vectors else None
+    hs = (_vp * n)(*[p._h.value for p in problems])
+    vp = (_vp * n)(*[_ptr(v) for v in vecs]) if vecs else None
+    ld = (_c_int64 * n)(*[p.N for p in problems])
+    infos = (KLEigInfo * n)()
+    sts = (ctypes.c_int * n)()
+    bi = KLBatchInfo()
+    st = load().kl_eigs_batched(hs, n, int(k), float(tol), ctypes.byref(opts), ev.ctypes.data_as(ctypes.c_void_p),
+                                vp, ld, infos, sts, ctypes.byref(bi))
+    if st != 0 and st != 4:
+        _check(st)
+    return (ev, vecs, [_info_dict(infos[i], k, sts[i]) for i in range(n)], list(sts),
+            {"rounds": bi.rounds, "cols_per_split": bi.cols_per_split, "ms_total": bi.ms_total})

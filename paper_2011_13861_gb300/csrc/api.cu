@@ -17,6 +17,8 @@ thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 }
 
+const std::string& last_error_message() { return g_last_error; }
+
 void count_launches(int n) { g_launches.fetch_add(uint64_t(n), std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -122,6 +124,8 @@ CovParams cov_params(kl_handle h) {
 }
 
 }  // namespace
+
+CovParams cov_params_of(kl_handle h) { return cov_params(h); }
 
 // Reads (and clears) the device status word written by kernels with bounded waits.
 kl_status check_device_status(kl_handle h, cudaStream_t s) {
@@ -304,51 +308,87 @@ static kl_status prof_end(kl_handle h, int slot, cudaStream_t s) {
     return KL_OK;
 }
 
-kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, double* y, int64_t ldy, int nvec,
-                     cudaStream_t s) {
-    if (nvec == 0) return KL_OK;
+// stages 1-4 of an application in the workspace of `precision`: u (double, or float for the
+// float32 paths) and the stage-5 output z (double)
+kl_status apply_forward(kl_handle h, int precision, const double* v, int64_t ldv, int nvec, cudaStream_t s,
+                        ApplyBufs* b) {
     const bool fp32 = (precision == KL_P_FP32 || precision == KL_P_TC32);
     KL_TRY(ensure_apply_ws(h, nvec, fp32, precision == KL_P_TC64));
     const int64_t ld = stride_of(h);
     double* A = static_cast<double*>(h->w_a.ptr);
     double* B = static_cast<double*>(h->w_b.ptr);
-    CovParams cp = cov_params(h);
-    const double s2 = h->kernel.sigma * h->kernel.sigma;
+    b->ld = ld;
     if (!fp32) {
-        // stages 1-4 -> u in A (the mode passes ping-pong through A/B and end in `u`)
+        // the mode passes ping-pong through A/B and end in `u`
         double* u = (h->dim % 2 == 1) ? A : B;
         KL_TRY(forward_generic<double, double>(h, v, ldv, u, ld, nvec, h->dCt, h->dJ, A, B, s));
-        double* z = (u == A) ? B : A;
-        int slot;
-        KL_TRY(prof_begin(h, precision, nvec, s, &slot));
-        double* part = static_cast<double*>(h->w_part.ptr);
-        cudaError_t e =
-            (precision == KL_P_DF64)   ? launch_covmv_df(cp, u, ld, nvec, z, ld, s2, h->dJ, part, covmv_df_splits(h->Nt), s)
-            : (precision == KL_P_TC64) ? launch_covmv_tc64(cp, u, ld, nvec, z, ld, s2, h->dJ, part, h->w_tcimg.ptr,
-                                                           h->dStatus, s)
-                                       : launch_covmv64_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, part,
-                                                            covmv_splits(h->Nt, nvec, false), s);
-        if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp64)");
-        KL_TRY(prof_end(h, slot, s));
-        double* other = (z == A) ? B : A;
-        // mode 1 reads z into `other`; z is then free to serve as the second buffer
-        return backward_generic<double>(h, z, ld, y, ldy, nvec, h->dC, other, z, s);
+        b->u = u;
+        b->z = (u == A) ? B : A;
+        return KL_OK;
     }
     float* FA = static_cast<float*>(h->w_f32a.ptr);
     float* FB = static_cast<float*>(h->w_f32b.ptr);
     float* u = (h->dim % 2 == 1) ? FA : FB;
     KL_TRY(forward_generic<float, float>(h, v, ldv, u, ld, nvec, h->fCt, h->fJ, FA, FB, s));
-    double* z = A;
+    b->u = u;
+    b->z = A;
+    return KL_OK;
+}
+
+// stages 6-9 from z (J already applied by stage 5)
+kl_status apply_backward(kl_handle h, int precision, const ApplyBufs& b, double* y, int64_t ldy, int nvec,
+                         cudaStream_t s) {
+    const bool fp32 = (precision == KL_P_FP32 || precision == KL_P_TC32);
+    double* A = static_cast<double*>(h->w_a.ptr);
+    double* B = static_cast<double*>(h->w_b.ptr);
+    if (!fp32) {
+        double* other = (b.z == A) ? B : A;
+        // mode 1 reads z into `other`; z is then free to serve as the second buffer
+        return backward_generic<double>(h, b.z, b.ld, y, ldy, nvec, h->dC, other, b.z, s);
+    }
+    return backward_generic<float>(h, b.z, b.ld, y, ldy, nvec, h->fC, static_cast<float*>(h->w_f32a.ptr),
+                                   static_cast<float*>(h->w_f32b.ptr), s);
+}
+
+kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, double* y, int64_t ldy, int nvec,
+                     cudaStream_t s) {
+    if (nvec == 0) return KL_OK;
+    ApplyBufs b;
+    KL_TRY(apply_forward(h, precision, v, ldv, nvec, s, &b));
+    const int64_t ld = b.ld;
+    CovParams cp = cov_params(h);
+    const double s2 = h->kernel.sigma * h->kernel.sigma;
+    double* part = static_cast<double*>(h->w_part.ptr);
     int slot;
-    KL_TRY(prof_begin(h, KL_P_FP32, nvec, s, &slot));
-    cudaError_t e = (precision == KL_P_TC32)
-                        ? launch_covmv_tc(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                          h->w_tcimg.ptr, h->dStatus, s)
-                        : launch_covmv32_sym(cp, u, ld, nvec, z, ld, s2, h->dJ, static_cast<double*>(h->w_part.ptr),
-                                             covmv_splits(h->Nt, nvec, true), s);
-    if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (fp32)");
+    const bool fp32 = (precision == KL_P_FP32 || precision == KL_P_TC32);
+    KL_TRY(prof_begin(h, fp32 ? KL_P_FP32 : precision, nvec, s, &slot));
+    if (h->batch && (precision == KL_P_FP32 || precision == KL_P_DF64)) {
+        // many instances solved together: stage 5 joins the other instances' requests
+        KL_TRY(batch_stage5(h, precision, b.u, ld, b.z, ld, nvec, true, s));
+    } else {
+        const double* u64 = static_cast<const double*>(b.u);
+        const float* u32 = static_cast<const float*>(b.u);
+        cudaError_t e;
+        switch (precision) {
+            case KL_P_DF64:
+                e = launch_covmv_df(cp, u64, ld, nvec, b.z, ld, s2, h->dJ, part, covmv_df_splits(h->Nt), s);
+                break;
+            case KL_P_TC64:
+                e = launch_covmv_tc64(cp, u64, ld, nvec, b.z, ld, s2, h->dJ, part, h->w_tcimg.ptr, h->dStatus, s);
+                break;
+            case KL_P_TC32:
+                e = launch_covmv_tc(cp, u32, ld, nvec, b.z, ld, s2, h->dJ, part, h->w_tcimg.ptr, h->dStatus, s);
+                break;
+            case KL_P_FP32:
+                e = launch_covmv32_sym(cp, u32, ld, nvec, b.z, ld, s2, h->dJ, part, covmv_splits(h->Nt, nvec, true), s);
+                break;
+            default:
+                e = launch_covmv64_sym(cp, u64, ld, nvec, b.z, ld, s2, h->dJ, part, covmv_splits(h->Nt, nvec, false), s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product");
+    }
     KL_TRY(prof_end(h, slot, s));
-    return backward_generic<float>(h, z, ld, y, ldy, nvec, h->fC, FA, FB, s);
+    return apply_backward(h, precision, b, y, ldy, nvec, s);
 }
 
 }  // namespace kl
@@ -696,6 +736,7 @@ void kl_destroy(kl_handle h) {
     release(h->w_f32b);
     release(h->w_part);
     release(h->w_tcimg);
+    if (h->batch_ready) cudaEventDestroy(h->batch_ready);
     for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
     delete h;
 }

@@ -19,6 +19,7 @@
 // reports KL_ERR_TIMEOUT.
 #include <cuda_bf16.h>
 
+#include "kernel32.cuh"
 #include "tc_common.cuh"
 
 // Stage 5 of Algorithm 1 as a tensor-core block contraction (tcgen05, sm_103a) for groups of up
@@ -100,30 +101,6 @@ __device__ __forceinline__ void split3(float g, uint32_t& w0, uint32_t& w1, uint
 
 // two bfloat16 (upper halves of a and b) packed as elements (k, k+1)
 __device__ __forceinline__ uint32_t pack_bf16(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
-
-template <int KIND>
-__device__ __forceinline__ float kernel_tc(float dx, float dy, float dz, float x0, float y0, float z0, float x1,
-                                           float y1, float z1, int pm) {
-    if (KIND == KL_K_EXP) {
-        float s = fmaxf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), 1e-30f);
-        float rs, g;
-        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(s));
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(-s * rs));
-        return g;
-    } else if (KIND == KL_K_GAUSS) {
-        float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx)), g;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(-s));
-        return g;
-    } else if (KIND == KL_K_EXP_SEPARABLE) {
-        float g;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(-(fabsf(dx) + fabsf(dy) + fabsf(dz))));
-        return g;
-    } else {
-        float f = fmaf(x0, x1, 1.f) * fmaf(y0, y1, 1.f) * fmaf(z0, z1, 1.f), r = 1.f;
-        for (int i = 0; i < pm; ++i) r *= f;
-        return r;
-    }
-}
 
 // The image of column chunk ch: the chunk's coordinates (x[32], y[32], z[32], zero past Ntilde)
 // and the group's u values split into three bfloat16 terms, in the K-major operand layout the
@@ -234,9 +211,9 @@ covmv_tc_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, dou
                 uint32_t w[kTcPieces][4];
 #pragma unroll
                 for (int e = 0; e < 8; e += 2) {
-                    const float ga = kernel_tc<KIND>(x0 - xs[e], y0 - ys[e], z0 - zs[e], x0, y0, z0, xs[e], ys[e],
+                    const float ga = kernel32<KIND>(x0 - xs[e], y0 - ys[e], z0 - zs[e], x0, y0, z0, xs[e], ys[e],
                                                      zs[e], cp.poly_m);
-                    const float gb = kernel_tc<KIND>(x0 - xs[e + 1], y0 - ys[e + 1], z0 - zs[e + 1], x0, y0, z0,
+                    const float gb = kernel32<KIND>(x0 - xs[e + 1], y0 - ys[e + 1], z0 - zs[e + 1], x0, y0, z0,
                                                      xs[e + 1], ys[e + 1], zs[e + 1], cp.poly_m);
                     uint32_t a0, a1, a2, b0, b1, b2;
                     split3(ga, a0, a1, a2);

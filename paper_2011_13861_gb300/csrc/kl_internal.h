@@ -16,6 +16,8 @@ namespace kl {
 // ----------------------------------------------------------------------------------------
 void set_error(const std::string& msg);
 kl_status fail(kl_status st, const std::string& msg);
+const std::string& last_error_message();   // this thread's last message
+int num_sms();                             // SMs of the current device (cached)
 kl_status cuda_fail(cudaError_t e, const char* what);
 void count_launches(int n);   // kernel-launch accounting (kl_kernel_launches)
 
@@ -155,6 +157,10 @@ void release(DevBuf& b);
 
 }  // namespace kl
 
+namespace kl {
+struct BatchRendezvous;
+}
+
 struct kl_handle_s {
     int dim = 0;
     kl_kernel kernel{};
@@ -166,6 +172,8 @@ struct kl_handle_s {
     float gscale = 1.f;       // see CovParams::gscale
     std::vector<double> X_host;  // Nt x 3 row-major physical points
     std::vector<double> J_host;  // Nt: J = sqrt(det DF) at the Greville points
+    kl::BatchRendezvous* batch = nullptr;   // set while kl_eigs_batched solves this instance
+    cudaEvent_t batch_ready = nullptr;       // u of this instance is ready for the batched stage 5
     // device set-up data
     double* dCt[3] = {nullptr, nullptr, nullptr};   // forward operator of mode k, layout n_k x nt_k
     double* dC[3] = {nullptr, nullptr, nullptr};    // backward operator of mode k, layout nt_k x n_k
@@ -201,4 +209,19 @@ kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, in
 kl_status check_device_status(kl_handle h, cudaStream_t s);
 kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host,
                     double* evecs_dev, int64_t ldv, kl_eig_info* info, cudaStream_t s);
+
+CovParams cov_params_of(kl_handle h);
+// one application split into its stages (the batched path joins other instances at stage 5)
+struct ApplyBufs {
+    const void* u = nullptr;   // stage-4 output: double, or float for the float32 paths
+    double* z = nullptr;       // stage-5 output
+    int64_t ld = 0;
+};
+kl_status apply_forward(kl_handle h, int precision, const double* v, int64_t ldv, int nvec, cudaStream_t s,
+                        ApplyBufs* b);
+kl_status apply_backward(kl_handle h, int precision, const ApplyBufs& b, double* y, int64_t ldy, int nvec,
+                         cudaStream_t s);
+// batched stage 5 (batch.cu)
+kl_status batch_stage5(kl_handle h, int prec, const void* U, int64_t ldu, double* Z, int64_t ldz, int nv,
+                       bool withJ, cudaStream_t s);
 }  // namespace kl

@@ -210,7 +210,6 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
     extern __shared__ double sT[];          // m x m, row-major with stride m
     __shared__ double cs[kEigMax / 2 + 1][2];
     __shared__ int prs[kEigMax / 2 + 1][2];
-    __shared__ int rotated;
     const int tid = threadIdx.x;
     for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e - i * m;
@@ -222,8 +221,7 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
     const int npairs = mp / 2;
     int sweep = 0;
     for (; sweep < 40; ++sweep) {
-        if (tid == 0) rotated = 0;
-        __syncthreads();
+        int rotated = 0;   // this thread applied a rotation in this sweep
         for (int r = 0; r < mp - 1; ++r) {
             for (int i = tid; i < npairs; i += blockDim.x) {
                 int a, b;
@@ -281,8 +279,9 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
             }
             __syncthreads();
         }
-        __syncthreads();
-        if (!rotated) break;
+        // every thread takes the same decision (a shared flag reset by one thread at the top of
+        // the next sweep could be read after the reset by a slower thread)
+        if (!__syncthreads_or(rotated)) break;
     }
     // sort descending: rank by (value desc, index asc)
     for (int i = tid; i < m; i += blockDim.x) {
@@ -336,7 +335,6 @@ sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __rest
     float* Wl = Wh + m * ld;
     __shared__ df::F2 cs[kEigDfMax / 2 + 1][2];
     __shared__ int prs[kEigDfMax / 2 + 1][2];
-    __shared__ int rotated;
     const int tid = threadIdx.x;
     for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e - i * m;
@@ -351,8 +349,7 @@ sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __rest
     const int npairs = mp / 2;
     int sweep = 0;
     for (; sweep < 40; ++sweep) {
-        if (tid == 0) rotated = 0;
-        __syncthreads();
+        int rotated = 0;   // this thread applied a rotation in this sweep
         for (int r = 0; r < mp - 1; ++r) {
             for (int i = tid; i < npairs; i += blockDim.x) {
                 int a, b;
@@ -411,8 +408,9 @@ sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __rest
             }
             __syncthreads();
         }
-        __syncthreads();
-        if (!rotated) break;
+        // every thread takes the same decision (a shared flag reset by one thread at the top of
+        // the next sweep could be read after the reset by a slower thread)
+        if (!__syncthreads_or(rotated)) break;
     }
     // sort descending: rank by (value desc, index asc)
     for (int i = tid; i < m; i += blockDim.x) {
@@ -538,6 +536,9 @@ int grid_for(int64_t work, int threads, int cap) {
 
 }  // namespace
 
+// the largest dynamic shared memory of gemm_tall_kernel: p <= kGramMaxP rows of B, 32 columns
+constexpr int kGemmMaxSmem = kGramMaxP * 32 * int(sizeof(double));
+
 int num_sms() {
     static int cached = 0;
     if (cached == 0) {
@@ -574,7 +575,9 @@ cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, in
         const int qq = (q - j0 < kGramMaxQ) ? q - j0 : kGramMaxQ;
         const size_t smem = size_t(kGramRows) * (gram_ld(p) + gram_ld(qq)) * sizeof(double);
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            // the largest request ever (set, never lowered: launches of other threads stay valid)
+            const int smax = int(size_t(kGramRows) * (gram_ld(kGramMaxP) + gram_ld(kGramMaxQ)) * sizeof(double));
+            cudaError_t e = cudaFuncSetAttribute(gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
             if (e != cudaSuccess) return e;
         }
         count_launches(2);
@@ -596,6 +599,7 @@ cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t
         // C = beta * C
         return (beta == 1.0) ? cudaSuccess : cudaErrorInvalidValue;
     }
+    if (p > kGramMaxP) return cudaErrorInvalidValue;
     for (int j0 = 0; j0 < q; j0 += 32) {
         const int qq = (q - j0 < 32) ? q - j0 : 32;
         const int QB = qq == 1 ? 1 : 4;
@@ -608,12 +612,14 @@ cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t
         cudaError_t e = cudaSuccess;
         if (QB == 1) {
             if (smem > 48 * 1024)
-                e = cudaFuncSetAttribute(gemm_tall_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+                e = cudaFuncSetAttribute(gemm_tall_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGemmMaxSmem);
             if (e != cudaSuccess) return e;
             gemm_tall_kernel<1><<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
         } else {
             if (smem > 48 * 1024)
-                e = cudaFuncSetAttribute(gemm_tall_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+                e = cudaFuncSetAttribute(gemm_tall_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kGemmMaxSmem);
             if (e != cudaSuccess) return e;
             gemm_tall_kernel<4><<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
         }
@@ -642,14 +648,16 @@ cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, do
     if (m > kEigMax || m < 1) return cudaErrorInvalidValue;
     if (m <= kEigDfMax) {
         const size_t smem = size_t(4) * m * (m | 1) * sizeof(float);
-        cudaError_t e = cudaFuncSetAttribute(sym_eig_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        cudaError_t e = cudaFuncSetAttribute(sym_eig_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(size_t(4) * kEigDfMax * (kEigDfMax | 1) * sizeof(float)));
         if (e != cudaSuccess) return e;
         sym_eig_df_kernel<<<1, kEigDfThreads, smem, s>>>(T, ldt, m, evals, S, lds, sweeps_out);
         count_launches(1);
         return cudaGetLastError();
     }
     const size_t smem = size_t(m) * m * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = cudaFuncSetAttribute(sym_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(size_t(kEigMax) * kEigMax * sizeof(double)));
     if (e != cudaSuccess) return e;
     sym_eig_kernel<<<1, kEigThreads, smem, s>>>(T, ldt, m, evals, S, lds, work, sweeps_out, false);
     count_launches(1);

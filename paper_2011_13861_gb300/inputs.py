@@ -46,3 +46,18 @@ def quarter_annulus_net(r_in=1.0, r_out=2.0, height=1.0, dim=3):
         ctrl[idx] = pt
         wts[idx] = wang[j]
     return {"deg": [2] * dim, "knots": knots, "ctrl": ctrl, "weights": wts}
+
+
+def batched_instances(count=64, seed=2011, ne_range=(8, 40), degrees=(2, 3), L_range=(0.1, 2.0)):
+    """Seeded instances of the batched workload: quarter annulus (radius 1..2, height 1, the net
+    of quarter_annulus_net), elements per direction uniform on ne_range, degree uniform on
+    `degrees` (same in every direction), kernels alternating exponential / Gaussian, L
+    log-uniform on L_range, sigma 1.  Returns dicts with dim, p, ne, kernel, L, sigma."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        ne = [int(x) for x in rng.integers(ne_range[0], ne_range[1] + 1, size=3)]
+        p = int(rng.choice(degrees))
+        L = float(np.exp(rng.uniform(np.log(L_range[0]), np.log(L_range[1]))))
+        out.append({"dim": 3, "p": p, "ne": ne, "kernel": "exp" if i % 2 == 0 else "gauss", "L": L, "sigma": 1.0})
+    return out

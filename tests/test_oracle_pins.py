@@ -357,3 +357,13 @@ def test_ibq_on_quarter_annulus_converges_to_galerkin():
         errs.append(np.abs(li - lg).max() / lg[0])
     assert errs[1] < errs[0] / 4
     assert errs[1] < 1e-3
+
+
+def test_batched_instance_generator_is_seeded():
+    from paper_2011_13861_gb300 import inputs as _inputs
+    a = _inputs.batched_instances(8)
+    b = _inputs.batched_instances(8)
+    assert a == b
+    for i, c in enumerate(_inputs.batched_instances(64)):
+        assert all(8 <= x <= 40 for x in c["ne"]) and c["p"] in (2, 3) and 0.1 <= c["L"] <= 2.0
+        assert c["kernel"] == ("exp" if i % 2 == 0 else "gauss")
