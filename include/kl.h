@@ -246,9 +246,11 @@ kl_status kl_apply_batched(kl_handle* handles, int count, int precision, const d
                            double* const* y_dev, const int* nvec, const int64_t* ldv, void* stream);
 
 typedef struct {
-    int rounds;             /* batched stage-5 launches (one per solver step of the instances) */
-    int cols_per_split;     /* column range chosen by the timing of the first batch */
+    int rounds;             /* batched stage-5 launches */
+    int cols_per_split;     /* column range chosen by the timing of the first representative batch */
     double ms_total;        /* wall time of the call */
+    double ms_stage5;       /* batched stage-5 time on the GPU (CUDA events around every launch) */
+    long long requests;     /* instance applications served by those launches */
 } kl_batch_info;
 
 /* kl_eigs for count instances with the same k, tol and options (opts may be NULL): one host

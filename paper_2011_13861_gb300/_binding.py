@@ -53,7 +53,8 @@ class KLEigInfo(ctypes.Structure):
 
 
 class KLBatchInfo(ctypes.Structure):
-    _fields_ = [("rounds", ctypes.c_int), ("cols_per_split", ctypes.c_int), ("ms_total", ctypes.c_double)]
+    _fields_ = [("rounds", ctypes.c_int), ("cols_per_split", ctypes.c_int), ("ms_total", ctypes.c_double),
+                ("ms_stage5", ctypes.c_double), ("requests", ctypes.c_longlong)]
 
 
 SIGNATURES = {
@@ -354,4 +355,5 @@ def eigs_batched(problems, k, tol=1e-8, method=0, block=4, ncv=0, maxiter=0, see
     if st != 0 and st != 4:
         _check(st)
     return (ev, vecs, [_info_dict(infos[i], k, sts[i]) for i in range(n)], list(sts),
-            {"rounds": bi.rounds, "cols_per_split": bi.cols_per_split, "ms_total": bi.ms_total})
+            {"rounds": bi.rounds, "cols_per_split": bi.cols_per_split, "ms_total": bi.ms_total,
+             "ms_stage5": bi.ms_stage5, "requests": bi.requests})

@@ -260,7 +260,7 @@ __global__ void batch_reduce(const BatchHdr* __restrict__ hdr, const BatchReq* _
     }
 }
 
-int batch_nv(int nv) { return nv <= 4 ? 4 : nv <= 8 ? 8 : nv <= 16 ? 16 : 32; }
+int batch_nv(int nv) { return nv <= 4 ? 4 : nv <= 8 ? 8 : nv <= 12 ? 12 : nv <= 16 ? 16 : 32; }
 
 template <int NV>
 cudaError_t occupancy_grid(int prec, int* grid) {
@@ -302,9 +302,15 @@ struct BatchRequest {
 struct BatchExec {
     // device resources
     DevBuf table, part, counter;
-    BatchHdr* hdr_host = nullptr;     // pinned staging: header followed by the request table
-    size_t host_cap = 0;
-    cudaEvent_t upload_done = nullptr;
+    // pinned staging for the table uploads, a ring so that filling the next table waits only
+    // for an upload several batches back
+    static constexpr int kRing = 4;
+    struct Slot {
+        BatchHdr* host = nullptr;      // header followed by the request table
+        size_t cap = 0;
+        cudaEvent_t uploaded = nullptr;
+    } ring[kRing];
+    int ring_pos = 0;
     std::map<long long, long long> tuned_cps;          // (prec, NV) -> columns per split
     std::map<long long, cudaGraphExec_t> graphs;       // (prec, NV, cps) -> captured sequence
     int last_cps = 0;
@@ -316,8 +322,11 @@ struct BatchExec {
     }
     ~BatchExec() {
         clear_graphs();
-        if (hdr_host) cudaFreeHost(hdr_host);
-        if (upload_done) cudaEventDestroy(upload_done);
+        for (Slot& sl : ring) {
+            if (sl.uploaded) cudaEventSynchronize(sl.uploaded);
+            if (sl.host) cudaFreeHost(sl.host);
+            if (sl.uploaded) cudaEventDestroy(sl.uploaded);
+        }
         release(table);
         release(part);
         release(counter);
@@ -371,34 +380,34 @@ kl_status run_batch_nv(BatchExec& X, const std::vector<BatchRequest>& reqs, int 
                        bool may_tune) {
     const size_t nreq = reqs.size();
     const size_t tbl_bytes = sizeof(BatchHdr) + nreq * sizeof(BatchReq);
-    if (X.host_cap < tbl_bytes) {
-        if (X.hdr_host) {
-            KL_CUDA(cudaEventSynchronize(X.upload_done));
-            cudaFreeHost(X.hdr_host);
-            X.hdr_host = nullptr;
-        }
-        KL_CUDA(cudaMallocHost(reinterpret_cast<void**>(&X.hdr_host), tbl_bytes * 2));
-        X.host_cap = tbl_bytes * 2;
-    }
-    if (!X.upload_done) KL_CUDA(cudaEventCreateWithFlags(&X.upload_done, cudaEventDisableTiming));
     KL_TRY(ensure(X.counter, sizeof(int)));
     int grid = 0;
     KL_CUDA(occupancy_grid<NV>(prec, &grid));
     const long long key = (long long)prec * 1000 + NV;
 
     auto upload_and_run = [&](long long cps, bool use_graph) -> kl_status {
-        KL_CUDA(cudaEventSynchronize(X.upload_done));   // the staging buffer is free again
-        BatchReq* tbl = reinterpret_cast<BatchReq*>(X.hdr_host + 1);
-        const size_t part_doubles = build_table(reqs, prec, cps, X.hdr_host, tbl);
-        if (X.hdr_host->total_items > 2147483647LL) return fail(KL_ERR_INVALID_ARG, "batch too large (work items)");
+        BatchExec::Slot& sl = X.ring[X.ring_pos];
+        X.ring_pos = (X.ring_pos + 1) % BatchExec::kRing;
+        if (!sl.uploaded) KL_CUDA(cudaEventCreateWithFlags(&sl.uploaded, cudaEventDisableTiming));
+        KL_CUDA(cudaEventSynchronize(sl.uploaded));   // this slot's previous upload has been read
+        if (sl.cap < tbl_bytes) {
+            if (sl.host) cudaFreeHost(sl.host);
+            sl.host = nullptr;
+            sl.cap = 0;
+            KL_CUDA(cudaMallocHost(reinterpret_cast<void**>(&sl.host), tbl_bytes * 2));
+            sl.cap = tbl_bytes * 2;
+        }
+        BatchReq* tbl = reinterpret_cast<BatchReq*>(sl.host + 1);
+        const size_t part_doubles = build_table(reqs, prec, cps, sl.host, tbl);
+        if (sl.host->total_items > 2147483647LL) return fail(KL_ERR_INVALID_ARG, "batch too large (work items)");
         if (X.part.bytes < part_doubles * sizeof(double) || X.table.bytes < tbl_bytes) {
             KL_CUDA(cudaStreamSynchronize(s));
             X.clear_graphs();
             KL_TRY(ensure(X.part, part_doubles * sizeof(double) + 256));
-            KL_TRY(ensure(X.table, tbl_bytes > X.host_cap / 2 ? tbl_bytes : X.host_cap / 2));
+            KL_TRY(ensure(X.table, 2 * tbl_bytes));
         }
-        KL_CUDA(cudaMemcpyAsync(X.table.ptr, X.hdr_host, tbl_bytes, cudaMemcpyHostToDevice, s));
-        KL_CUDA(cudaEventRecord(X.upload_done, s));
+        KL_CUDA(cudaMemcpyAsync(X.table.ptr, sl.host, tbl_bytes, cudaMemcpyHostToDevice, s));
+        KL_CUDA(cudaEventRecord(sl.uploaded, s));
         const BatchHdr* hdr = static_cast<const BatchHdr*>(X.table.ptr);
         const BatchReq* dreq = reinterpret_cast<const BatchReq*>(hdr + 1);
         int* counter = static_cast<int*>(X.counter.ptr);
@@ -486,6 +495,7 @@ kl_status run_batch(BatchExec& X, const std::vector<BatchRequest>& reqs, int pre
     switch (batch_nv(nv)) {
         case 4: return run_batch_nv<4>(X, reqs, prec, s, may_tune);
         case 8: return run_batch_nv<8>(X, reqs, prec, s, may_tune);
+        case 12: return run_batch_nv<12>(X, reqs, prec, s, may_tune);
         case 16: return run_batch_nv<16>(X, reqs, prec, s, may_tune);
         default: return run_batch_nv<32>(X, reqs, prec, s, may_tune);
     }
@@ -522,12 +532,22 @@ struct BatchRendezvous {
     cudaEvent_t done = nullptr;
     BatchExec exec;
     int rounds = 0;
+    long long requests = 0;
+    std::vector<cudaEvent_t> tev;   // begin/end of every round on the batch stream
 
     // called with mu held once every active participant has submitted
     void launch_locked() {
         kl_status st = KL_OK;
         for (const auto& p : pending)
             if (cudaStreamWaitEvent(bs, p.ready, 0) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "batch wait");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+            cudaEventRecord(e0, bs);
+            tev.push_back(e0);
+            tev.push_back(e1);
+        } else {
+            e1 = nullptr;
+        }
         for (int prec : {KL_P_FP32, KL_P_DF64}) {
             std::vector<BatchRequest> g;
             for (const auto& p : pending)
@@ -539,6 +559,8 @@ struct BatchRendezvous {
                 if (st != KL_OK) error_msg = last_error_message();
             }
         }
+        if (e1) cudaEventRecord(e1, bs);
+        requests += (long long)pending.size();
         if (st == KL_OK && cudaEventRecord(done, bs) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "batch record");
         if (st != KL_OK && error == KL_OK) error = st;
         pending.clear();
@@ -597,11 +619,19 @@ BatchRendezvous* batch_create(int participants, kl_status* st) {
     return R;
 }
 
-void batch_destroy(BatchRendezvous* R, int* rounds, int* cps) {
+void batch_destroy(BatchRendezvous* R, int* rounds, int* cps, double* ms_stage5, long long* requests) {
     if (!R) return;
     if (R->bs) cudaStreamSynchronize(R->bs);
     if (rounds) *rounds = R->rounds;
     if (cps) *cps = R->exec.last_cps;
+    if (requests) *requests = R->requests;
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < R->tev.size(); i += 2) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, R->tev[i], R->tev[i + 1]) == cudaSuccess) ms += t;
+    }
+    for (cudaEvent_t e : R->tev) cudaEventDestroy(e);
+    if (ms_stage5) *ms_stage5 = ms;
     if (R->done) cudaEventDestroy(R->done);
     if (R->bs) cudaStreamDestroy(R->bs);
     delete R;
@@ -723,10 +753,14 @@ kl_status kl_eigs_batched(kl_handle* handles, int count, int k, double tol, cons
     }
     for (int i = 0; i < count; ++i) handles[i]->batch = nullptr;
     int rounds = 0, cps = 0;
-    batch_destroy(R, &rounds, &cps);
+    double ms5 = 0.0;
+    long long nreq = 0;
+    batch_destroy(R, &rounds, &cps, &ms5, &nreq);
     if (binfo) {
         binfo->rounds = rounds;
         binfo->cols_per_split = cps;
+        binfo->ms_stage5 = ms5;
+        binfo->requests = nreq;
         binfo->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     kl_status first = KL_OK;
