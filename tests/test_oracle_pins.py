@@ -367,3 +367,110 @@ def test_batched_instance_generator_is_seeded():
     for i, c in enumerate(_inputs.batched_instances(64)):
         assert all(8 <= x <= 40 for x in c["ne"]) and c["p"] in (2, 3) and 0.1 <= c["L"] <= 2.0
         assert c["kernel"] == ("exp" if i % 2 == 0 else "gauss")
+
+
+# ---------------------------------------------------------------------------------------------
+# learned warm start: MLP, projector loss, Adam, prolongation between nested spline spaces
+# ---------------------------------------------------------------------------------------------
+
+def test_bf16_rounding_matches_torch():
+    import torch
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(1000) * 10.0 ** rng.integers(-8, 8, 1000),
+                        [1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -1.0 - 2 ** -8, 0.0, 65504.0]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(x), ref)
+    assert mlp.bf16(np.array([1.0 + 2 ** -8]))[0] == 1.0          # tie to even
+    assert mlp.bf16(np.array([1.0 + 3 * 2 ** -9]))[0] == 1.0 + 2 ** -7
+
+
+def _tiny_net(rng, sizes):
+    Ws = [rng.standard_normal((a, b)) / np.sqrt(a) for a, b in zip(sizes[:-1], sizes[1:])]
+    bs = [0.1 * rng.standard_normal(b) for b in sizes[1:]]
+    return Ws, bs
+
+
+def test_projector_loss_closed_form_and_invariance():
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    n, k, B = 9, 3, 4
+    out = rng.standard_normal((B, k * n))
+    Vs = np.stack([np.linalg.qr(rng.standard_normal((n, k)))[0] for _ in range(B)])
+    loss, _ = mlp.projector_loss(out, Vs, k)
+    dense = np.mean([np.sum((out[s].reshape(k, n).T @ out[s].reshape(k, n) - Vs[s] @ Vs[s].T) ** 2)
+                     for s in range(B)]) / k
+    assert abs(loss - dense) < 1e-12 * dense
+    R = np.linalg.qr(rng.standard_normal((k, k)))[0] * np.array([1.0, -1.0, 1.0])
+    rot = np.stack([(out[s].reshape(k, n).T @ R).T.reshape(-1) for s in range(B)])
+    assert abs(mlp.projector_loss(rot, Vs, k)[0] - loss) < 1e-12 * loss
+    exact = np.stack([(Vs[s] @ R).T.reshape(-1) for s in range(B)])
+    assert abs(mlp.projector_loss(exact, Vs, k)[0]) < 1e-14   # cancellation of k - 2k + k
+
+
+def test_mlp_gradient_finite_differences():
+    """Backward propagation and the loss gradient against central differences of the float64
+    network (roundings off), for every weight and bias of a small 4-layer tanh network."""
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    n, k, B = 5, 2, 3
+    Ws, bs = _tiny_net(rng, [4, 6, 6, 6, k * n])
+    x = rng.standard_normal((B, 4))
+    Vs = np.stack([np.linalg.qr(rng.standard_normal((n, k)))[0] for _ in range(B)])
+
+    def f(Ws_, bs_):
+        out, _ = mlp.forward(Ws_, bs_, x, rounding=False)
+        return mlp.projector_loss(out, Vs, k)[0]
+    out, cache = mlp.forward(Ws, bs, x, rounding=False)
+    _, g = mlp.projector_loss(out, Vs, k)
+    dWs, dbs = mlp.backward(Ws, bs, cache, g, rounding=False)
+    h = 1e-6
+    for l in range(len(Ws)):
+        for idx in [(0, 0), (Ws[l].shape[0] - 1, Ws[l].shape[1] - 1), (1, 2)]:
+            Wp = [w.copy() for w in Ws]
+            Wm = [w.copy() for w in Ws]
+            Wp[l][idx] += h
+            Wm[l][idx] -= h
+            fd = (f(Wp, bs) - f(Wm, bs)) / (2 * h)
+            assert abs(fd - dWs[l][idx]) < 1e-6 * max(1.0, abs(fd)), (l, idx)
+        bp = [b.copy() for b in bs]
+        bm = [b.copy() for b in bs]
+        bp[l][1] += h
+        bm[l][1] -= h
+        fd = (f(Ws, bp) - f(Ws, bm)) / (2 * h)
+        assert abs(fd - dbs[l][1]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_adam_matches_torch():
+    import torch
+    from oracle import mlp
+    rng = np.random.default_rng(6)
+    p0 = rng.standard_normal(20)
+    grads = [rng.standard_normal(20) for _ in range(3)]
+    p = p0.copy()
+    m = np.zeros(20)
+    v = np.zeros(20)
+    for t, g in enumerate(grads, start=1):
+        mlp.adam_step(p, g, m, v, t, 1e-2)
+    tp = torch.nn.Parameter(torch.from_numpy(p0.copy()))
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for g in grads:
+        tp.grad = torch.from_numpy(g.copy())
+        opt.step()
+    assert np.abs(tp.detach().numpy() - p).max() < 1e-12
+
+
+def test_prolongation_is_exact_and_norm_preserving():
+    """Coarse and prolonged fine splines are the same function at random points, and in the
+    standard form (Sec. 4.1) the map has orthonormal columns (L2 norms are preserved)."""
+    from oracle import prolong
+    rng = np.random.default_rng(7)
+    for p, nc, nf in [(2, 4, 12), (3, 5, 10), (3, 8, 24)]:
+        P = prolong.prolongation_1d(p, nc, nf)
+        x = rng.random(200)
+        tc = bspline.open_uniform_knots(p, nc)
+        tf = bspline.open_uniform_knots(p, nf)
+        c = rng.standard_normal(P.shape[1])
+        assert np.abs(bspline.basis_matrix(tc, p, x) @ c - bspline.basis_matrix(tf, p, x) @ (P @ c)).max() < 1e-13
+        Q = prolong.standard_form_map_1d(p, nc, nf)
+        assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 1e-12
