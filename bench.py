@@ -52,6 +52,11 @@ def parse():
                     help="skip the 64-instance quarter-annulus batch")
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the 132,651-point Gaussian cube (mixed precision with blocks of 16)")
+    ap.add_argument("--no-c5", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--c5-train-solves", type=int, default=400,
+                    help="coarse (16^3, p=3) training solves of the warm-start network (2000 = the full set)")
+    ap.add_argument("--c5-epochs", type=int, default=100)
+    ap.add_argument("--c5-eval", type=int, default=2, help="unseen parameter sets solved at 48^3")
     return ap.parse_args()
 
 
@@ -205,6 +210,65 @@ def measure_c4(kl, inputs):
            "timing": "wall clock with a device synchronisation on both sides, one run each"}
     for G in Gs:
         G.close()
+    return out
+
+
+def measure_c5(kl, inputs, train_solves, epochs, n_eval):
+    """Learned warm start on the quarter annulus: a 4 x 256 bfloat16 network trained on the
+    32 leading eigenvectors of `train_solves` coarse problems (p=3, 16^3 elements; kernel, L and
+    radii drawn with seed 5), then used, prolonged exactly to 48^3 elements, as the start block
+    of the mixed solver (20 eigenpairs, residual 1e-8) for unseen parameter sets (seed 6); against
+    the same solver from the random start (block 32 as the warm start, and block 16, its best
+    width) and, for the first parameter set, random-start float64 block Lanczos (block 4)."""
+    import numpy as np
+    import torch
+    from paper_2011_13861_gb300 import warmstart
+    ws = warmstart.WarmStart(p=3, ne_coarse=16, k=32, width=256, depth=4, seed=5)
+    X, T, st = ws.targets(inputs.warmstart_params(train_solves, seed=5))
+    hist = ws.fit(X, T, epochs=epochs, batch=64, lr=1e-3, seed=6)
+    torch.cuda.synchronize()
+    out = {"workload": "quarter annulus r_in~U(0.8,1.2) r_out~U(1.8,2.2) h=1, exp/gauss, L~logU(0.1,2); "
+                       "coarse p=3 16^3 (6,859 dof), fine p=3 48^3 (132,651 dof), k=20 of a 32-vector start",
+           "train_solves": st["solves"], "train_targets_s": st["seconds"], "train_not_converged": st["not_converged"],
+           "epochs": epochs, "fit_s": ws.fit_seconds, "loss_first_last": [float(hist[0]), float(hist[-1])],
+           "network": "4 x 256 tanh, bfloat16 weights and layer inputs, float32 sums, %d parameters" % ws.net.nparam,
+           "eval": []}
+    del X, T
+    k = 20
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    for i, prm in enumerate(inputs.warmstart_params(n_eval, seed=6)):
+        fine = warmstart.problem(prm, 3, 48)
+        mixed = dict(method=1, precision=kl.KL_P_TC64)
+        tw, (ev_w, vec_w, iw) = timed(lambda: ws.solve(fine, prm, k, tol=TOL))
+        t32, (ev_r, _, i32) = timed(lambda: fine.eigs(k, TOL, block=32, want_vectors=False, **mixed))
+        t16, (_, _, i16) = timed(lambda: fine.eigs(k, TOL, block=16, want_vectors=False, **mixed))
+        # subspace of the prediction against the converged eigenvectors (diagnostic)
+        start = ws.start_block(fine, prm)
+        Qs, _ = torch.linalg.qr(start.T)
+        cosv = torch.linalg.svdvals(Qs.T @ vec_w.T).cpu().numpy()
+        row = {"kernel": prm["kernel"], "L": prm["L"], "r_in": prm["r_in"], "r_out": prm["r_out"],
+               "path": iw["path"], "warm_s": tw, "warm_applies": iw["applies"], "warm_restarts": iw["restarts"],
+               "warm_start_block_ms": iw.get("ms_start_block", iw.get("warm", {}).get("ms_start_block")),
+               "random32_s": t32, "random32_applies": i32["applies"], "random16_s": t16,
+               "random16_applies": i16["applies"], "gain_vs_random32": t32 / tw, "gain_vs_random16": t16 / tw,
+               "max_resid_warm": max(iw["resid"][:k]),
+               "max_rel_eig_diff_warm_vs_random": float(np.max(np.abs(ev_w - ev_r) / np.abs(ev_r))),
+               "prediction_max_sine_top20": float(np.sqrt(max(0.0, 1.0 - cosv.min() ** 2)))}
+        if i == 0:
+            tp, (ev_p, _, ip) = timed(lambda: fine.eigs(k, TOL, method=0, block=4, want_vectors=False))
+            row.update({"fp64_lanczos_s": tp, "fp64_lanczos_applies": ip["applies"], "gain_vs_fp64_lanczos": tp / tw,
+                        "max_rel_eig_diff_warm_vs_fp64": float(np.max(np.abs(ev_w - ev_p) / np.abs(ev_p)))})
+        out["eval"].append(row)
+        fine.close()
+    out["timing"] = "wall clock with a device synchronisation on both sides, one run each (warm includes " \
+                    "the network forward pass and the prolongation)"
     return out
 
 
@@ -379,6 +443,9 @@ def main():
     c4 = None
     if world == 1 and not args.no_c4:
         c4 = measure_c4(kl, inputs)
+    c5 = None
+    if world == 1 and not args.no_c5:
+        c5 = measure_c5(kl, inputs, args.c5_train_solves, args.c5_epochs, args.c5_eval)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -438,6 +505,8 @@ def main():
         line["c3_mixed_with_blocks"] = c3
     if c4:
         line["c4_batched_instances"] = c4
+    if c5:
+        line["c5_learned_warm_start"] = c5
     if cpu:
         line["cpu_baseline"] = cpu
     if rank == 0:

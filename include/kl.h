@@ -265,6 +265,45 @@ kl_status kl_eigs_batched(kl_handle* handles, int count, int k, double tol, cons
                           double* evals_host, double* const* evecs_dev, const int64_t* ldv, kl_eig_info* infos,
                           kl_status* statuses, kl_batch_info* binfo);
 
+/* ---- Learned warm start (no counterpart in the paper) ---------------------------------
+ * A multilayer perceptron maps problem parameters to k standard-form vectors on a coarse
+ * mesh; kl_prolong carries them exactly to a finer nested mesh, where they start kl_eigs
+ * (opts.start_dev, block k).  Weights and layer inputs are bfloat16, sums float32, hidden
+ * layers tanh, output linear; training minimises the mean of ||Y Y^T - V V^T||_F^2 / k over
+ * samples (V: orthonormal target vectors, Y: predicted vectors; invariant under rotations and
+ * sign flips of Y) with Adam (float32 master weights).  All device pointers are float32. */
+typedef struct kl_mlp_s* kl_mlp;
+
+/* n_in inputs, `depth` hidden layers of `width`, n_out outputs; weights uniform(+-sqrt(3/fan_in))
+ * from a splitmix64 stream of `seed`, biases 0.  KL_ERR_INVALID_ARG for non-positive sizes. */
+kl_status kl_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed, kl_mlp* out);
+kl_status kl_mlp_num_params(kl_mlp m, int64_t* n);
+/* Copy the float32 parameters (per layer: weights in x out row-major, then biases) to host
+ * (direction 0) or from host (direction 1; the bfloat16 copy is refreshed).  Synchronous. */
+kl_status kl_mlp_params(kl_mlp m, float* host, int direction);
+/* out_dev (batch x n_out) = network(x_dev (batch x n_in)).  Asynchronous on `stream`. */
+kl_status kl_mlp_forward(kl_mlp m, const float* x_dev, int batch, float* out_dev, void* stream);
+/* One forward and backward pass: per-sample losses to loss_dev (batch floats) and, when
+ * grad_host is not NULL, the gradient of the batch-mean loss (same layout as the parameters;
+ * synchronous then).  tgt_dev: batch x (k n), vector j of sample s at s*k*n + j*n; k n = n_out. */
+kl_status kl_mlp_loss_grad(kl_mlp m, const float* x_dev, const float* tgt_dev, int batch, int k, int n,
+                           float* loss_dev, float* grad_host, void* stream);
+/* `epochs` passes of Adam (learning rate lr) over `samples` rows in minibatches of `batch`
+ * (seeded shuffle; an incomplete last batch is skipped); loss_host (epochs doubles, may be NULL)
+ * receives each epoch's mean loss.  Synchronous on `stream`. */
+kl_status kl_mlp_train(kl_mlp m, const float* x_dev, const float* tgt_dev, int samples, int k, int n, int epochs,
+                       int batch, double lr, uint64_t seed, double* loss_host, void* stream);
+void kl_mlp_destroy(kl_mlp m);
+
+/* Exact prolongation of standard-form vectors (Sec. 4.1: v' = L^T v) from the trial space of
+ * `coarse` to that of `fine`: every direction must have the same degree and a fine element
+ * count that is a multiple of the coarse one (nested uniform knots), so each coarse spline is a
+ * fine spline (knot insertion); per direction Q_k = L_f^T P_k L_c^{-T} with P_k from collocation
+ * at the fine Greville points, applied as one contraction per direction.  v_dev: N_c x nvec,
+ * y_dev: N_f x nvec, leading dimensions N_c and N_f.  Synchronous on `stream` (the factors
+ * are uploaded per call and released once the contractions have run). */
+kl_status kl_prolong(kl_handle coarse, kl_handle fine, const double* v_dev, double* y_dev, int nvec, void* stream);
+
 /* The k (<= 64) largest eigenvalues of A~' (descending) to relative residual tol.
  * evals_host: k values (host).  evecs_dev: N x k orthonormal eigenvectors in standard
  * form (v'^T v' = I), leading dimension ldv (may be NULL).  info may be NULL.

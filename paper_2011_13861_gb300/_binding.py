@@ -80,6 +80,16 @@ SIGNATURES = {
                                        ctypes.POINTER(KLEigOpts), _vp, ctypes.POINTER(_vp), ctypes.POINTER(_c_int64),
                                        ctypes.POINTER(KLEigInfo), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(KLBatchInfo)]),
+    "kl_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.POINTER(_vp)]),
+    "kl_mlp_num_params": (ctypes.c_int, [_vp, ctypes.POINTER(_c_int64)]),
+    "kl_mlp_params": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "kl_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "kl_mlp_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "kl_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
+    "kl_mlp_destroy": (None, [_vp]),
+    "kl_prolong": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
     "kl_destroy": (None, [_vp]),
@@ -357,3 +367,90 @@ def eigs_batched(problems, k, tol=1e-8, method=0, block=4, ncv=0, maxiter=0, see
     return (ev, vecs, [_info_dict(infos[i], k, sts[i]) for i in range(n)], list(sts),
             {"rounds": bi.rounds, "cols_per_split": bi.cols_per_split, "ms_total": bi.ms_total,
              "ms_stage5": bi.ms_stage5, "requests": bi.requests})
+
+
+class MLP:
+    """The warm-start network (kl_mlp_*): n_in -> depth x width (tanh) -> n_out, bfloat16 weights and
+    layer inputs, float32 sums.  Inputs, targets and outputs are float32 CUDA tensors."""
+
+    def __init__(self, n_in, width, depth, n_out, seed=0):
+        h = ctypes.c_void_p()
+        _check(load().kl_mlp_create(int(n_in), int(width), int(depth), int(n_out), int(seed) & (2 ** 64 - 1),
+                                    ctypes.byref(h)))
+        self._h = h
+        self.n_in, self.width, self.depth, self.n_out = n_in, width, depth, n_out
+        n = _c_int64()
+        _check(load().kl_mlp_num_params(h, ctypes.byref(n)))
+        self.nparam = n.value
+
+    def layer_shapes(self):
+        dims = [self.n_in] + [self.width] * self.depth + [self.n_out]
+        return list(zip(dims[:-1], dims[1:]))
+
+    def get_params(self):
+        """Float32 parameters as lists (Ws, bs) of numpy arrays (W: in x out)."""
+        import numpy as np
+        flat = np.zeros(self.nparam, dtype=np.float32)
+        _check(load().kl_mlp_params(self._h, flat.ctypes.data_as(ctypes.c_void_p), 0))
+        return self._split(flat)
+
+    def set_params(self, Ws, bs):
+        import numpy as np
+        flat = np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32)])
+                               for W, b in zip(Ws, bs)])
+        _check(load().kl_mlp_params(self._h, flat.ctypes.data_as(ctypes.c_void_p), 1))
+
+    def _split(self, flat):
+        Ws, bs, o = [], [], 0
+        for a, b in self.layer_shapes():
+            Ws.append(flat[o:o + a * b].reshape(a, b))
+            o += a * b
+            bs.append(flat[o:o + b])
+            o += b
+        return Ws, bs
+
+    def forward(self, x, stream=None):
+        import torch
+        out = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        _check(load().kl_mlp_forward(self._h, _ptr(x), int(x.shape[0]), _ptr(out), _stream(stream)))
+        return out
+
+    def loss_grad(self, x, tgt, k, n, stream=None):
+        """Per-sample losses (tensor) and the gradient of the batch-mean loss as (dWs, dbs)."""
+        import numpy as np
+        import torch
+        loss = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        g = np.zeros(self.nparam, dtype=np.float32)
+        _check(load().kl_mlp_loss_grad(self._h, _ptr(x), _ptr(tgt), int(x.shape[0]), int(k), int(n), _ptr(loss),
+                                       g.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return loss, self._split(g)
+
+    def train(self, x, tgt, k, n, epochs, batch, lr, seed=0, stream=None):
+        """Adam epochs over the rows of x / tgt; returns the per-epoch mean losses."""
+        import numpy as np
+        hist = np.zeros(max(int(epochs), 1))
+        _check(load().kl_mlp_train(self._h, _ptr(x), _ptr(tgt), int(x.shape[0]), int(k), int(n), int(epochs),
+                                   int(batch), float(lr), int(seed) & (2 ** 64 - 1),
+                                   hist.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return hist[:int(epochs)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kl_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prolong(coarse, fine, v, stream=None):
+    """Standard-form vectors of `coarse`'s trial space carried exactly to `fine`'s (kl_prolong):
+    v (nvec, N_c) float64 CUDA tensor -> (nvec, N_f)."""
+    import torch
+    vb = KLProblem._block(v, coarse.N)
+    out = torch.empty((vb.shape[0], fine.N), dtype=torch.float64, device=vb.device)
+    _check(load().kl_prolong(coarse._h, fine._h, _ptr(vb), _ptr(out), int(vb.shape[0]), _stream(stream)))
+    return out if v.dim() > 1 else out.reshape(-1)

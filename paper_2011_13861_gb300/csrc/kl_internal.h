@@ -42,9 +42,11 @@ struct Direction {
     std::vector<double> xi;   // Greville abscissae of the interpolation space (nt)
     std::vector<double> C;    // C_k = B~_k^{-T} M_k L_k^{-T}, nt x n row-major
     std::vector<double> Linv; // L_k^{-1}, n x n row-major (lower triangular)
+    std::vector<double> L;    // L_k, Z_k = L_k L_k^T, n x n row-major (lower triangular)
 };
 
 kl_status build_direction(int p, int ne, int pt, int net, Direction* out);
+kl_status build_prolongation(const Direction& c, const Direction& f, std::vector<double>* Q);
 
 // tensor-product NURBS geometry map: knots per direction, control records (x, y, z, w),
 // direction 1 fastest; directions >= dim have one control point

@@ -227,6 +227,7 @@ kl_status build_direction(int p, int ne, int pt, int net, Direction* out) {
             Lk[size_t(i) * n + j] = t / ljj;
         }
     }
+    d.L = Lk;
     // L_k^{-1} by forward substitution on the identity
     d.Linv.assign(size_t(n) * n, 0.0);
     for (int c = 0; c < n; ++c) {
@@ -315,6 +316,58 @@ void nurbs_map_point(const NurbsMap& m, const double* xh, double* X, double* det
         *detDF = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) - D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
                  D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
     }
+}
+
+
+// Q = L_f^T P L_c^{-T} (n_f x n_c, row-major): the standard-form coefficients (Sec. 4.1) of every
+// coarse trial function in the fine trial space.  The spaces have the same degree and nested
+// uniform knots, so each coarse B-spline is a fine spline and P = B_f^{-1} B_c(x_f) holds its
+// fine coefficients exactly (interpolation at the fine Greville points, Sec. 4.2).
+kl_status build_prolongation(const Direction& c, const Direction& f, std::vector<double>* Q) {
+    if (c.p != f.p) return fail(KL_ERR_INVALID_ARG, "prolongation: the spaces must have the same degree");
+    if (f.ne % c.ne != 0) return fail(KL_ERR_INVALID_ARG, "prolongation: the fine mesh must refine the coarse one");
+    const int p = c.p;
+    const Space tc = make_space(p, c.ne), tf = make_space(p, f.ne);
+    const int nc = tc.n, nf = tf.n;
+    std::vector<double> xf(size_t(nf), 0.0);
+    for (int i = 0; i < nf; ++i) {
+        double s = 0.0;
+        for (int r = 1; r <= p; ++r) s += tf.t[size_t(i + r)];
+        xf[size_t(i)] = s / p;
+    }
+    std::vector<double> Bf(size_t(nf) * nf, 0.0), Bc(size_t(nf) * nc, 0.0), Nv(size_t(p) + 1);
+    for (int i = 0; i < nf; ++i) {
+        int s = find_span(tf.t, p, xf[size_t(i)]);
+        nonzero_basis(tf.t, p, s, xf[size_t(i)], Nv.data());
+        for (int r = 0; r <= p; ++r) Bf[size_t(i) * nf + (s - p + r)] = Nv[size_t(r)];
+        s = find_span(tc.t, p, xf[size_t(i)]);
+        nonzero_basis(tc.t, p, s, xf[size_t(i)], Nv.data());
+        for (int r = 0; r <= p; ++r) Bc[size_t(i) * nc + (s - p + r)] = Nv[size_t(r)];
+    }
+    if (!invert(Bf, nf)) return fail(KL_ERR_NUMERIC, "prolongation: fine collocation matrix is singular");
+    std::vector<double> P(size_t(nf) * nc, 0.0), T(size_t(nf) * nc, 0.0);
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nc; ++j) {
+            double s = 0.0;
+            for (int r = 0; r < nf; ++r) s += Bf[size_t(i) * nf + r] * Bc[size_t(r) * nc + j];
+            P[size_t(i) * nc + j] = s;
+        }
+    // T = P L_c^{-T}: T[i][j] = sum_r P[i][r] Linv_c[j][r]
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nc; ++j) {
+            double s = 0.0;
+            for (int r = 0; r <= j; ++r) s += P[size_t(i) * nc + r] * c.Linv[size_t(j) * nc + r];
+            T[size_t(i) * nc + j] = s;
+        }
+    // Q = L_f^T T: Q[i][j] = sum_{r >= i} L_f[r][i] T[r][j]
+    Q->assign(size_t(nf) * nc, 0.0);
+    for (int i = 0; i < nf; ++i)
+        for (int j = 0; j < nc; ++j) {
+            double s = 0.0;
+            for (int r = i; r < nf; ++r) s += f.L[size_t(r) * nf + i] * T[size_t(r) * nc + j];
+            (*Q)[size_t(i) * nc + j] = s;
+        }
+    return KL_OK;
 }
 
 }  // namespace kl

@@ -61,3 +61,18 @@ def batched_instances(count=64, seed=2011, ne_range=(8, 40), degrees=(2, 3), L_r
         L = float(np.exp(rng.uniform(np.log(L_range[0]), np.log(L_range[1]))))
         out.append({"dim": 3, "p": p, "ne": ne, "kernel": "exp" if i % 2 == 0 else "gauss", "L": L, "sigma": 1.0})
     return out
+
+
+def warmstart_params(count, seed, L_range=(0.1, 2.0), r_in_range=(0.8, 1.2), r_out_range=(1.8, 2.2)):
+    """Seeded parameter sets of the learned-warm-start workload (quarter annulus of height 1):
+    kernel exponential or Gaussian with probability 1/2 each, L log-uniform on L_range, inner
+    and outer radius uniform on their ranges, sigma 1.  Returns dicts with kernel, L, r_in, r_out."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        kern = "exp" if rng.random() < 0.5 else "gauss"
+        L = float(np.exp(rng.uniform(np.log(L_range[0]), np.log(L_range[1]))))
+        r_in = float(rng.uniform(*r_in_range))
+        r_out = float(rng.uniform(*r_out_range))
+        out.append({"kernel": kern, "L": L, "r_in": r_in, "r_out": r_out})
+    return out

@@ -1,0 +1,135 @@
+"""Learned warm start for the eigensolver (no counterpart in the paper).
+
+A small network maps the parameters of a quarter-annulus KL problem (correlation length L,
+kernel type, inner and outer radius) to k standard-form vectors of a coarse trial space
+(degree p, ne_c elements per direction).  It is trained on eigenvectors that the solver itself
+computes on coarse meshes, with the loss on orthogonal projectors (invariant under rotations
+and sign flips of the predicted vectors).  For a fine problem of the same degree whose
+element counts are multiples of ne_c, the prediction is carried exactly to the fine space
+(kl_prolong: every coarse spline is a fine spline) and becomes the start block of kl_eigs.
+When the warm-started solve does not converge within its restart budget, the problem is
+solved again from the seeded random start (the method without the network).
+
+Every numerical step runs in the library's kernels: the network's forward and backward
+passes and Adam (kl_mlp_*), the coarse solves, the prolongation and the fine solve; this
+module only builds the problems, moves tensors between them and keeps the bookkeeping.
+"""
+import math
+import time
+
+import numpy as np
+
+from . import _binding as B
+from .inputs import quarter_annulus_net
+
+N_FEATURES = 4
+
+
+def features(prm):
+    """Network inputs of one parameter set: log L, +1 (exponential) / -1 (Gaussian), 5 (r_in - 1),
+    5 (r_out - 2) (all of order one on the ranges used)."""
+    return [math.log(prm["L"]), 1.0 if prm["kernel"] == "exp" else -1.0, 5.0 * (prm["r_in"] - 1.0),
+            5.0 * (prm["r_out"] - 2.0)]
+
+
+def problem(prm, p, ne, height=1.0, sigma=1.0):
+    """The KL problem of one parameter set on the quarter annulus (degree p, ne elements per
+    direction, the NURBS net of quarter_annulus_net)."""
+    net = quarter_annulus_net(prm["r_in"], prm["r_out"], height, 3)
+    return B.KLProblem(3, p, ne, kernel=prm["kernel"], sigma=sigma, L=prm["L"], nurbs=net)
+
+
+class WarmStart:
+    """Network + coarse space.  k: number of predicted vectors (the start block width);
+    width x depth: hidden layers (tanh); seed: initial weights."""
+
+    def __init__(self, p=3, ne_coarse=16, k=32, width=256, depth=4, seed=5):
+        self.p, self.ne_c, self.k = int(p), int(ne_coarse), int(k)
+        self.n = (self.ne_c + self.p) ** 3          # open uniform knots: ne + p splines per direction
+        # targets are the eigenvectors scaled by sqrt(n) (entries of order one, like the outputs of
+        # the initial network); the projector loss is then n^2 times that of unit vectors
+        self.scale = math.sqrt(self.n)
+        self.net = B.MLP(N_FEATURES, width, depth, self.k * self.n, seed)
+        self.history = []
+
+    # ---- training data ------------------------------------------------------------------
+    def targets(self, params, tol=1e-6, block=16, precision=B.KL_P_TC64, maxiter=200):
+        """Solve every coarse problem for its k leading eigenvectors.  Returns (X, T, stats):
+        X (S, 4) and T (S, k n) float32 CUDA tensors (vector j of sample s at T[s, j n:(j+1) n])."""
+        import torch
+        X = torch.tensor([features(q) for q in params], dtype=torch.float32, device="cuda")
+        T = torch.empty((len(params), self.k * self.n), dtype=torch.float32, device="cuda")
+        applies, unconv = 0, 0
+        t0 = time.perf_counter()
+        for s, prm in enumerate(params):
+            pr = problem(prm, self.p, self.ne_c)
+            _, vecs, info = pr.eigs(self.k, tol=tol, method=1, block=block, precision=precision, maxiter=maxiter,
+                                    raise_on_nonconv=False, verify=True)
+            T[s] = (vecs * self.scale).to(torch.float32).reshape(-1)
+            applies += info["applies"]
+            unconv += int(info["converged"] < self.k)
+            pr.close()
+        torch.cuda.synchronize()
+        return X, T, {"solves": len(params), "seconds": time.perf_counter() - t0, "applies": applies,
+                      "not_converged": unconv}
+
+    def fit(self, X, T, epochs=200, batch=64, lr=1e-3, seed=6, stages=8):
+        """Adam epochs over (X, T) with a stepwise cosine decay of the learning rate (`stages`
+        constant pieces); returns the per-epoch mean loss of unit-norm vectors
+        (||Y Y^T - V V^T||_F^2 / k)."""
+        t0 = time.perf_counter()
+        stages = max(1, min(int(stages), int(epochs)))
+        hist = []
+        done = 0
+        for i in range(stages):
+            e = (epochs * (i + 1)) // stages - done
+            if e <= 0:
+                continue
+            lr_i = lr * 0.5 * (1.0 + math.cos(math.pi * (i + 0.5) / stages))
+            hist += list(self.net.train(X, T, self.k, self.n, e, min(batch, X.shape[0]), lr_i, seed + i))
+            done += e
+        hist = np.asarray(hist) / float(self.n) ** 2
+        self.history += list(hist)
+        self.fit_seconds = time.perf_counter() - t0
+        return hist
+
+    # ---- prediction ---------------------------------------------------------------------
+    def predict(self, prm):
+        """(k, n) float64 standard-form vectors of the coarse space."""
+        import torch
+        x = torch.tensor([features(prm)], dtype=torch.float32, device="cuda")
+        return self.net.forward(x).reshape(self.k, self.n).to(torch.float64) / self.scale
+
+    def start_block(self, fine, prm):
+        """The prediction carried to the trial space of `fine` (same degree, element counts a
+        multiple of the coarse ones): (k, N_fine) float64."""
+        coarse = problem(prm, self.p, self.ne_c)
+        try:
+            return B.prolong(coarse, fine, self.predict(prm))
+        finally:
+            coarse.close()
+
+    def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, **eig_kw):
+        """The nev leading eigenpairs of `fine` from the warm start (block = k); when that solve
+        has not converged after `maxiter` restarts, the seeded random start with the same options
+        and block width eig_kw['block'] (default 16) (fallback=True).  Returns (evals, evecs, info) with info['path'] = 'warm' | 'fallback'
+        and info['warm'] = the warm attempt's info."""
+        import torch
+        kw = dict(method=1, precision=B.KL_P_TC64)
+        kw.update(eig_kw)
+        fb_block = kw.pop("block", 16)
+        t0 = time.perf_counter()
+        start = self.start_block(fine, prm).contiguous()
+        torch.cuda.synchronize()
+        t_start = time.perf_counter() - t0
+        ev, vecs, info = fine.eigs(nev, tol=tol, block=self.k, start=start, maxiter=maxiter, raise_on_nonconv=False,
+                                   **kw)
+        info["ms_start_block"] = 1e3 * t_start
+        if info["converged"] >= nev or not fallback:
+            info["path"] = "warm"
+            return ev, vecs, info
+        ev2, vecs2, info2 = fine.eigs(nev, tol=tol, block=fb_block, **kw)
+        info2["path"] = "fallback"
+        info2["warm"] = info
+        return ev2, vecs2, info2
+
