@@ -207,7 +207,8 @@ typedef struct {
                              * 0 = the Lanczos estimates */
     int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default), KL_P_DF64 or KL_P_TC64;
                              * method 0: every application, method 1: the polish */
-    int polish_block;       /* method 1: width of the polish block (0 = k; k..48) */
+    int polish_block;       /* method 1: width of the polish block (k..48; 0 = k, or max(k, 32)
+                             * for KL_P_TC64, whose launches cost the same up to 32 vectors) */
     int polish_ncv;         /* method 1: polish basis size (0 = 3 x polish_block, at most 160) */
     int low_precision;      /* method 1: first-phase arithmetic, KL_P_FP32 (0 = default) or KL_P_TC32 */
 } kl_eig_opts;

@@ -343,7 +343,11 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     while ((m - keep) % b != 0) --keep;
 
     // float64 polish of the mixed method: one wide block over the kept float32 Ritz vectors
-    const int pol_b = std::min(std::max(o.polish_block > 0 ? o.polish_block : k, k), 48);
+    // a tensor-core float64-class launch costs the same for any width up to 32 vectors (the
+    // kernel values, which dominate, are shared by the block), so its polish block defaults to
+    // 32 with the vectors beyond k as guards; the other precisions default to k
+    const int pol_def = (o.precision == KL_P_TC64) ? std::max(k, int(std::min<int64_t>(32, N / 3))) : k;
+    const int pol_b = std::min(std::max(o.polish_block > 0 ? o.polish_block : pol_def, k), 48);
     int pol_m = o.polish_ncv > 0 ? o.polish_ncv / pol_b * pol_b : 3 * pol_b;
     pol_m = std::min(std::max(pol_m, 2 * pol_b), 160 / pol_b * pol_b);
 

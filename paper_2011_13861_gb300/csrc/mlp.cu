@@ -4,11 +4,19 @@
 // a loss on orthogonal projectors, ||Y Y^T - V V^T||_F^2 / k (rotation and sign invariant):
 //   loss = ||Y^T Y||_F^2 - 2 ||V^T Y||_F^2 + ||V^T V||_F^2,   dL/dY = 4 Y (Y^T Y) - 4 V (V^T Y).
 //
-// Kernels: a tiled GEMM for bfloat16 operands with float32 accumulation (any strides, so the
-// forward product and both backward products use it; long contractions are split over CTAs
-// and the splits added in a fixed order), bias + tanh epilogues, column sums, the per-sample
-// Gram matrices of the loss, the loss gradient, and Adam (Kingma and Ba 2015, Algorithm 1)
-// with float32 master weights and a bfloat16 copy refreshed after every step.
+// The three products of a training step run on the tensor cores (tcgen05, bfloat16 operands,
+// float32 accumulators in tensor memory), each written as C[m][n] = sum_k A[m][k] B[n][k] with
+// both operands K-contiguous, so that the large dimension (the output width) is the M side:
+//   forward   Z^T = W^T H^T        A = W^T (dout x din), B = H (batch x din)
+//   dW        dW^T = dZ^T H        A = dZ^T (dout x batch), B = H^T (din x batch)
+//   dH        dH^T = W dZ^T        A = W (din x dout), B = dZ (batch x dout), split over dout
+// Operands are staged by cp.async (16 bytes per thread) straight into the canonical no-swizzle
+// K-major layout, four stages deep; one thread issues the MMAs; four warps read the
+// accumulators back and store C transposed (coalesced along m).  Shapes the tensor-core kernel
+// cannot take (an inner dimension that is not a multiple of 8, e.g. the 4 network inputs) go
+// through a tiled float32-FMA GEMM.  The loss Gram matrices are split over row chunks and
+// reduced in a fixed order; Adam (Kingma and Ba 2015, Algorithm 1) keeps float32 master
+// weights and refreshes both bfloat16 copies (W and W^T) in one tiled pass per layer.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -17,32 +25,271 @@
 #include <vector>
 
 #include "kl_internal.h"
+#include "tc_common.cuh"
 
 struct kl_mlp_s {
     int n_in = 0, width = 0, depth = 0, n_out = 0;
     int layers = 0;
     std::vector<int> din, dout;                 // per layer
     std::vector<size_t> woff, boff;             // offsets into the flat parameter array
-    size_t nparam = 0;
+    std::vector<size_t> wtoff;                  // offsets of W^T (dout x din) in Wt, multiples of 8
+    size_t nparam = 0, nwt = 0;
     float* P = nullptr;                         // float32 master parameters (weights then biases per layer)
     float* G = nullptr;                         // gradients
     float* M = nullptr;                         // Adam first moments
     float* V = nullptr;                         // Adam second moments
-    __nv_bfloat16* Wb = nullptr;                // bfloat16 copy of the parameters
+    __nv_bfloat16* Wb = nullptr;                // bfloat16 copy of the parameters (parameter layout)
+    __nv_bfloat16* Wt = nullptr;                // bfloat16 W^T per layer
     int t = 0;                                  // Adam step
-    kl::DevBuf act, actb, dz, dzb, part, gram, lossbuf;
+    int cap = 0;                                // batch the activation buffers hold
+    std::vector<size_t> aoff;                   // per level 0..layers: offset of [batch][d] activations
+    kl::DevBuf hf, hb, ht, dzf, dzb, dzt, dh, part, gpart, gram, status;
 };
 
 namespace kl {
 namespace {
 
+using bf16 = __nv_bfloat16;
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------------------
+// tensor-core GEMM: C[m][n] = sum_{k in split z} A[m*lda + k] B[n*ldb + k]
+// ---------------------------------------------------------------------------------------
+constexpr int kTcM = 128, kTcK = 64, kTcStages = 4, kTcLag = kTcStages - 1, kTcThreads = 160;
+constexpr int kTcAStage = kTcM * kTcK * 2;                    // 16 KB
+constexpr int kTcMaxSmem = kTcStages * (kTcAStage + 256 * kTcK * 2) + 256;
+
+struct TcArgs {
+    int M, N, K;
+    const bf16* A;
+    int64_t lda;
+    const bf16* B;
+    int64_t ldb;
+    int NT;               // N tile (multiple of 16, at most 256)
+    int tmem_cols;        // power of two >= max(32, NT)
+    int kchunk;           // K range per split (multiple of kTcK)
+    const float* bias;    // per m (forward), or null
+    int act;              // 1: tanh
+    float* out;           // out[(z * N + n) * ldo + m]
+    bf16* outb;           // optional bfloat16 copy (same indexing)
+    int64_t ldo;
+    int* status;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+// one stage of rows [r0, r0 + rows) x K columns [kb, kb + 64) of a K-contiguous operand into the
+// no-swizzle K-major layout (16-column sub-tiles of rows * 32 bytes); rows beyond `valid_rows`
+// and columns beyond k1 are zero-filled
+__device__ __forceinline__ void stage_rows(uint32_t dst, const bf16* __restrict__ X, int64_t ld, int r0, int rows,
+                                           int valid_rows, int kb, int k1, int tid) {
+    const int sub = rows * 32;
+    for (int c = tid; c < rows * 8; c += 128) {
+        const int r = c >> 3, kc = c & 7;
+        const int k = kb + kc * 8;
+        const int row = r0 + r;
+        const bool v = (row < valid_rows) && (k < k1);
+        const bf16* src = v ? X + int64_t(row) * ld + k : X;
+        cp_async16(dst + (kc >> 1) * sub + (r >> 3) * 256 + (kc & 1) * 128 + (r & 7) * 16, src, v ? 16u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(TcArgs a) {
+    using namespace kl::tc;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NT = a.NT;
+    const int stage_bytes = kTcAStage + NT * kTcK * 2;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + kTcStages * stage_bytes;     // full[S], empty[S], done
+    const uint32_t bar_full = bar0, bar_empty = bar0 + 8 * kTcStages, bar_done = bar0 + 16 * kTcStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kTcStages * stage_bytes + 16 * kTcStages + 8);
+    int* s_fail = reinterpret_cast<int*>(smem + kTcStages * stage_bytes + 16 * kTcStages + 16);
+
+    const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * NT, z = blockIdx.z;
+    const int k0 = z * a.kchunk;
+    const int k1 = min(a.K, k0 + a.kchunk);
+    const int nk = (k1 - k0 + kTcK - 1) / kTcK;
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(bar_full + 8 * s, 128);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_done, 1);
+        *s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 4) tmem_alloc(smem_u32(tmem_slot), uint32_t(a.tmem_cols));
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ---------------- producers, then epilogue ----------------
+        bool ok = true;
+        int arrived = 0;
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % kTcStages;
+            if (i >= kTcStages) {
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * st, uint32_t(((i / kTcStages) - 1) & 1)));
+                if (!ok) break;
+            }
+            const int kb = k0 + i * kTcK;
+            const uint32_t sa = sbase + st * stage_bytes;
+            stage_rows(sa, a.A, a.lda, m0, kTcM, a.M, kb, k1, tid);
+            stage_rows(sa + kTcAStage, a.B, a.ldb, n0, NT, a.N, kb, k1, tid);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            if (i >= kTcLag) {
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcLag) : "memory");
+                fence_proxy_async();
+                mbar_arrive(bar_full + 8 * ((i - kTcLag) % kTcStages));
+                arrived = i - kTcLag + 1;
+            }
+        }
+        // every copy of this thread has landed before the CTA can leave
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        fence_proxy_async();
+        if (ok) {
+            for (int j = arrived; j < nk; ++j) mbar_arrive(bar_full + 8 * (j % kTcStages));
+            ok = __all_sync(0xffffffffu, mbar_wait(bar_done, 0));
+        }
+        if (ok) {
+            fence_after_sync();
+            const int m = m0 + warp * 32 + lane;
+            for (int c0 = 0; c0 < NT; c0 += 16) {
+                uint32_t d[16];
+                const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];\n"
+                    : "=r"(d[0]), "=r"(d[1]), "=r"(d[2]), "=r"(d[3]), "=r"(d[4]), "=r"(d[5]), "=r"(d[6]), "=r"(d[7]),
+                      "=r"(d[8]), "=r"(d[9]), "=r"(d[10]), "=r"(d[11]), "=r"(d[12]), "=r"(d[13]), "=r"(d[14]),
+                      "=r"(d[15])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (m < a.M) {
+                    const float bm = a.bias ? a.bias[m] : 0.f;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = n0 + c0 + j;
+                        if (n < a.N) {
+                            float v = __uint_as_float(d[j]) + bm;
+                            if (a.act) v = tanhf(v);
+                            const int64_t o = (int64_t(z) * a.N + n) * a.ldo + m;
+                            a.out[o] = v;
+                            if (a.outb) a.outb[o] = __float2bfloat16_rn(v);
+                        }
+                    }
+                }
+            }
+        }
+        if (!ok) atomicExch(s_fail, 1);
+    } else if (lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_bf16(kTcM, NT);
+        bool ok = true;
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % kTcStages;
+            ok = mbar_wait(bar_full + 8 * st, uint32_t((i / kTcStages) & 1));
+            if (!ok) break;
+            fence_after_sync();
+            const uint32_t sa = sbase + st * stage_bytes, sb = sa + kTcAStage;
+#pragma unroll
+            for (int t = 0; t < kTcK / 16; ++t) {
+                const uint64_t ad = make_desc(sa + t * (kTcM * 32), 128, 256);
+                const uint64_t bd = make_desc(sb + t * (NT * 32), 128, 256);
+                mma_bf16(tmem, ad, bd, idesc, (i > 0 || t > 0) ? 1u : 0u);
+            }
+            mma_commit(bar_empty + 8 * st);
+        }
+        // arrives once every MMA issued above has completed
+        mma_commit(bar_done);
+        if (!ok) atomicExch(s_fail, 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 4) {
+        // the accumulators may be released only after the MMAs have finished
+        if (lane == 0 && *s_fail) mbar_wait(bar_done, 0);
+        __syncwarp();
+        fence_after_sync();
+        tmem_dealloc(tmem, uint32_t(a.tmem_cols));
+    }
+    if (tid == 0 && *s_fail) atomicExch(a.status, int(KL_ERR_TIMEOUT));
+}
+
+bool tc_shape_ok(int K, const void* A, int64_t lda, const void* B, int64_t ldb) {
+    return K > 0 && K % 8 == 0 && lda % 8 == 0 && ldb % 8 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+}
+
+// launches the tensor-core GEMM over `splits` K ranges of kchunk (a multiple of 64); split z
+// writes to out + z * N * ldo
+kl_status tc_gemm(int M, int N, int K, const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int kchunk,
+                  const float* bias, int act, float* out, bf16* outb, int64_t ldo, int* status, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        KL_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem));
+        attr = true;
+    }
+    if (M < 1 || N < 1 || K < 1 || kchunk < kTcK || kchunk % kTcK != 0)
+        return fail(KL_ERR_INVALID_ARG, "tensor-core GEMM: bad shape");
+    TcArgs a;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.A = A;
+    a.lda = lda;
+    a.B = B;
+    a.ldb = ldb;
+    a.NT = int(std::min<size_t>(256, round_up(size_t(N), 16)));
+    a.tmem_cols = 32;
+    while (a.tmem_cols < a.NT) a.tmem_cols *= 2;
+    a.kchunk = kchunk;
+    a.bias = bias;
+    a.act = act;
+    a.out = out;
+    a.outb = outb;
+    a.ldo = ldo;
+    a.status = status;
+    const int splits = (K + kchunk - 1) / kchunk;
+    const size_t smem = size_t(kTcStages) * (kTcAStage + size_t(a.NT) * kTcK * 2) + 256;
+    dim3 grid((M + kTcM - 1) / kTcM, (N + a.NT - 1) / a.NT, splits);
+    tc_gemm_kernel<<<grid, kTcThreads, smem, s>>>(a);
+    KL_CUDA(cudaGetLastError());
+    count_launches(1);
+    return KL_OK;
+}
+
+// K range per split for a contraction of length K producing `tiles` output tiles: about two
+// CTAs per SM, at least two K blocks per split
+int tc_kchunk(int tiles, int K) {
+    const int want = num_sms() * 2;
+    int sp = 1;
+    if (tiles < want && K > 4 * kTcK) {
+        sp = (want + tiles - 1) / tiles;
+        sp = std::min(sp, (K + 2 * kTcK - 1) / (2 * kTcK));
+        sp = std::max(sp, 1);
+    }
+    return int(round_up(size_t((K + sp - 1) / sp), kTcK));
+}
+
+// ---------------------------------------------------------------------------------------
+// float32-FMA GEMM for shapes the tensor-core kernel does not take
+// ---------------------------------------------------------------------------------------
 constexpr int kBM = 64, kBN = 64, kBK = 16, kGemmThreads = 256;
 
 // C[m][n] (+)= sum_k A(m,k) B(k,n) over k in [k0, k1); A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn].
 // Output of split z to out + z * M * N (row-major, float32).
 __global__ void __launch_bounds__(kGemmThreads)
-gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64_t sam, int64_t sak,
-                 const __nv_bfloat16* __restrict__ B, int64_t sbk, int64_t sbn, float* __restrict__ out, int kchunk) {
+gemm_bf16_kernel(int M, int N, int K, const bf16* __restrict__ A, int64_t sam, int64_t sak,
+                 const bf16* __restrict__ B, int64_t sbk, int64_t sbn, float* __restrict__ out, int kchunk) {
     __shared__ float sA[kBK][kBM + 1];
     __shared__ float sB[kBK][kBN + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -65,15 +312,15 @@ gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
-            float a[4], b[4];
+            float av[4], bv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sA[kk][ty * 4 + i];
+            for (int i = 0; i < 4; ++i) av[i] = sA[kk][ty * 4 + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = sB[kk][tx * 4 + j];
+            for (int j = 0; j < 4; ++j) bv[j] = sB[kk][tx * 4 + j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -92,7 +339,7 @@ gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int64
 
 // out[m][n] = act(sum_z part[z][m][n] + bias[n]) (fixed split order); optional bfloat16 copy
 __global__ void gemm_epilogue(const float* __restrict__ part, int splits, int M, int N, const float* __restrict__ bias,
-                              int tanh_act, float* __restrict__ out, __nv_bfloat16* __restrict__ outb) {
+                              int tanh_act, float* __restrict__ out, bf16* __restrict__ outb) {
     const size_t total = size_t(M) * N;
     for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
         float s = 0.f;
@@ -104,19 +351,37 @@ __global__ void gemm_epilogue(const float* __restrict__ part, int splits, int M,
     }
 }
 
-// dz = dh * (1 - h^2) with h = tanh(z) kept from the forward pass; bfloat16 copy
-__global__ void tanh_backward(const float* __restrict__ dh, const float* __restrict__ h, size_t n, float* __restrict__ dz,
-                              __nv_bfloat16* __restrict__ dzb) {
-    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-        const float v = dh[i] * (1.f - h[i] * h[i]);
+// dz[b][j] = (sum_z part[z][b][j]) * (1 - h[b][j]^2) (fixed split order); bfloat16 copy
+__global__ void split_tanh_backward(const float* __restrict__ part, int splits, size_t total,
+                                    const float* __restrict__ h, float* __restrict__ dz, bf16* __restrict__ dzb) {
+    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[size_t(z) * total + i];
+        const float v = s * (1.f - h[i] * h[i]);
         dz[i] = v;
         dzb[i] = __float2bfloat16_rn(v);
     }
 }
 
-__global__ void to_bf16(const float* __restrict__ x, size_t n, __nv_bfloat16* __restrict__ y) {
+__global__ void to_bf16(const float* __restrict__ x, size_t n, bf16* __restrict__ y) {
     for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
         y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// dst[c][r] = src[r][c] for r < rows, 0 for rows <= r < ldd (32 x 32 tiles through shared memory)
+__global__ void transpose_bf16(const bf16* __restrict__ src, int rows, int cols, int64_t lds, bf16* __restrict__ dst,
+                               int64_t ldd) {
+    __shared__ bf16 tile[32][34];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? src[int64_t(r) * lds + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < ldd) dst[int64_t(c) * ldd + r] = tile[threadIdx.x][i];
+    }
 }
 
 // db[n] = sum over rows m of dz[m][n] (fixed order)
@@ -128,65 +393,129 @@ __global__ void column_sums(const float* __restrict__ dz, int M, int N, float* _
     }
 }
 
-// per sample s (one CTA): YtY = Y^T Y and VtY = V^T Y (k x k), Y[i][a] = out[s][a*n + i],
-// V[i][a] = tgt[s][a*n + i]; loss[s] = (||YtY||^2 - 2 ||VtY||^2 + ||V^T V||^2) / k
-__global__ void loss_gram(const float* __restrict__ out, const float* __restrict__ tgt, int n, int k,
-                          float* __restrict__ gram, float* __restrict__ loss) {
-    extern __shared__ float sg[];        // YtY, VtY, VtV: 3 k*k
-    const int s = blockIdx.x;
+// ---------------------------------------------------------------------------------------
+// projector loss
+// ---------------------------------------------------------------------------------------
+// per sample s and row chunk c: partial Y^T Y, V^T Y, V^T V over rows [c*ch, c*ch + ch), with
+// Y[i][a] = out[s][a*n + i], V[i][a] = tgt[s][a*n + i]; gp[((s*nch + c)*3 + w)*k*k + a*k + b]
+__global__ void loss_gram_partial(const float* __restrict__ out, const float* __restrict__ tgt, int n, int k, int ch,
+                                  float* __restrict__ gp) {
+    extern __shared__ float sh[];          // Y chunk then V chunk, k rows of ch + 1
+    const int s = blockIdx.y, c = blockIdx.x, nch = gridDim.x;
+    const int i0 = c * ch, ld = ch + 1;
+    float* Ys = sh;
+    float* Vs = sh + k * ld;
     const float* Y = out + size_t(s) * k * n;
     const float* V = tgt + size_t(s) * k * n;
-    const int kk = k * k;
-    for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
-        const int which = e / kk, ab = e - which * kk, a = ab / k, b = ab - a * k;
-        const float* X1 = which == 0 ? Y : V;
-        const float* X2 = which == 2 ? V : Y;
-        float acc = 0.f;
-        for (int i = 0; i < n; ++i) acc = fmaf(X1[size_t(a) * n + i], X2[size_t(b) * n + i], acc);
-        sg[e] = acc;
+    for (int e = threadIdx.x; e < k * ch; e += blockDim.x) {
+        const int a = e / ch, ii = e - a * ch;
+        const int i = i0 + ii;
+        Ys[a * ld + ii] = i < n ? Y[size_t(a) * n + i] : 0.f;
+        Vs[a * ld + ii] = i < n ? V[size_t(a) * n + i] : 0.f;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) gram[size_t(s) * 2 * kk + e] = sg[e];
-    if (threadIdx.x == 0) {
-        float l = 0.f;
-        for (int e = 0; e < kk; ++e) l += sg[e] * sg[e] - 2.f * sg[kk + e] * sg[kk + e] + sg[2 * kk + e] * sg[2 * kk + e];
-        loss[s] = l / float(k);
-    }
-}
-
-// dY[s][b*n + i] = scale * (4 sum_a Y[i][a] YtY[a][b] - 4 sum_a V[i][a] VtY[a][b])
-__global__ void loss_grad(const float* __restrict__ out, const float* __restrict__ tgt, const float* __restrict__ gram,
-                          int n, int k, int samples, float scale, float* __restrict__ dy, __nv_bfloat16* __restrict__ dyb) {
-    const size_t total = size_t(samples) * k * n;
     const int kk = k * k;
-    for (size_t idx = blockIdx.x * size_t(blockDim.x) + threadIdx.x; idx < total; idx += size_t(gridDim.x) * blockDim.x) {
-        const size_t s = idx / (size_t(k) * n);
-        const size_t r = idx - s * size_t(k) * n;
-        const int b = int(r / n), i = int(r - size_t(b) * n);
-        const float* Y = out + s * k * n;
-        const float* V = tgt + s * k * n;
-        const float* YtY = gram + s * 2 * kk;
-        const float* VtY = YtY + kk;
+    for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        const int w = e / kk, ab = e - w * kk, a = ab / k, b = ab - a * k;
+        const float* X1 = (w == 0 ? Ys : Vs) + a * ld;
+        const float* X2 = (w == 2 ? Vs : Ys) + b * ld;
         float acc = 0.f;
-        for (int a = 0; a < k; ++a) acc = fmaf(Y[size_t(a) * n + i], YtY[a * k + b], fmaf(-V[size_t(a) * n + i], VtY[a * k + b], acc));
-        const float g = 4.f * scale * acc;
-        dy[idx] = g;
-        dyb[idx] = __float2bfloat16_rn(g);
+        for (int ii = 0; ii < ch; ++ii) acc = fmaf(X1[ii], X2[ii], acc);
+        gp[(size_t(s) * nch + c) * 3 * kk + e] = acc;
     }
 }
 
-__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                            __nv_bfloat16* __restrict__ pb, size_t n, float lr, float b1, float b2, float eps, float c1,
-                            float c2) {
-    for (size_t i = blockIdx.x * size_t(blockDim.x) + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        p[i] = pi;
-        pb[i] = __float2bfloat16_rn(pi);
+// per sample (one CTA of 256 threads): chunks summed in order; gram[s] = (Y^T Y, V^T Y);
+// loss[s] = (||Y^T Y||^2 - 2 ||V^T Y||^2 + ||V^T V||^2) / k (fixed-order tree)
+__global__ void loss_gram_reduce(const float* __restrict__ gp, int nch, int k, float* __restrict__ gram,
+                                 float* __restrict__ loss) {
+    __shared__ float red[256];
+    const int s = blockIdx.x, kk = k * k;
+    float l = 0.f;
+    for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        float acc = 0.f;
+        for (int c = 0; c < nch; ++c) acc += gp[(size_t(s) * nch + c) * 3 * kk + e];
+        const int w = e / kk;
+        if (w < 2) gram[size_t(s) * 2 * kk + e] = acc;
+        l += (w == 1 ? -2.f : 1.f) * acc * acc;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss[s] = red[0] / float(k);
+}
+
+// dY[s][b*n + i] = scale * (4 sum_a Y[i][a] YtY[a][b] - 4 sum_a V[i][a] VtY[a][b]);
+// thread = row i, block.y = 8 samples
+template <int KMAX>
+__global__ void loss_grad(const float* __restrict__ out, const float* __restrict__ tgt, const float* __restrict__ gram,
+                          int n, int k, int samples, float scale, float* __restrict__ dy, bf16* __restrict__ dyb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int kk = k * k;
+    const int s1 = min(samples, int(blockIdx.y) * 8 + 8);
+    for (int s = blockIdx.y * 8; s < s1; ++s) {
+        const float* Y = out + size_t(s) * k * n + i;
+        const float* V = tgt + size_t(s) * k * n + i;
+        const float* YtY = gram + size_t(s) * 2 * kk;
+        const float* VtY = YtY + kk;
+        float acc[KMAX];
+#pragma unroll
+        for (int b = 0; b < KMAX; ++b) acc[b] = 0.f;
+        for (int a = 0; a < k; ++a) {
+            const float ya = Y[size_t(a) * n], va = V[size_t(a) * n];
+#pragma unroll
+            for (int b = 0; b < KMAX; ++b)
+                if (b < k) acc[b] = fmaf(ya, YtY[a * k + b], fmaf(-va, VtY[a * k + b], acc[b]));
+        }
+        float* d = dy + size_t(s) * k * n + i;
+        bf16* db = dyb + size_t(s) * k * n + i;
+#pragma unroll
+        for (int b = 0; b < KMAX; ++b)
+            if (b < k) {
+                const float g = 4.f * scale * acc[b];
+                d[size_t(b) * n] = g;
+                db[size_t(b) * n] = __float2bfloat16_rn(g);
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Adam and the bfloat16 copies
+// ---------------------------------------------------------------------------------------
+// one layer's (din + 1) x dout block of the flat parameters (the bias is row din); update = 0
+// only refreshes Wb and Wt from P.  32 x 32 tiles, W^T written through shared memory.
+__global__ void adam_layer(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ Mo,
+                           float* __restrict__ Vo, bf16* __restrict__ Wb, bf16* __restrict__ Wt, size_t woff, int din,
+                           int dout, int update, float lr, float b1, float b2, float eps, float c1, float c2) {
+    __shared__ bf16 tile[32][34];
+    const int o0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int j = j0 + r, o = o0 + threadIdx.x;
+        if (j <= din && o < dout) {
+            const size_t idx = woff + size_t(j) * dout + o;
+            float p = P[idx];
+            if (update) {
+                const float gi = G[idx];
+                const float mi = b1 * Mo[idx] + (1.f - b1) * gi;
+                const float vi = b2 * Vo[idx] + (1.f - b2) * gi * gi;
+                Mo[idx] = mi;
+                Vo[idx] = vi;
+                p = p - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+                P[idx] = p;
+            }
+            const bf16 pb = __float2bfloat16_rn(p);
+            Wb[idx] = pb;
+            tile[r][threadIdx.x] = pb;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int o = o0 + r, j = j0 + threadIdx.x;
+        if (o < dout && j < din) Wt[size_t(o) * din + j] = tile[threadIdx.x][r];
     }
 }
 
@@ -213,9 +542,9 @@ int blocks_for(size_t n) {
     return int(b < 1 ? 1 : b);
 }
 
-// out (+ bias, act) = A x B with the strides described at gemm_bf16_kernel
-kl_status gemm(kl_mlp m, int M, int N, int K, const __nv_bfloat16* A, int64_t sam, int64_t sak, const __nv_bfloat16* B,
-               int64_t sbk, int64_t sbn, const float* bias, int act, float* out, __nv_bfloat16* outb, cudaStream_t s) {
+// float32-FMA product out (+ bias, act) = A x B with the strides described at gemm_bf16_kernel
+kl_status gemm(kl_mlp m, int M, int N, int K, const bf16* A, int64_t sam, int64_t sak, const bf16* B, int64_t sbk,
+               int64_t sbn, const float* bias, int act, float* out, bf16* outb, cudaStream_t s) {
     const int tiles = ((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
     int splits = 1;
     const int want = num_sms() * 4;
@@ -240,87 +569,162 @@ kl_status gemm(kl_mlp m, int M, int N, int K, const __nv_bfloat16* A, int64_t sa
     return KL_OK;
 }
 
-size_t act_floats(kl_mlp m, int batch) {
-    size_t t = size_t(batch) * m->n_in;
-    for (int l = 0; l < m->layers; ++l) t += size_t(batch) * m->dout[l];
-    return t;
+int level_dim(kl_mlp m, int l) { return l == 0 ? m->n_in : m->dout[size_t(l) - 1]; }
+
+// activation buffers for `batch` rows: per level l, [batch][d_l] float32 and bfloat16
+kl_status ensure_acts(kl_mlp m, int batch, cudaStream_t s) {
+    if (batch <= m->cap) return KL_OK;
+    KL_CUDA(cudaStreamSynchronize(s));
+    m->aoff.assign(size_t(m->layers) + 2, 0);
+    size_t o = 0, dmax = 0;
+    for (int l = 0; l <= m->layers; ++l) {
+        m->aoff[size_t(l)] = o;
+        o += round_up(size_t(batch) * level_dim(m, l), 64);
+        dmax = std::max(dmax, size_t(level_dim(m, l)));
+    }
+    m->aoff[size_t(m->layers) + 1] = o;
+    const size_t ldb = round_up(size_t(batch), 8);
+    KL_TRY(ensure(m->hf, o * sizeof(float)));
+    KL_TRY(ensure(m->hb, o * sizeof(bf16)));
+    KL_TRY(ensure(m->ht, dmax * ldb * sizeof(bf16)));
+    KL_TRY(ensure(m->dzf, size_t(batch) * dmax * sizeof(float)));
+    KL_TRY(ensure(m->dzb, size_t(batch) * dmax * sizeof(bf16)));
+    KL_TRY(ensure(m->dzt, dmax * ldb * sizeof(bf16)));
+    KL_TRY(ensure(m->dh, size_t(batch) * dmax * sizeof(float)));
+    m->cap = batch;
+    return KL_OK;
+}
+
+int* status_ptr(kl_mlp m) { return static_cast<int*>(m->status.ptr); }
+
+kl_status check_status(kl_mlp m, cudaStream_t s) {
+    int h = 0;
+    KL_CUDA(cudaMemcpyAsync(&h, m->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KL_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        cudaMemsetAsync(m->status.ptr, 0, sizeof(int), s);
+        return fail(KL_ERR_TIMEOUT, "warm-start network: a tensor-core wait gave up");
+    }
+    return KL_OK;
 }
 
 // forward for `batch` rows of x (float32, batch x n_in); activations kept for backward
 kl_status forward_impl(kl_mlp m, const float* x, int batch, cudaStream_t s) {
-    KL_TRY(grow(m->act, act_floats(m, batch) * sizeof(float), s));
-    KL_TRY(grow(m->actb, act_floats(m, batch) * sizeof(__nv_bfloat16), s));
-    float* a = static_cast<float*>(m->act.ptr);
-    __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(m->actb.ptr);
-    KL_CUDA(cudaMemcpyAsync(a, x, size_t(batch) * m->n_in * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    to_bf16<<<blocks_for(size_t(batch) * m->n_in), 256, 0, s>>>(a, size_t(batch) * m->n_in, ab);
+    KL_TRY(ensure_acts(m, batch, s));
+    float* hf = static_cast<float*>(m->hf.ptr);
+    bf16* hb = static_cast<bf16*>(m->hb.ptr);
+    KL_CUDA(cudaMemcpyAsync(hf, x, size_t(batch) * m->n_in * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    to_bf16<<<blocks_for(size_t(batch) * m->n_in), 256, 0, s>>>(hf, size_t(batch) * m->n_in, hb);
     KL_CUDA(cudaGetLastError());
-    size_t off = size_t(batch) * m->n_in;
-    size_t prev = 0;
+    count_launches(1);
     for (int l = 0; l < m->layers; ++l) {
-        const int di = m->din[l], dout = m->dout[l];
+        const int di = m->din[size_t(l)], dout = m->dout[size_t(l)];
         const bool last = (l == m->layers - 1);
-        KL_TRY(gemm(m, batch, dout, di, ab + prev, di, 1, m->Wb + m->woff[l], dout, 1, m->P + m->boff[l], last ? 0 : 1,
-                    a + off, ab + off, s));
-        prev = off;
-        off += size_t(batch) * dout;
+        const bf16* in = hb + m->aoff[size_t(l)];
+        float* of = hf + m->aoff[size_t(l) + 1];
+        bf16* ob = last ? nullptr : hb + m->aoff[size_t(l) + 1];
+        const bf16* wt = m->Wt + m->wtoff[size_t(l)];
+        if (tc_shape_ok(di, wt, di, in, di)) {
+            // Z^T = W^T H^T: m = output feature, n = sample; stored as Z[n][m]
+            KL_TRY(tc_gemm(dout, batch, di, wt, di, in, di, int(round_up(size_t(di), kTcK)), m->P + m->boff[size_t(l)],
+                           last ? 0 : 1, of, ob, dout, status_ptr(m), s));
+        } else {
+            KL_TRY(gemm(m, batch, dout, di, in, di, 1, m->Wb + m->woff[size_t(l)], dout, 1, m->P + m->boff[size_t(l)],
+                        last ? 0 : 1, of, ob, s));
+        }
     }
     return KL_OK;
 }
 
 // loss of the current outputs against targets (float32, batch x k*n) and backward pass into m->G
 kl_status backward_impl(kl_mlp m, const float* tgt, int batch, int k, int n, float* loss_dev, cudaStream_t s) {
-    float* a = static_cast<float*>(m->act.ptr);
-    __nv_bfloat16* ab = static_cast<__nv_bfloat16*>(m->actb.ptr);
-    std::vector<size_t> off(size_t(m->layers) + 1);
-    off[0] = 0;
-    size_t o = size_t(batch) * m->n_in;
-    for (int l = 0; l < m->layers; ++l) {
-        off[size_t(l) + 1] = o;
-        o += size_t(batch) * m->dout[l];
-    }
-    const float* out = a + off[size_t(m->layers)];
+    if (k > 64) return fail(KL_ERR_INVALID_ARG, "warm-start loss: at most 64 vectors per sample");
+    float* hf = static_cast<float*>(m->hf.ptr);
+    bf16* hb = static_cast<bf16*>(m->hb.ptr);
+    const float* out = hf + m->aoff[size_t(m->layers)];
+    float* dzf = static_cast<float*>(m->dzf.ptr);
+    bf16* dzb = static_cast<bf16*>(m->dzb.ptr);
+    bf16* dzt = static_cast<bf16*>(m->dzt.ptr);
+    bf16* ht = static_cast<bf16*>(m->ht.ptr);
+    const int ldb = int(round_up(size_t(batch), 8));
+
+    // Gram matrices in row chunks (shared memory: 2 k (ch + 1) floats <= 48 KB), reduced in order
+    int ch = int((48 * 1024 / (8 * size_t(k))) - 1);
+    ch = std::max(32, std::min(256, ch / 32 * 32));
+    const int nch = (n + ch - 1) / ch;
+    KL_TRY(grow(m->gpart, size_t(batch) * nch * 3 * k * k * sizeof(float), s));
     KL_TRY(grow(m->gram, size_t(batch) * 2 * k * k * sizeof(float), s));
-    const size_t smem = size_t(3) * k * k * sizeof(float);
-    if (smem > 48 * 1024) return fail(KL_ERR_INVALID_ARG, "warm-start loss: k too large");
-    loss_gram<<<batch, 256, smem, s>>>(out, tgt, n, k, static_cast<float*>(m->gram.ptr), loss_dev);
+    float* gp = static_cast<float*>(m->gpart.ptr);
+    float* gram = static_cast<float*>(m->gram.ptr);
+    loss_gram_partial<<<dim3(nch, batch), 256, size_t(2) * k * (ch + 1) * sizeof(float), s>>>(out, tgt, n, k, ch, gp);
     KL_CUDA(cudaGetLastError());
-    size_t maxw = size_t(m->n_out);
-    for (int l = 0; l < m->layers; ++l) maxw = std::max(maxw, size_t(m->din[l]));
-    KL_TRY(grow(m->dz, 2 * size_t(batch) * maxw * sizeof(float), s));
-    KL_TRY(grow(m->dzb, 2 * size_t(batch) * maxw * sizeof(__nv_bfloat16), s));
-    float* dz = static_cast<float*>(m->dz.ptr);
-    float* dh = dz + size_t(batch) * maxw;
-    __nv_bfloat16* dzb = static_cast<__nv_bfloat16*>(m->dzb.ptr);
-    loss_grad<<<blocks_for(size_t(batch) * k * n), 256, 0, s>>>(out, tgt, static_cast<float*>(m->gram.ptr), n, k, batch,
-                                                                1.f / float(k * batch), dz, dzb);
+    loss_gram_reduce<<<batch, 256, 0, s>>>(gp, nch, k, gram, loss_dev);
     KL_CUDA(cudaGetLastError());
-    count_launches(2);
+    const dim3 lg((n + 127) / 128, (batch + 7) / 8);
+    const float scale = 1.f / float(k * batch);
+    if (k <= 16)
+        loss_grad<16><<<lg, 128, 0, s>>>(out, tgt, gram, n, k, batch, scale, dzf, dzb);
+    else if (k <= 32)
+        loss_grad<32><<<lg, 128, 0, s>>>(out, tgt, gram, n, k, batch, scale, dzf, dzb);
+    else
+        loss_grad<64><<<lg, 128, 0, s>>>(out, tgt, gram, n, k, batch, scale, dzf, dzb);
+    KL_CUDA(cudaGetLastError());
+    count_launches(3);
+
     for (int l = m->layers - 1; l >= 0; --l) {
-        const int di = m->din[l], dout = m->dout[l];
-        // dW = h_{l-1}^T dz  (di x dout), db = column sums of dz
-        KL_TRY(gemm(m, di, dout, batch, ab + off[size_t(l)], 1, di, dzb, dout, 1, nullptr, 0, m->G + m->woff[l], nullptr, s));
-        column_sums<<<(dout + 255) / 256, 256, 0, s>>>(dz, batch, dout, m->G + m->boff[l]);
+        const int di = m->din[size_t(l)], dout = m->dout[size_t(l)];
+        const bf16* hin = hb + m->aoff[size_t(l)];
+        // dW^T = dZ^T H: A = dZ^T (dout x ldb), B = H^T (di x ldb), zero columns beyond the batch
+        transpose_bf16<<<dim3((dout + 31) / 32, (ldb + 31) / 32), dim3(32, 8), 0, s>>>(dzb, batch, dout, dout, dzt, ldb);
+        transpose_bf16<<<dim3((di + 31) / 32, (ldb + 31) / 32), dim3(32, 8), 0, s>>>(hin, batch, di, di, ht, ldb);
+        KL_CUDA(cudaGetLastError());
+        count_launches(2);
+        KL_TRY(tc_gemm(dout, di, ldb, dzt, ldb, ht, ldb, int(round_up(size_t(ldb), kTcK)), nullptr, 0,
+                       m->G + m->woff[size_t(l)], nullptr, dout, status_ptr(m), s));
+        column_sums<<<(dout + 255) / 256, 256, 0, s>>>(dzf, batch, dout, m->G + m->boff[size_t(l)]);
         KL_CUDA(cudaGetLastError());
         count_launches(1);
         if (l == 0) break;
-        // dh_{l-1} = dz W^T (batch x di), then through tanh
-        KL_TRY(gemm(m, batch, di, dout, dzb, dout, 1, m->Wb + m->woff[l], 1, dout, nullptr, 0, dh, nullptr, s));
-        tanh_backward<<<blocks_for(size_t(batch) * di), 256, 0, s>>>(dh, a + off[size_t(l)], size_t(batch) * di, dz, dzb);
+        // dH^T = W dZ^T, then through tanh: dz_{l-1} = dH (1 - h^2)
+        const float* hprev = hf + m->aoff[size_t(l)];
+        const bf16* w = m->Wb + m->woff[size_t(l)];
+        if (tc_shape_ok(dout, w, dout, dzb, dout)) {
+            const int tiles = ((di + kTcM - 1) / kTcM) * ((batch + 255) / 256);
+            const int kchunk = tc_kchunk(tiles, dout);
+            const int splits = (dout + kchunk - 1) / kchunk;
+            KL_TRY(grow(m->part, size_t(splits) * batch * di * sizeof(float), s));
+            float* part = static_cast<float*>(m->part.ptr);
+            KL_TRY(tc_gemm(di, batch, dout, w, dout, dzb, dout, kchunk, nullptr, 0, part, nullptr, di, status_ptr(m),
+                           s));
+            split_tanh_backward<<<blocks_for(size_t(batch) * di), 256, 0, s>>>(part, splits, size_t(batch) * di, hprev,
+                                                                               dzf, dzb);
+        } else {
+            float* dh = static_cast<float*>(m->dh.ptr);
+            KL_TRY(gemm(m, batch, di, dout, dzb, dout, 1, w, 1, dout, nullptr, 0, dh, nullptr, s));
+            split_tanh_backward<<<blocks_for(size_t(batch) * di), 256, 0, s>>>(dh, 1, size_t(batch) * di, hprev, dzf,
+                                                                               dzb);
+        }
         KL_CUDA(cudaGetLastError());
         count_launches(1);
     }
     return KL_OK;
 }
 
-kl_status adam_impl(kl_mlp m, double lr, cudaStream_t s) {
-    m->t += 1;
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = float(1.0 - std::pow(0.9, m->t)), c2 = float(1.0 - std::pow(0.999, m->t));
-    adam_kernel<<<blocks_for(m->nparam), 256, 0, s>>>(m->P, m->G, m->M, m->V, m->Wb, m->nparam, float(lr), b1, b2, 1e-8f,
-                                                      c1, c2);
-    KL_CUDA(cudaGetLastError());
-    count_launches(1);
+kl_status refresh_copies(kl_mlp m, int update, double lr, cudaStream_t s) {
+    float c1 = 1.f, c2 = 1.f;
+    if (update) {
+        m->t += 1;
+        c1 = float(1.0 - std::pow(0.9, m->t));
+        c2 = float(1.0 - std::pow(0.999, m->t));
+    }
+    for (int l = 0; l < m->layers; ++l) {
+        const int di = m->din[size_t(l)], dout = m->dout[size_t(l)];
+        adam_layer<<<dim3((dout + 31) / 32, (di + 1 + 31) / 32), dim3(32, 8), 0, s>>>(
+            m->P, m->G, m->M, m->V, m->Wb, m->Wt + m->wtoff[size_t(l)], m->woff[size_t(l)], di, dout, update, float(lr),
+            0.9f, 0.999f, 1e-8f, c1, c2);
+        KL_CUDA(cudaGetLastError());
+    }
+    count_launches(m->layers);
     return KL_OK;
 }
 
@@ -343,7 +747,7 @@ kl_status kl_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
     m->depth = depth;
     m->n_out = n_out;
     m->layers = depth + 1;
-    size_t off = 0;
+    size_t off = 0, toff = 0;
     for (int l = 0; l < m->layers; ++l) {
         m->din.push_back(l == 0 ? n_in : width);
         m->dout.push_back(l == m->layers - 1 ? n_out : width);
@@ -351,8 +755,11 @@ kl_status kl_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
         off += size_t(m->din.back()) * m->dout.back();
         m->boff.push_back(off);
         off += size_t(m->dout.back());
+        m->wtoff.push_back(toff);
+        toff += round_up(size_t(m->din.back()) * m->dout.back(), 8);
     }
     m->nparam = off;
+    m->nwt = toff;
     // initialisation: uniform(-a, a), a = sqrt(3 / fan_in) (unit variance per layer), biases 0;
     // splitmix64 stream from the seed, drawn on the host
     std::vector<float> P(off, 0.f);
@@ -369,8 +776,6 @@ kl_status kl_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
         for (size_t i = 0; i < size_t(m->din[size_t(l)]) * m->dout[size_t(l)]; ++i)
             P[m->woff[size_t(l)] + i] = float((2.0 * next() - 1.0) * a);
     }
-    std::vector<__nv_bfloat16> Pb(off);
-    for (size_t i = 0; i < off; ++i) Pb[i] = __float2bfloat16_rn(P[i]);
     kl_status st = KL_OK;
     auto chk = [&](cudaError_t e) {
         if (st == KL_OK && e != cudaSuccess) st = cuda_fail(e, "warm-start network allocation");
@@ -379,14 +784,18 @@ kl_status kl_mlp_create(int n_in, int width, int depth, int n_out, uint64_t seed
     chk(cudaMalloc(&m->G, off * sizeof(float)));
     chk(cudaMalloc(&m->M, off * sizeof(float)));
     chk(cudaMalloc(&m->V, off * sizeof(float)));
-    chk(cudaMalloc(&m->Wb, off * sizeof(__nv_bfloat16)));
+    chk(cudaMalloc(&m->Wb, off * sizeof(bf16)));
+    chk(cudaMalloc(&m->Wt, std::max<size_t>(toff, 8) * sizeof(bf16)));
+    if (st == KL_OK) st = ensure(m->status, sizeof(int));
     if (st == KL_OK) {
         chk(cudaMemcpy(m->P, P.data(), off * sizeof(float), cudaMemcpyHostToDevice));
-        chk(cudaMemcpy(m->Wb, Pb.data(), off * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
         chk(cudaMemset(m->M, 0, off * sizeof(float)));
         chk(cudaMemset(m->V, 0, off * sizeof(float)));
         chk(cudaMemset(m->G, 0, off * sizeof(float)));
+        chk(cudaMemset(m->status.ptr, 0, sizeof(int)));
     }
+    if (st == KL_OK) st = refresh_copies(m, 0, 0.0, nullptr);
+    if (st == KL_OK) chk(cudaStreamSynchronize(nullptr));
     if (st != KL_OK) {
         kl_mlp_destroy(m);
         return st;
@@ -401,9 +810,8 @@ kl_status kl_mlp_params(kl_mlp m, float* host, int direction) {
         KL_CUDA(cudaMemcpy(host, m->P, m->nparam * sizeof(float), cudaMemcpyDeviceToHost));
     } else {
         KL_CUDA(cudaMemcpy(m->P, host, m->nparam * sizeof(float), cudaMemcpyHostToDevice));
-        std::vector<__nv_bfloat16> Pb(m->nparam);
-        for (size_t i = 0; i < m->nparam; ++i) Pb[i] = __float2bfloat16_rn(host[i]);
-        KL_CUDA(cudaMemcpy(m->Wb, Pb.data(), m->nparam * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+        KL_TRY(refresh_copies(m, 0, 0.0, nullptr));
+        KL_CUDA(cudaStreamSynchronize(nullptr));
     }
     return KL_OK;
 }
@@ -419,37 +827,34 @@ kl_status kl_mlp_forward(kl_mlp m, const float* x_dev, int batch, float* out_dev
     if (batch == 0) return KL_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     KL_TRY(forward_impl(m, x_dev, batch, s));
-    size_t off = size_t(batch) * m->n_in;
-    for (int l = 0; l < m->layers - 1; ++l) off += size_t(batch) * m->dout[size_t(l)];
-    KL_CUDA(cudaMemcpyAsync(out_dev, static_cast<float*>(m->act.ptr) + off, size_t(batch) * m->n_out * sizeof(float),
-                            cudaMemcpyDeviceToDevice, s));
-    return KL_OK;
+    KL_CUDA(cudaMemcpyAsync(out_dev, static_cast<float*>(m->hf.ptr) + m->aoff[size_t(m->layers)],
+                            size_t(batch) * m->n_out * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return check_status(m, s);
 }
 
 kl_status kl_mlp_loss_grad(kl_mlp m, const float* x_dev, const float* tgt_dev, int batch, int k, int n, float* loss_dev,
                            float* grad_host, void* stream) {
-    if (!m || !x_dev || !tgt_dev || !loss_dev || batch < 1 || k < 1 || n < 1 || k * n != m->n_out)
+    if (!m || !x_dev || !tgt_dev || !loss_dev || batch < 1 || k < 1 || n < 1 || int64_t(k) * n != m->n_out)
         return fail(KL_ERR_INVALID_ARG, "bad argument (the output must hold k vectors of length n)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     KL_TRY(forward_impl(m, x_dev, batch, s));
     KL_TRY(backward_impl(m, tgt_dev, batch, k, n, loss_dev, s));
-    if (grad_host) {
-        KL_CUDA(cudaMemcpyAsync(grad_host, m->G, m->nparam * sizeof(float), cudaMemcpyDeviceToHost, s));
-        KL_CUDA(cudaStreamSynchronize(s));
-    }
-    return KL_OK;
+    if (grad_host) KL_CUDA(cudaMemcpyAsync(grad_host, m->G, m->nparam * sizeof(float), cudaMemcpyDeviceToHost, s));
+    return check_status(m, s);
 }
 
 kl_status kl_mlp_train(kl_mlp m, const float* x_dev, const float* tgt_dev, int samples, int k, int n, int epochs,
                        int batch, double lr, uint64_t seed, double* loss_host, void* stream) {
-    if (!m || !x_dev || !tgt_dev || samples < 1 || k < 1 || n < 1 || k * n != m->n_out || epochs < 0 || batch < 1)
+    if (!m || !x_dev || !tgt_dev || samples < 1 || k < 1 || n < 1 || int64_t(k) * n != m->n_out || epochs < 0 ||
+        batch < 1)
         return fail(KL_ERR_INVALID_ARG, "bad argument (the output must hold k vectors of length n)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (batch > samples) batch = samples;
+    const int nb = samples / batch;
     DevBuf xb, tb, lb, ib;
     KL_TRY(ensure(xb, size_t(batch) * m->n_in * sizeof(float)));
     KL_TRY(ensure(tb, size_t(batch) * m->n_out * sizeof(float)));
-    KL_TRY(ensure(lb, size_t(batch) * sizeof(float)));
+    KL_TRY(ensure(lb, size_t(std::max(1, epochs)) * nb * batch * sizeof(float)));
     KL_TRY(ensure(ib, size_t(samples) * sizeof(int)));
     std::vector<int> order(static_cast<size_t>(samples));
     for (int i = 0; i < samples; ++i) order[size_t(i)] = i;
@@ -460,40 +865,45 @@ kl_status kl_mlp_train(kl_mlp m, const float* x_dev, const float* tgt_dev, int s
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         return z ^ (z >> 31);
     };
-    std::vector<float> lh(static_cast<size_t>(samples));
-    for (int ep = 0; ep < epochs; ++ep) {
+    float* losses = static_cast<float*>(lb.ptr);
+    kl_status st = KL_OK;
+    for (int ep = 0; ep < epochs && st == KL_OK; ++ep) {
         // seeded shuffle (Fisher-Yates), one upload of the epoch's order
         for (int i = samples - 1; i > 0; --i) std::swap(order[size_t(i)], order[size_t(next() % uint64_t(i + 1))]);
         KL_CUDA(cudaStreamSynchronize(s));
         KL_CUDA(cudaMemcpy(ib.ptr, order.data(), size_t(samples) * sizeof(int), cudaMemcpyHostToDevice));
         const int* idx = static_cast<const int*>(ib.ptr);
-        double ep_loss = 0.0;
-        int used = 0;
-        for (int b0 = 0; b0 + batch <= samples; b0 += batch) {
+        for (int bi = 0; bi < nb && st == KL_OK; ++bi) {
+            const int b0 = bi * batch;
             gather_rows<<<blocks_for(size_t(batch) * m->n_in), 256, 0, s>>>(x_dev, idx + b0, batch, m->n_in,
                                                                              static_cast<float*>(xb.ptr));
             gather_rows<<<blocks_for(size_t(batch) * m->n_out), 256, 0, s>>>(tgt_dev, idx + b0, batch, m->n_out,
                                                                               static_cast<float*>(tb.ptr));
             KL_CUDA(cudaGetLastError());
             count_launches(2);
-            KL_TRY(forward_impl(m, static_cast<float*>(xb.ptr), batch, s));
-            KL_TRY(backward_impl(m, static_cast<float*>(tb.ptr), batch, k, n, static_cast<float*>(lb.ptr), s));
-            KL_TRY(adam_impl(m, lr, s));
-            if (loss_host) {
-                KL_CUDA(cudaMemcpyAsync(lh.data(), lb.ptr, size_t(batch) * sizeof(float), cudaMemcpyDeviceToHost, s));
-                KL_CUDA(cudaStreamSynchronize(s));
-                for (int j = 0; j < batch; ++j) ep_loss += lh[size_t(j)];
-                used += batch;
-            }
+            st = forward_impl(m, static_cast<float*>(xb.ptr), batch, s);
+            if (st == KL_OK)
+                st = backward_impl(m, static_cast<float*>(tb.ptr), batch, k, n, losses + (size_t(ep) * nb + bi) * batch,
+                                   s);
+            if (st == KL_OK) st = refresh_copies(m, 1, lr, s);
         }
-        if (loss_host) loss_host[ep] = used ? ep_loss / used : 0.0;
     }
-    KL_CUDA(cudaStreamSynchronize(s));
+    if (st == KL_OK) st = check_status(m, s);
+    if (st == KL_OK && loss_host && epochs > 0) {
+        std::vector<float> lh(size_t(epochs) * nb * batch);
+        KL_CUDA(cudaMemcpy(lh.data(), losses, lh.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (int ep = 0; ep < epochs; ++ep) {
+            double sum = 0.0;
+            for (size_t j = 0; j < size_t(nb) * batch; ++j) sum += lh[size_t(ep) * nb * batch + j];
+            loss_host[ep] = nb ? sum / (double(nb) * batch) : 0.0;
+        }
+    }
+    cudaStreamSynchronize(s);
     release(xb);
     release(tb);
     release(lb);
     release(ib);
-    return KL_OK;
+    return st;
 }
 
 void kl_mlp_destroy(kl_mlp m) {
@@ -503,13 +913,18 @@ void kl_mlp_destroy(kl_mlp m) {
     if (m->M) cudaFree(m->M);
     if (m->V) cudaFree(m->V);
     if (m->Wb) cudaFree(m->Wb);
-    release(m->act);
-    release(m->actb);
-    release(m->dz);
+    if (m->Wt) cudaFree(m->Wt);
+    release(m->hf);
+    release(m->hb);
+    release(m->ht);
+    release(m->dzf);
     release(m->dzb);
+    release(m->dzt);
+    release(m->dh);
     release(m->part);
+    release(m->gpart);
     release(m->gram);
-    release(m->lossbuf);
+    release(m->status);
     delete m;
 }
 

@@ -110,7 +110,8 @@ class WarmStart:
             coarse.close()
 
     def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, **eig_kw):
-        """The nev leading eigenpairs of `fine` from the warm start (block = k); when that solve
+        """The nev leading eigenpairs of `fine` from the warm start (block = k, basis 3 k unless
+        eig_kw['ncv'] says otherwise); when that solve
         has not converged after `maxiter` restarts, the seeded random start with the same options
         and block width eig_kw['block'] (default 16) (fallback=True).  Returns (evals, evecs, info) with info['path'] = 'warm' | 'fallback'
         and info['warm'] = the warm attempt's info."""
@@ -118,12 +119,14 @@ class WarmStart:
         kw = dict(method=1, precision=B.KL_P_TC64)
         kw.update(eig_kw)
         fb_block = kw.pop("block", 16)
+        warm_kw = dict(kw)
+        warm_kw.setdefault("ncv", max(3 * self.k, -(-(nev + 2 * self.k) // self.k) * self.k))
         t0 = time.perf_counter()
         start = self.start_block(fine, prm).contiguous()
         torch.cuda.synchronize()
         t_start = time.perf_counter() - t0
         ev, vecs, info = fine.eigs(nev, tol=tol, block=self.k, start=start, maxiter=maxiter, raise_on_nonconv=False,
-                                   **kw)
+                                   **warm_kw)
         info["ms_start_block"] = 1e3 * t_start
         if info["converged"] >= nev or not fallback:
             info["path"] = "warm"

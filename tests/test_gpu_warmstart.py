@@ -36,9 +36,12 @@ def abs_bound(Ws, x):
     return h
 
 
-# n_in, width, depth, k, n, batch: ragged tiles (width 80, batch 37), a split contraction in the
-# backward product dz W^T (n_out = 600 > 512) and, for batch 530, in dW = h^T dz as well
-SHAPES = [(4, 80, 3, 4, 150, 37), (4, 64, 1, 2, 40, 9), (5, 48, 2, 3, 200, 530)]
+# n_in, width, depth, k, n, batch: ragged tiles (width 80, batch 37, n_out 600 = 4 M-tiles + 88
+# rows), a split contraction over n_out in dH = dZ W^T, three N-tiles for batch 530, inner
+# dimensions that are not multiples of 8 (width 20, n_out 21: the float32-FMA GEMM), and a
+# first layer on the tensor cores (8 inputs)
+SHAPES = [(4, 80, 3, 4, 150, 37), (4, 64, 1, 2, 40, 9), (5, 48, 2, 3, 200, 530), (3, 20, 2, 3, 7, 5),
+          (8, 32, 1, 2, 64, 16)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "w%d-d%d-b%d" % (s[1], s[2], s[5]))
@@ -222,13 +225,15 @@ def test_warm_start_gains_over_random_start(kl, trained):
 
 
 def test_fallback_when_the_warm_solve_stalls(kl):
-    """An untrained network and a one-restart budget: the warm attempt does not converge and the
-    random-start solve takes over and converges."""
-    from paper_2011_13861_gb300 import inputs, warmstart
+    """An untrained network, a short correlation length (slowly decaying spectrum) and a budget of
+    one restart of the float64 iteration: the warm attempt does not converge and the random-start
+    solve takes over and converges."""
+    from paper_2011_13861_gb300 import warmstart
     ws = warmstart.WarmStart(seed=9, **SMALL)
-    prm = inputs.warmstart_params(1, seed=7)[0]
+    prm = {"kernel": "gauss", "L": 0.1, "r_in": 1.0, "r_out": 2.0}
     fine = warmstart.problem(prm, SMALL["p"], FINE_NE)
-    ev, vec, info = ws.solve(fine, prm, NEV, tol=1e-10, maxiter=1, ncv=24)
+    ev, vec, info = ws.solve(fine, prm, NEV, tol=1e-10, maxiter=1, ncv=24, block=SMALL["k"], method=0,
+                             precision=kl.KL_P_FP64)
     assert info["path"] == "fallback"
     assert info["warm"]["converged"] < NEV
     assert info["converged"] >= NEV
