@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the 132,651-point Gaussian cube (mixed precision with blocks of 16)")
     ap.add_argument("--no-c5", action="store_true", help="skip the learned warm start")
-    ap.add_argument("--c5-train-solves", type=int, default=400,
+    ap.add_argument("--c5-train-solves", type=int, default=2000,
                     help="coarse (16^3, p=3) training solves of the warm-start network (2000 = the full set)")
     ap.add_argument("--c5-epochs", type=int, default=100)
     ap.add_argument("--c5-eval", type=int, default=2, help="unseen parameter sets solved at 48^3")

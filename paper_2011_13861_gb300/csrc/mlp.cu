@@ -56,9 +56,10 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // ---------------------------------------------------------------------------------------
 // tensor-core GEMM: C[m][n] = sum_{k in split z} A[m*lda + k] B[n*ldb + k]
 // ---------------------------------------------------------------------------------------
-constexpr int kTcM = 128, kTcK = 64, kTcStages = 4, kTcLag = kTcStages - 1, kTcThreads = 160;
+constexpr int kTcM = 128, kTcK = 64, kTcMaxStages = 4, kTcThreads = 160;
 constexpr int kTcAStage = kTcM * kTcK * 2;                    // 16 KB
-constexpr int kTcMaxSmem = kTcStages * (kTcAStage + 256 * kTcK * 2) + 256;
+constexpr int kTcMaxSmem = kTcMaxStages * (kTcAStage + 256 * kTcK * 2) + 256;
+constexpr int kSmemPerSm = 233472;                            // 228 KB, of which 1 KB per CTA is reserved
 
 struct TcArgs {
     int M, N, K;
@@ -69,6 +70,7 @@ struct TcArgs {
     int NT;               // N tile (multiple of 16, at most 256)
     int tmem_cols;        // power of two >= max(32, NT)
     int kchunk;           // K range per split (multiple of kTcK)
+    int stages;           // 1..4 shared-memory stages of kTcK columns
     const float* bias;    // per m (forward), or null
     int act;              // 1: tanh
     float* out;           // out[(z * N + n) * ldo + m]
@@ -79,6 +81,16 @@ struct TcArgs {
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+// wait until at most n of this thread's cp.async groups are pending (n = 0..3)
+__device__ __forceinline__ void cp_async_wait(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    }
 }
 
 // one stage of rows [r0, r0 + rows) x K columns [kb, kb + 64) of a K-contiguous operand into the
@@ -101,13 +113,13 @@ __global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(TcArgs a) {
     using namespace kl::tc;
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NT = a.NT;
+    const int NT = a.NT, S = a.stages, lag = a.stages - 1;
     const int stage_bytes = kTcAStage + NT * kTcK * 2;
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + kTcStages * stage_bytes;     // full[S], empty[S], done
-    const uint32_t bar_full = bar0, bar_empty = bar0 + 8 * kTcStages, bar_done = bar0 + 16 * kTcStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kTcStages * stage_bytes + 16 * kTcStages + 8);
-    int* s_fail = reinterpret_cast<int*>(smem + kTcStages * stage_bytes + 16 * kTcStages + 16);
+    const uint32_t bar0 = sbase + S * stage_bytes;              // full[4], empty[4], done
+    const uint32_t bar_full = bar0, bar_empty = bar0 + 8 * kTcMaxStages, bar_done = bar0 + 16 * kTcMaxStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + S * stage_bytes + 16 * kTcMaxStages + 8);
+    int* s_fail = reinterpret_cast<int*>(smem + S * stage_bytes + 16 * kTcMaxStages + 16);
 
     const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * NT, z = blockIdx.z;
     const int k0 = z * a.kchunk;
@@ -115,7 +127,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(TcArgs a) {
     const int nk = (k1 - k0 + kTcK - 1) / kTcK;
 
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(bar_full + 8 * s, 128);
             mbar_init(bar_empty + 8 * s, 1);
         }
@@ -134,9 +146,9 @@ __global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(TcArgs a) {
         bool ok = true;
         int arrived = 0;
         for (int i = 0; i < nk; ++i) {
-            const int st = i % kTcStages;
-            if (i >= kTcStages) {
-                ok = __all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * st, uint32_t(((i / kTcStages) - 1) & 1)));
+            const int st = i % S;
+            if (i >= S) {
+                ok = __all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * st, uint32_t(((i / S) - 1) & 1)));
                 if (!ok) break;
             }
             const int kb = k0 + i * kTcK;
@@ -144,18 +156,18 @@ __global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(TcArgs a) {
             stage_rows(sa, a.A, a.lda, m0, kTcM, a.M, kb, k1, tid);
             stage_rows(sa + kTcAStage, a.B, a.ldb, n0, NT, a.N, kb, k1, tid);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
-            if (i >= kTcLag) {
-                asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcLag) : "memory");
+            if (i >= lag) {
+                cp_async_wait(lag);
                 fence_proxy_async();
-                mbar_arrive(bar_full + 8 * ((i - kTcLag) % kTcStages));
-                arrived = i - kTcLag + 1;
+                mbar_arrive(bar_full + 8 * ((i - lag) % S));
+                arrived = i - lag + 1;
             }
         }
         // every copy of this thread has landed before the CTA can leave
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         fence_proxy_async();
         if (ok) {
-            for (int j = arrived; j < nk; ++j) mbar_arrive(bar_full + 8 * (j % kTcStages));
+            for (int j = arrived; j < nk; ++j) mbar_arrive(bar_full + 8 * (j % S));
             ok = __all_sync(0xffffffffu, mbar_wait(bar_done, 0));
         }
         if (ok) {
@@ -195,8 +207,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(TcArgs a) {
         const uint32_t idesc = idesc_bf16(kTcM, NT);
         bool ok = true;
         for (int i = 0; i < nk; ++i) {
-            const int st = i % kTcStages;
-            ok = mbar_wait(bar_full + 8 * st, uint32_t((i / kTcStages) & 1));
+            const int st = i % S;
+            ok = mbar_wait(bar_full + 8 * st, uint32_t((i / S) & 1));
             if (!ok) break;
             fence_after_sync();
             const uint32_t sa = sbase + st * stage_bytes, sb = sa + kTcAStage;
@@ -259,7 +271,15 @@ kl_status tc_gemm(int M, int N, int K, const bf16* A, int64_t lda, const bf16* B
     a.ldo = ldo;
     a.status = status;
     const int splits = (K + kchunk - 1) / kchunk;
-    const size_t smem = size_t(kTcStages) * (kTcAStage + size_t(a.NT) * kTcK * 2) + 256;
+    // short contractions (<= 4 K blocks per CTA) are latency-bound: two stages and more CTAs per
+    // SM; long ones get four stages.  Shared memory is padded so that the resident CTAs never ask
+    // for more than the 512 tensor-memory columns of an SM.
+    const int nk = kchunk / kTcK;
+    a.stages = nk > 4 ? kTcMaxStages : std::min(nk, 2);
+    size_t smem = size_t(a.stages) * (kTcAStage + size_t(a.NT) * kTcK * 2) + 256;
+    const size_t occ_tmem = size_t(512 / a.tmem_cols);
+    const size_t min_smem = (kSmemPerSm + occ_tmem) / (occ_tmem + 1) - 1024 + 16;
+    if (smem < min_smem) smem = min_smem;
     dim3 grid((M + kTcM - 1) / kTcM, (N + a.NT - 1) / a.NT, splits);
     tc_gemm_kernel<<<grid, kTcThreads, smem, s>>>(a);
     KL_CUDA(cudaGetLastError());
@@ -396,46 +416,80 @@ __global__ void column_sums(const float* __restrict__ dz, int M, int N, float* _
 // ---------------------------------------------------------------------------------------
 // projector loss
 // ---------------------------------------------------------------------------------------
-// per sample s and row chunk c: partial Y^T Y, V^T Y, V^T V over rows [c*ch, c*ch + ch), with
-// Y[i][a] = out[s][a*n + i], V[i][a] = tgt[s][a*n + i]; gp[((s*nch + c)*3 + w)*k*k + a*k + b]
-__global__ void loss_gram_partial(const float* __restrict__ out, const float* __restrict__ tgt, int n, int k, int ch,
-                                  float* __restrict__ gp) {
-    extern __shared__ float sh[];          // Y chunk then V chunk, k rows of ch + 1
-    const int s = blockIdx.y, c = blockIdx.x, nch = gridDim.x;
-    const int i0 = c * ch, ld = ch + 1;
-    float* Ys = sh;
-    float* Vs = sh + k * ld;
+// Gram matrix of X = [Y V] (the k predicted and the k target vectors of one sample, n rows):
+// C = X^T X (2k x 2k, rows padded to R with zeros), of which Y^T Y, V^T Y and V^T V are used.
+// CTA (c, s) accumulates row chunks c, c + gridDim.x, ... of sample s: each chunk of ch rows is
+// staged in shared memory (X^T rows of ch + 4 floats) and every thread keeps an (R/16) x (R/16)
+// tile C[tr + 16 i][tc + 16 j] in registers, reading four rows at a time as float4.
+// Partial sums to gp[(s * gridDim.x + c) * R * R].
+template <int R>
+__global__ void __launch_bounds__(256) loss_gram_partial(const float* __restrict__ out, const float* __restrict__ tgt,
+                                                         int n, int k, int ch, float* __restrict__ gp) {
+    constexpr int T = R / 16;
+    extern __shared__ __align__(16) float xs[];          // R rows of ld floats
+    const int s = blockIdx.y, ld = ch + 4;
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
     const float* Y = out + size_t(s) * k * n;
     const float* V = tgt + size_t(s) * k * n;
-    for (int e = threadIdx.x; e < k * ch; e += blockDim.x) {
-        const int a = e / ch, ii = e - a * ch;
-        const int i = i0 + ii;
-        Ys[a * ld + ii] = i < n ? Y[size_t(a) * n + i] : 0.f;
-        Vs[a * ld + ii] = i < n ? V[size_t(a) * n + i] : 0.f;
+    float acc[T][T];
+#pragma unroll
+    for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j) acc[i][j] = 0.f;
+    const int nch = (n + ch - 1) / ch;
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int i0 = c * ch;
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * ch; e += blockDim.x) {
+            const int a = e / ch, ii = e - a * ch;
+            const int i = i0 + ii;
+            float v = 0.f;
+            if (i < n) {
+                if (a < k)
+                    v = Y[size_t(a) * n + i];
+                else if (a < 2 * k)
+                    v = V[size_t(a - k) * n + i];
+            }
+            xs[a * ld + ii] = v;
+        }
+        __syncthreads();
+        for (int ii = 0; ii < ch; ii += 4) {
+            float4 ra[T], rb[T];
+#pragma unroll
+            for (int i = 0; i < T; ++i) ra[i] = *reinterpret_cast<const float4*>(xs + (tr + 16 * i) * ld + ii);
+#pragma unroll
+            for (int j = 0; j < T; ++j) rb[j] = *reinterpret_cast<const float4*>(xs + (tc + 16 * j) * ld + ii);
+#pragma unroll
+            for (int i = 0; i < T; ++i)
+#pragma unroll
+                for (int j = 0; j < T; ++j) {
+                    acc[i][j] = fmaf(ra[i].x, rb[j].x, acc[i][j]);
+                    acc[i][j] = fmaf(ra[i].y, rb[j].y, acc[i][j]);
+                    acc[i][j] = fmaf(ra[i].z, rb[j].z, acc[i][j]);
+                    acc[i][j] = fmaf(ra[i].w, rb[j].w, acc[i][j]);
+                }
+        }
     }
-    __syncthreads();
-    const int kk = k * k;
-    for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
-        const int w = e / kk, ab = e - w * kk, a = ab / k, b = ab - a * k;
-        const float* X1 = (w == 0 ? Ys : Vs) + a * ld;
-        const float* X2 = (w == 2 ? Vs : Ys) + b * ld;
-        float acc = 0.f;
-        for (int ii = 0; ii < ch; ++ii) acc = fmaf(X1[ii], X2[ii], acc);
-        gp[(size_t(s) * nch + c) * 3 * kk + e] = acc;
-    }
+    float* g = gp + (size_t(s) * gridDim.x + blockIdx.x) * R * R;
+#pragma unroll
+    for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j) g[(tr + 16 * i) * R + tc + 16 * j] = acc[i][j];
 }
 
-// per sample (one CTA of 256 threads): chunks summed in order; gram[s] = (Y^T Y, V^T Y);
+// per sample (one CTA of 256 threads): partial Grams summed in order; gram[s] = (Y^T Y, V^T Y);
 // loss[s] = (||Y^T Y||^2 - 2 ||V^T Y||^2 + ||V^T V||^2) / k (fixed-order tree)
-__global__ void loss_gram_reduce(const float* __restrict__ gp, int nch, int k, float* __restrict__ gram,
+__global__ void loss_gram_reduce(const float* __restrict__ gp, int parts, int R, int k, float* __restrict__ gram,
                                  float* __restrict__ loss) {
     __shared__ float red[256];
     const int s = blockIdx.x, kk = k * k;
     float l = 0.f;
     for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+        const int w = e / kk, ab = e - w * kk, a = ab / k, b = ab - a * k;
+        // w = 0: Y^T Y = C[a][b]; w = 1: V^T Y = C[k + a][b]; w = 2: V^T V = C[k + a][k + b]
+        const int row = (w == 0 ? a : k + a), col = (w == 2 ? k + b : b);
         float acc = 0.f;
-        for (int c = 0; c < nch; ++c) acc += gp[(size_t(s) * nch + c) * 3 * kk + e];
-        const int w = e / kk;
+        for (int c = 0; c < parts; ++c) acc += gp[(size_t(s) * parts + c) * R * R + row * R + col];
         if (w < 2) gram[size_t(s) * 2 * kk + e] = acc;
         l += (w == 1 ? -2.f : 1.f) * acc * acc;
     }
@@ -449,38 +503,50 @@ __global__ void loss_gram_reduce(const float* __restrict__ gp, int nch, int k, f
 }
 
 // dY[s][b*n + i] = scale * (4 sum_a Y[i][a] YtY[a][b] - 4 sum_a V[i][a] VtY[a][b]);
-// thread = row i, block.y = 8 samples
+// thread = row i, block.y = sample; the two k x k matrices of the sample in shared memory
+// (rows of KMAX floats, read as broadcast float4)
 template <int KMAX>
-__global__ void loss_grad(const float* __restrict__ out, const float* __restrict__ tgt, const float* __restrict__ gram,
-                          int n, int k, int samples, float scale, float* __restrict__ dy, bf16* __restrict__ dyb) {
+__global__ void __launch_bounds__(256) loss_grad(const float* __restrict__ out, const float* __restrict__ tgt,
+                                                 const float* __restrict__ gram, int n, int k, float scale,
+                                                 float* __restrict__ dy, bf16* __restrict__ dyb) {
+    __shared__ __align__(16) float g1[KMAX * KMAX], g2[KMAX * KMAX];
+    const int s = blockIdx.y, kk = k * k;
+    const float* YtY = gram + size_t(s) * 2 * kk;
+    for (int e = threadIdx.x; e < KMAX * KMAX; e += blockDim.x) {
+        const int a = e / KMAX, b = e - a * KMAX;
+        const bool v = a < k && b < k;
+        g1[e] = v ? YtY[a * k + b] : 0.f;
+        g2[e] = v ? -YtY[kk + a * k + b] : 0.f;
+    }
+    __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int kk = k * k;
-    const int s1 = min(samples, int(blockIdx.y) * 8 + 8);
-    for (int s = blockIdx.y * 8; s < s1; ++s) {
-        const float* Y = out + size_t(s) * k * n + i;
-        const float* V = tgt + size_t(s) * k * n + i;
-        const float* YtY = gram + size_t(s) * 2 * kk;
-        const float* VtY = YtY + kk;
-        float acc[KMAX];
+    const float* Y = out + size_t(s) * k * n + i;
+    const float* V = tgt + size_t(s) * k * n + i;
+    float acc[KMAX];
 #pragma unroll
-        for (int b = 0; b < KMAX; ++b) acc[b] = 0.f;
-        for (int a = 0; a < k; ++a) {
-            const float ya = Y[size_t(a) * n], va = V[size_t(a) * n];
+    for (int b = 0; b < KMAX; ++b) acc[b] = 0.f;
+    for (int a = 0; a < k; ++a) {
+        const float ya = Y[size_t(a) * n], va = V[size_t(a) * n];
 #pragma unroll
-            for (int b = 0; b < KMAX; ++b)
-                if (b < k) acc[b] = fmaf(ya, YtY[a * k + b], fmaf(-va, VtY[a * k + b], acc[b]));
+        for (int b = 0; b < KMAX; b += 4) {
+            const float4 p = *reinterpret_cast<const float4*>(g1 + a * KMAX + b);
+            const float4 q = *reinterpret_cast<const float4*>(g2 + a * KMAX + b);
+            acc[b] = fmaf(ya, p.x, fmaf(va, q.x, acc[b]));
+            acc[b + 1] = fmaf(ya, p.y, fmaf(va, q.y, acc[b + 1]));
+            acc[b + 2] = fmaf(ya, p.z, fmaf(va, q.z, acc[b + 2]));
+            acc[b + 3] = fmaf(ya, p.w, fmaf(va, q.w, acc[b + 3]));
         }
-        float* d = dy + size_t(s) * k * n + i;
-        bf16* db = dyb + size_t(s) * k * n + i;
-#pragma unroll
-        for (int b = 0; b < KMAX; ++b)
-            if (b < k) {
-                const float g = 4.f * scale * acc[b];
-                d[size_t(b) * n] = g;
-                db[size_t(b) * n] = __float2bfloat16_rn(g);
-            }
     }
+    float* d = dy + size_t(s) * k * n + i;
+    bf16* db = dyb + size_t(s) * k * n + i;
+#pragma unroll
+    for (int b = 0; b < KMAX; ++b)
+        if (b < k) {
+            const float g = 4.f * scale * acc[b];
+            d[size_t(b) * n] = g;
+            db[size_t(b) * n] = __float2bfloat16_rn(g);
+        }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -648,26 +714,34 @@ kl_status backward_impl(kl_mlp m, const float* tgt, int batch, int k, int n, flo
     bf16* ht = static_cast<bf16*>(m->ht.ptr);
     const int ldb = int(round_up(size_t(batch), 8));
 
-    // Gram matrices in row chunks (shared memory: 2 k (ch + 1) floats <= 48 KB), reduced in order
-    int ch = int((48 * 1024 / (8 * size_t(k))) - 1);
-    ch = std::max(32, std::min(256, ch / 32 * 32));
-    const int nch = (n + ch - 1) / ch;
-    KL_TRY(grow(m->gpart, size_t(batch) * nch * 3 * k * k * sizeof(float), s));
+    // Gram matrices of [Y V] in row chunks (shared memory: R rows of ch + 4 floats), at most 8
+    // chunk groups per sample, reduced in order
+    const int R = (2 * k <= 32) ? 32 : (2 * k <= 64 ? 64 : 128);
+    const int ch = (R == 128) ? 88 : 160;
+    const int parts = std::min(8, (n + ch - 1) / ch);
+    KL_TRY(grow(m->gpart, size_t(batch) * parts * R * R * sizeof(float), s));
     KL_TRY(grow(m->gram, size_t(batch) * 2 * k * k * sizeof(float), s));
     float* gp = static_cast<float*>(m->gpart.ptr);
     float* gram = static_cast<float*>(m->gram.ptr);
-    loss_gram_partial<<<dim3(nch, batch), 256, size_t(2) * k * (ch + 1) * sizeof(float), s>>>(out, tgt, n, k, ch, gp);
+    const size_t gsm = size_t(R) * (ch + 4) * sizeof(float);
+    const dim3 gg(parts, batch);
+    if (R == 32)
+        loss_gram_partial<32><<<gg, 256, gsm, s>>>(out, tgt, n, k, ch, gp);
+    else if (R == 64)
+        loss_gram_partial<64><<<gg, 256, gsm, s>>>(out, tgt, n, k, ch, gp);
+    else
+        loss_gram_partial<128><<<gg, 256, gsm, s>>>(out, tgt, n, k, ch, gp);
     KL_CUDA(cudaGetLastError());
-    loss_gram_reduce<<<batch, 256, 0, s>>>(gp, nch, k, gram, loss_dev);
+    loss_gram_reduce<<<batch, 256, 0, s>>>(gp, parts, R, k, gram, loss_dev);
     KL_CUDA(cudaGetLastError());
-    const dim3 lg((n + 127) / 128, (batch + 7) / 8);
+    const dim3 lg((n + 255) / 256, batch);
     const float scale = 1.f / float(k * batch);
     if (k <= 16)
-        loss_grad<16><<<lg, 128, 0, s>>>(out, tgt, gram, n, k, batch, scale, dzf, dzb);
+        loss_grad<16><<<lg, 256, 0, s>>>(out, tgt, gram, n, k, scale, dzf, dzb);
     else if (k <= 32)
-        loss_grad<32><<<lg, 128, 0, s>>>(out, tgt, gram, n, k, batch, scale, dzf, dzb);
+        loss_grad<32><<<lg, 256, 0, s>>>(out, tgt, gram, n, k, scale, dzf, dzb);
     else
-        loss_grad<64><<<lg, 128, 0, s>>>(out, tgt, gram, n, k, batch, scale, dzf, dzb);
+        loss_grad<64><<<lg, 256, 0, s>>>(out, tgt, gram, n, k, scale, dzf, dzb);
     KL_CUDA(cudaGetLastError());
     count_launches(3);
 

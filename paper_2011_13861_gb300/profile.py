@@ -4,6 +4,11 @@
 
 Builds the handle, runs stages 1-4 once to obtain u, then calls kl_covmv `reps` times on the
 current stream and prints the CUDA-event time per call.
+
+  python -m paper_2011_13861_gb300.profile --mlp-train --batch 64 --reps 3
+
+times training steps of the warm-start network (4 inputs, 4 x 256 tanh, 32 x 6,859 outputs) on
+seeded synthetic inputs and targets: one warm-up epoch, then `reps` epochs of 256 samples.
 """
 import argparse
 import json
@@ -12,6 +17,23 @@ import torch
 
 import paper_2011_13861_gb300 as kl
 from paper_2011_13861_gb300 import inputs
+
+
+def mlp_train(a):
+    k, n, S = 32, 6859, 256
+    net = kl.MLP(4, 256, 4, k * n, seed=1)
+    x = torch.from_numpy(inputs.random_block(S, 4, seed=2).astype("float32")).cuda()
+    t = torch.from_numpy(inputs.random_block(S, k * n, seed=3).astype("float32")).cuda()
+    net.train(x, t, k, n, 1, a.batch, 1e-4, 0)
+    out = []
+    for r in range(a.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.train(x, t, k, n, 1, a.batch, 1e-4, r + 1)
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1) / (S // a.batch))
+    print(json.dumps({"mlp_train": {"batch": a.batch, "params": net.nparam, "ms_per_step": out}}))
 
 
 def main():
@@ -28,9 +50,13 @@ def main():
     ap.add_argument("--polish-block", type=int, default=0)
     ap.add_argument("--polish-ncv", type=int, default=0)
     ap.add_argument("--low", default="fp32", choices=["fp32", "tc32"])
+    ap.add_argument("--mlp-train", action="store_true", help="time training steps of the warm-start network")
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--accurate", default="df64", choices=["fp64", "df64", "tc64"],
                     help="accurate-phase arithmetic of --solve plain_df / mixed")
     a = ap.parse_args()
+    if a.mlp_train:
+        return mlp_train(a)
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     if a.solve:

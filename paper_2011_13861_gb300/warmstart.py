@@ -53,22 +53,32 @@ class WarmStart:
         self.history = []
 
     # ---- training data ------------------------------------------------------------------
-    def targets(self, params, tol=1e-6, block=16, precision=B.KL_P_TC64, maxiter=200):
-        """Solve every coarse problem for its k leading eigenvectors.  Returns (X, T, stats):
-        X (S, 4) and T (S, k n) float32 CUDA tensors (vector j of sample s at T[s, j n:(j+1) n])."""
+    def targets(self, params, tol=1e-6, block=16, precision=B.KL_P_DF64, maxiter=200, batch=64):
+        """Solve every coarse problem for its k leading eigenvectors, `batch` problems at a time
+        through kl_eigs_batched (one shared stage-5 launch per step; batch=1 solves them one by
+        one with kl_eigs).  Returns (X, T, stats): X (S, 4) and T (S, k n) float32 CUDA tensors
+        (vector j of sample s at T[s, j n:(j+1) n], scaled by sqrt(n))."""
         import torch
         X = torch.tensor([features(q) for q in params], dtype=torch.float32, device="cuda")
         T = torch.empty((len(params), self.k * self.n), dtype=torch.float32, device="cuda")
         applies, unconv = 0, 0
         t0 = time.perf_counter()
-        for s, prm in enumerate(params):
-            pr = problem(prm, self.p, self.ne_c)
-            _, vecs, info = pr.eigs(self.k, tol=tol, method=1, block=block, precision=precision, maxiter=maxiter,
-                                    raise_on_nonconv=False, verify=True)
-            T[s] = (vecs * self.scale).to(torch.float32).reshape(-1)
-            applies += info["applies"]
-            unconv += int(info["converged"] < self.k)
-            pr.close()
+        for c0 in range(0, len(params), max(1, batch)):
+            chunk = params[c0:c0 + max(1, batch)]
+            probs = [problem(q, self.p, self.ne_c) for q in chunk]
+            if len(probs) > 1:
+                _, vecs, infos, _, _ = B.eigs_batched(probs, self.k, tol=tol, method=1, block=block,
+                                                      precision=precision, maxiter=maxiter)
+            else:
+                _, v, info = probs[0].eigs(self.k, tol=tol, method=1, block=block, precision=precision,
+                                           maxiter=maxiter, raise_on_nonconv=False)
+                vecs, infos = [v], [info]
+            for j, (v, info) in enumerate(zip(vecs, infos)):
+                T[c0 + j] = (v * self.scale).to(torch.float32).reshape(-1)
+                applies += info["applies"]
+                unconv += int(info["converged"] < self.k)
+            for pr in probs:
+                pr.close()
         torch.cuda.synchronize()
         return X, T, {"solves": len(params), "seconds": time.perf_counter() - t0, "applies": applies,
                       "not_converged": unconv}
