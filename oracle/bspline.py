@@ -7,7 +7,11 @@ eq. univariate_mass_matrix2 (mixed mass matrix M_k).
 
 Knot vectors are open and uniform: degree p, ne elements on [0, 1], end knots
 of multiplicity p+1, interior knots simple, so the spline space is C^{p-1} and
-has n = ne + p functions (reading stated in the design doc).
+has n = ne + p functions.  Multipatch domains (Sec. 3.6) add patch interfaces:
+interior breakpoints where the trial space is only C^0 (knot multiplicity p) and
+the interpolation space is C^{-1} (multiplicity p+1).  A C^{-1} space has two
+Greville abscissae at such a knot; the basis is evaluated there from the side of
+the function whose support ends or starts at the knot (left / right limit).
 """
 import math
 
@@ -23,6 +27,20 @@ def open_uniform_knots(p, ne):
     return np.array([0.0] * (p + 1) + interior + [1.0] * (p + 1))
 
 
+def knots_with_interfaces(p, ne, interfaces=(), mult=None):
+    """Open uniform knot vector with each interface value (an interior breakpoint i/ne of the
+    uniform mesh) repeated to multiplicity `mult` (p: C^0 there; p + 1: C^{-1})."""
+    t = list(open_uniform_knots(p, ne))
+    for x in interfaces:
+        i = int(round(float(x) * ne))
+        if not (0 < i < ne) or abs(float(x) * ne - i) > 1e-12:
+            raise ValueError("an interface must be an interior breakpoint of the uniform mesh")
+        xv = i / ne
+        have = sum(1 for y in t if y == xv)
+        t += [xv] * (int(mult) - have)
+    return np.array(sorted(t))
+
+
 def dimension(t, p):
     """Number of B-splines of degree p on knot vector t."""
     return len(t) - p - 1
@@ -36,25 +54,31 @@ def greville(t, p):
     return np.array([sum(t[i + 1:i + p + 1]) / p for i in range(n)])
 
 
-def basis_matrix(t, p, x):
+def basis_matrix(t, p, x, side=None):
     """Values of all n B-splines of degree p at the points x: B[a, i] = B_{i,p}(x_a).
 
     Cox-de Boor recursion written out over degrees.  The degree-0 functions are
     indicator functions of [t_i, t_{i+1}); at the right end of the domain the
     last non-empty interval is taken closed so that the basis is a partition of
-    unity on the whole closed interval.
+    unity on the whole closed interval.  Points with side[a] < 0 take the left
+    limit instead: the indicators of (t_i, t_{i+1}] (and the first interval closed).
     """
     t = np.asarray(t, dtype=np.float64)
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    left = np.zeros(len(x), dtype=bool) if side is None else (np.asarray(side) < 0)
     m = len(t) - 1  # number of knot spans (some empty)
     last = max(i for i in range(m) if t[i] < t[i + 1])
+    first = min(i for i in range(m) if t[i] < t[i + 1])
     B = np.zeros((len(x), m))
     for i in range(m):
         if t[i] < t[i + 1]:
             inside = (t[i] <= x) & (x < t[i + 1])
             if i == last:
                 inside |= (x == t[i + 1])
-            B[:, i] = inside.astype(np.float64)
+            inside_l = (t[i] < x) & (x <= t[i + 1])
+            if i == first:
+                inside_l |= (x == t[i])
+            B[:, i] = np.where(left, inside_l, inside).astype(np.float64)
     for q in range(1, p + 1):
         Bn = np.zeros((len(x), m - q))
         for i in range(m - q):
@@ -109,8 +133,18 @@ def gramian(t, p):
     return mass_matrix(t, p, t, p, q=p + 1)
 
 
-def collocation_matrix(t, p, x=None):
-    """Collocation matrix B~[i, j] = B~_j(x_i) at the Greville abscissae (Sec. 4.2 eq. interpolation_matrix)."""
+def greville_sides(t, p):
+    """-1 for a Greville abscissa that sits on an interior knot where its own function's support
+    ends (evaluate from the left there), 0 otherwise (the default right-limit evaluation)."""
+    x = greville(t, p)
+    n = dimension(t, p)
+    return np.array([-1 if (t[i + p + 1] == x[i] and t[0] < x[i] < t[-1]) else 0 for i in range(n)])
+
+
+def collocation_matrix(t, p, x=None, side=None):
+    """Collocation matrix B~[i, j] = B~_j(x_i) at the Greville abscissae (Sec. 4.2 eq. interpolation_matrix),
+    one-sided at the knots of a C^{-1} space."""
     if x is None:
         x = greville(t, p)
-    return basis_matrix(t, p, x)
+        side = greville_sides(t, p)
+    return basis_matrix(t, p, x, side)

@@ -21,21 +21,28 @@ from .kernels import kernel_matrix
 
 
 class Direction:
-    """Univariate data of one parametric direction k (trial space p, ne; interpolation space pt, net)."""
+    """Univariate data of one parametric direction k (trial space p, ne; interpolation space pt, net).
 
-    def __init__(self, p, ne, pt=None, net=None):
+    `interfaces`: patch interfaces of a multipatch domain (Sec. 3.6) in this direction, interior
+    breakpoints of both uniform meshes; the trial space is C^0 there and the interpolation space
+    C^{-1} (Sec. 6.2, Example 1-1), whose two Greville abscissae at the knot are evaluated from
+    the left and from the right."""
+
+    def __init__(self, p, ne, pt=None, net=None, interfaces=()):
         self.p, self.ne = int(p), int(ne)
         self.pt = int(pt if pt else p)
         self.net = int(net if net else ne)
-        self.t = bspline.open_uniform_knots(self.p, self.ne)
-        self.tt = bspline.open_uniform_knots(self.pt, self.net)
+        self.interfaces = tuple(interfaces)
+        self.t = bspline.knots_with_interfaces(self.p, self.ne, self.interfaces, self.p)
+        self.tt = bspline.knots_with_interfaces(self.pt, self.net, self.interfaces, self.pt + 1)
         self.n = bspline.dimension(self.t, self.p)
         self.nt = bspline.dimension(self.tt, self.pt)
         self.xi = bspline.greville(self.tt, self.pt)              # Greville abscissae of B~
+        self.side = bspline.greville_sides(self.tt, self.pt)      # -1: left limit at a C^{-1} knot
         self.Z = bspline.gramian(self.t, self.p)                   # eq. univariate_mass_matrix
         self.L = np.linalg.cholesky(self.Z)                        # eq. cholesky (lower)
         self.M = bspline.mass_matrix(self.tt, self.pt, self.t, self.p)   # eq. univariate_mass_matrix2
-        self.Bt = bspline.collocation_matrix(self.tt, self.pt, self.xi)  # eq. interpolation_matrix
+        self.Bt = bspline.collocation_matrix(self.tt, self.pt)     # eq. interpolation_matrix
         self.Bt_lu = sla.lu_factor(self.Bt)
 
 
@@ -46,10 +53,10 @@ class BoxMap:
         self.lo = np.asarray(lo, dtype=np.float64)
         self.hi = np.asarray(hi, dtype=np.float64)
 
-    def __call__(self, xh):
+    def __call__(self, xh, sides=None):
         return self.lo + (self.hi - self.lo) * xh
 
-    def detDF(self, xh):
+    def detDF(self, xh, sides=None):
         return np.full(xh.shape[0], np.prod(self.hi - self.lo))
 
 
@@ -57,14 +64,15 @@ class Problem:
     """One discretised KL problem: directions, geometry map and covariance kernel."""
 
     def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None,
-                 lo=None, hi=None, geom=None):
+                 lo=None, hi=None, geom=None, interfaces=None):
         def per_dir(v):
             return list(v) if np.ndim(v) else [v] * dim
         p, ne = per_dir(p), per_dir(ne)
         pt = per_dir(pt) if pt is not None else [None] * dim
         net = per_dir(net) if net is not None else [None] * dim
+        itf = list(interfaces) if interfaces is not None else [()] * dim
         self.dim = dim
-        self.dirs = [Direction(p[k], ne[k], pt[k], net[k]) for k in range(dim)]
+        self.dirs = [Direction(p[k], ne[k], pt[k], net[k], itf[k]) for k in range(dim)]
         # geometry map F: the affine box map by default, or any object with F(xh) and detDF(xh)
         # (e.g. a NURBS map, oracle.nurbs.NURBSMap)
         self.geom = geom if geom is not None else BoxMap(lo if lo is not None else [0.0] * dim,
@@ -74,17 +82,23 @@ class Problem:
         self.Nt = int(np.prod([d.nt for d in self.dirs]))
 
     # -- Greville grid -----------------------------------------------------------------
-    def parametric_points(self):
-        """Tensor Greville grid in vec order (k_1 fastest): array Nt x d."""
+    def parametric_points(self, sides=False):
+        """Tensor Greville grid in vec order (k_1 fastest): array Nt x d (and, with sides=True,
+        the per-direction evaluation sides of every point)."""
         grids = np.meshgrid(*[d.xi for d in reversed(self.dirs)], indexing="ij")
         # grids[j] varies along axis j of the C-order array [nt_d, ..., nt_1]
         cols = [grids[self.dim - 1 - k].ravel() for k in range(self.dim)]
-        return np.stack(cols, axis=1)
+        xh = np.stack(cols, axis=1)
+        if not sides:
+            return xh
+        sg = np.meshgrid(*[d.side for d in reversed(self.dirs)], indexing="ij")
+        return xh, np.stack([sg[self.dim - 1 - k].ravel() for k in range(self.dim)], axis=1)
 
     def points_and_J(self):
-        """Mapped Greville points X = F(xh) and J = sqrt(det DF(xh)) (Sec. 4.4.1)."""
-        xh = self.parametric_points()
-        return self.geom(xh), np.sqrt(self.geom.detDF(xh))
+        """Mapped Greville points X = F(xh) and J = sqrt(det DF(xh)) (Sec. 4.4.1); at a patch
+        interface det DF is taken from the side the point's interpolation function lives on."""
+        xh, sd = self.parametric_points(sides=True)
+        return self.geom(xh, sd), np.sqrt(self.geom.detDF(xh, sd))
 
     # -- Kronecker factors expanded (Sec. 2.2 eq. kron_*) -------------------------------
     def kron(self, attr):

@@ -18,12 +18,13 @@ import numpy as np
 from . import bspline
 
 
-def basis_derivative_matrix(t, p, x):
-    """dB[a, i] = d/dx B_{i,p}(x_a) on knot vector t (p >= 1)."""
+def basis_derivative_matrix(t, p, x, side=None):
+    """dB[a, i] = d/dx B_{i,p}(x_a) on knot vector t (p >= 1); one-sided (left limit) where
+    side[a] < 0."""
     t = np.asarray(t, dtype=np.float64)
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     n = bspline.dimension(t, p)
-    Bm = bspline.basis_matrix(t, p - 1, x)          # n + 1 functions of degree p - 1
+    Bm = bspline.basis_matrix(t, p - 1, x, side)    # n + 1 functions of degree p - 1
     dB = np.zeros((len(x), n))
     for i in range(n):
         left = t[i + p] - t[i]
@@ -53,11 +54,12 @@ class NURBSMap:
         assert self.ctrl.shape == tuple(reversed(self.n)) + (self.d,)
         assert self.w.shape == tuple(reversed(self.n))
 
-    def _eval(self, xh):
+    def _eval(self, xh, sides=None):
         xh = np.atleast_2d(np.asarray(xh, dtype=np.float64))
         m = xh.shape[0]
-        B = [bspline.basis_matrix(self.knots[k], self.deg[k], xh[:, k]) for k in range(self.d)]
-        dB = [basis_derivative_matrix(self.knots[k], self.deg[k], xh[:, k]) for k in range(self.d)]
+        sd = [None] * self.d if sides is None else [np.asarray(sides)[:, k] for k in range(self.d)]
+        B = [bspline.basis_matrix(self.knots[k], self.deg[k], xh[:, k], sd[k]) for k in range(self.d)]
+        dB = [basis_derivative_matrix(self.knots[k], self.deg[k], xh[:, k], sd[k]) for k in range(self.d)]
         # flatten the control net in vec order (direction 1 fastest)
         Pw = (self.ctrl * self.w[..., None]).reshape(-1, self.d)     # w_I P_I
         w = self.w.reshape(-1)
@@ -80,14 +82,15 @@ class NURBSMap:
             DF[:, :, j] = (dP * W[:, None] - P * dW[:, None]) / (W * W)[:, None]
         return F, DF
 
-    def __call__(self, xh):
-        return self._eval(xh)[0]
+    def __call__(self, xh, sides=None):
+        return self._eval(xh, sides)[0]
 
-    def jacobian(self, xh):
-        return self._eval(xh)[1]
+    def jacobian(self, xh, sides=None):
+        return self._eval(xh, sides)[1]
 
-    def detDF(self, xh):
-        return np.linalg.det(self.jacobian(xh))
+    def detDF(self, xh, sides=None):
+        """det DF; at a C^0 knot of the map, sides[a, k] < 0 takes the derivative from the left."""
+        return np.linalg.det(self.jacobian(xh, sides))
 
 
 def quarter_annulus(r_in=1.0, r_out=2.0, height=1.0, dim=3):
@@ -116,3 +119,57 @@ def quarter_annulus(r_in=1.0, r_out=2.0, height=1.0, dim=3):
                 ctrl[kz, j, i] = [radii[i] * dirs[j][0], radii[i] * dirs[j][1], zs[kz]]
                 wts[kz, j, i] = wang[j]
     return NURBSMap([2, 2, 2], knots, ctrl, wts)
+
+
+def two_patch_annulus(r_in=1.0, r_out=2.0, height=1.0, dim=3, split=1.0 / 3.0):
+    """Half annulus r in [r_in, r_out], angle in [0, pi], made of two quarter-annulus patches
+    joined with C^0 continuity at the angular parameter `split` (knot of multiplicity 2 in the
+    degree-2 angular direction).  Each patch is the exact rational quadratic quarter circle; the
+    patches have parametric lengths split and 1 - split, so det DF jumps at the interface unless
+    split = 1/2."""
+    ka = np.array([0.0, 0.0, 0.0, split, split, 1.0, 1.0, 1.0])
+    kl = np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    radii = [r_in, 0.5 * (r_in + r_out), r_out]
+    dirs = [(1.0, 0.0), (1.0, 1.0), (0.0, 1.0), (-1.0, 1.0), (-1.0, 0.0)]
+    wang = [1.0, np.sqrt(0.5), 1.0, np.sqrt(0.5), 1.0]
+    if dim == 2:
+        ctrl = np.zeros((5, 3, 2))
+        wts = np.zeros((5, 3))
+        for j in range(5):
+            for i in range(3):
+                ctrl[j, i] = [radii[i] * dirs[j][0], radii[i] * dirs[j][1]]
+                wts[j, i] = wang[j]
+        return NURBSMap([2, 2], [kl, ka], ctrl, wts)
+    zs = [0.0, 0.5 * height, height]
+    ctrl = np.zeros((3, 5, 3, 3))
+    wts = np.zeros((3, 5, 3))
+    for kz in range(3):
+        for j in range(5):
+            for i in range(3):
+                ctrl[kz, j, i] = [radii[i] * dirs[j][0], radii[i] * dirs[j][1], zs[kz]]
+                wts[kz, j, i] = wang[j]
+    return NURBSMap([2, 2, 2], [kl, ka, kl], ctrl, wts)
+
+
+def two_patch_bar(a=0.25, split=0.5, dim=2):
+    """Piecewise affine map of [0,1]^dim: direction 1 is degree 1 with a C^0 knot at `split`
+    (x_1 = a xi / split on the first patch, a + (1 - a)(xi - split)/(1 - split) on the second),
+    the other directions are the identity.  det DF is piecewise constant and jumps at the
+    interface unless a = split."""
+    k1 = np.array([0.0, 0.0, split, 1.0, 1.0])
+    kid = np.array([0.0, 0.0, 1.0, 1.0])
+    xs = [0.0, a, 1.0]
+    if dim == 1:
+        return NURBSMap([1], [k1], np.array(xs)[:, None], np.ones(3))
+    if dim == 2:
+        ctrl = np.zeros((2, 3, 2))
+        for j in range(2):
+            for i in range(3):
+                ctrl[j, i] = [xs[i], float(j)]
+        return NURBSMap([1, 1], [k1, kid], ctrl, np.ones((2, 3)))
+    ctrl = np.zeros((2, 2, 3, 3))
+    for kz in range(2):
+        for j in range(2):
+            for i in range(3):
+                ctrl[kz, j, i] = [xs[i], float(j), float(kz)]
+    return NURBSMap([1, 1, 1], [k1, kid, kid], ctrl, np.ones((2, 2, 3)))

@@ -13,7 +13,7 @@ import pytest
 import scipy.linalg as sla
 from scipy.special import comb
 
-from oracle import bspline, closed_form, galerkin, ibq
+from oracle import bspline, closed_form, galerkin, ibq, nurbs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -474,3 +474,101 @@ def test_prolongation_is_exact_and_norm_preserving():
         assert np.abs(bspline.basis_matrix(tc, p, x) @ c - bspline.basis_matrix(tf, p, x) @ (P @ c)).max() < 1e-13
         Q = prolong.standard_form_map_1d(p, nc, nf)
         assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------------------
+# Multipatch domains (Sec. 3.6): C^0 trial spaces and C^{-1} interpolation spaces at patch
+# interfaces (Sec. 6.2, Example 1-1; Sec. 6.3)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("pt", [1, 2, 3])
+def test_c_minus1_interpolation_reproduces_a_jump(pt):
+    """Interpolation at the one-sided Greville abscissae of a C^{-1} space reproduces every
+    piecewise polynomial of degree <= pt with a jump at the interface; the C^{pt-1} space of the
+    same mesh cannot."""
+    rng = np.random.default_rng(pt)
+    s = 1.0 / 3.0
+    cl, cr = rng.standard_normal(pt + 1), rng.standard_normal(pt + 1)
+
+    def g(x, side=None):
+        left = (x < s) if side is None else ((x < s) | ((x == s) & (np.asarray(side) < 0)))
+        return np.where(left, np.polyval(cl, x), np.polyval(cr, x))
+
+    xe = rng.uniform(0, 1, 200)
+    xe = xe[np.abs(xe - s) > 1e-9]
+    t = bspline.knots_with_interfaces(pt, 6, [s], pt + 1)
+    xi, sd = bspline.greville(t, pt), bspline.greville_sides(t, pt)
+    assert np.sum(xi == s) == 2 and list(sd[xi == s]) == [-1, 0]
+    c = np.linalg.solve(bspline.collocation_matrix(t, pt), g(xi, sd))
+    assert np.abs(bspline.basis_matrix(t, pt, xe) @ c - g(xe)).max() < 1e-12
+    t0 = bspline.open_uniform_knots(pt, 6)
+    c0 = np.linalg.solve(bspline.collocation_matrix(t0, pt), g(bspline.greville(t0, pt)))
+    assert np.abs(bspline.basis_matrix(t0, pt, xe) @ c0 - g(xe)).max() > 1e-3
+
+
+def test_left_limit_evaluation():
+    """Left limits at a C^{-1} knot are the values of the left piece; partition of unity holds
+    on both sides."""
+    t = bspline.knots_with_interfaces(2, 4, [0.5], 3)
+    B_r = bspline.basis_matrix(t, 2, [0.5])
+    B_l = bspline.basis_matrix(t, 2, [0.5], [-1])
+    assert abs(B_r.sum() - 1) < 1e-15 and abs(B_l.sum() - 1) < 1e-15
+    n = bspline.dimension(t, 2)
+    left_funcs = [i for i in range(n) if t[i + 3] <= 0.5]
+    assert B_l[0, left_funcs].sum() == 1.0 and B_r[0, left_funcs].sum() == 0.0
+    # the left limit equals the limit of values just left of the knot
+    B_near = bspline.basis_matrix(t, 2, [0.5 - 1e-12])
+    assert np.abs(B_near - B_l).max() < 1e-10
+
+
+@pytest.mark.parametrize("dim,p,ne,m", [(1, 2, [6], 2), (2, [2, 2], [6, 2], 2), (2, [3, 1], [3, 2], 1)])
+def test_ibq_exact_on_two_patch_affine_domain(dim, p, ne, m):
+    """Two affine patches joined with C^0 continuity: the pull-back of the polynomial kernel is
+    piecewise polynomial and J = sqrt(det DF) is piecewise constant, jumping at the interface.
+    With the C^{-1} interpolation space the IBQ matrix equals the brute-force Galerkin matrix;
+    with the C^{pt-1} space of the same mesh it does not."""
+    s = 1.0 / 3.0
+    F = nurbs.two_patch_bar(a=0.6, split=s, dim=dim)
+    itf = [[s]] + [[]] * (dim - 1)
+    P = ibq.Problem(dim, p, ne, kernel="poly", L=m, geom=F, interfaces=itf)
+    pmax = max(d.p for d in P.dirs)
+    A, _ = galerkin.galerkin_matrices(P, q=pmax + m + 2)
+    assert np.abs(P.dense()["At"] - A).max() / np.abs(A).max() < 1e-12
+    P0 = ibq.Problem(dim, p, ne, kernel="poly", L=m, geom=F)
+    A0, _ = galerkin.galerkin_matrices(P0, q=pmax + m + 2)
+    assert np.abs(P0.dense()["At"] - A0).max() / np.abs(A0).max() > 1e-4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_two_patch_annulus_interface_and_area(dim):
+    """The half annulus of two quarter-circle patches of parametric lengths s and 1 - s: F is
+    continuous across the interface, det DF has the one-sided closed forms
+    (r_out - r_in) sqrt(2) r / s (left) and (r_out - r_in) sqrt(2) r / (1 - s) (right), and the
+    volume is pi (r_out^2 - r_in^2) / 2 (times the height)."""
+    s, r_in, r_out, h = 1.0 / 3.0, 1.0, 2.0, 1.5
+    F = nurbs.two_patch_annulus(r_in, r_out, h, dim, split=s)
+    x1 = np.array([0.0, 0.3, 1.0])
+    xh = np.zeros((3, dim))
+    xh[:, 0] = x1
+    xh[:, 1] = s
+    if dim == 3:
+        xh[:, 2] = 0.4
+    left = np.zeros((3, dim), dtype=int)
+    left[:, 1] = -1
+    assert np.abs(F(xh, left) - F(xh)).max() < 1e-14
+    r = r_in + x1 * (r_out - r_in)
+    fac = (r_out - r_in) * np.sqrt(2.0) * r * (h if dim == 3 else 1.0)
+    assert np.abs(F.detDF(xh, left) - fac / s).max() < 1e-12 * fac.max() / s
+    assert np.abs(F.detDF(xh) - fac / (1 - s)).max() < 1e-12 * fac.max() / s
+    # volume by Gauss quadrature on each patch (det DF is rational in the angle: 24 points)
+    g1, w1 = bspline.gauss_legendre(6, 0.0, 1.0)
+    ga, wa = np.concatenate([bspline.gauss_legendre(24, 0.0, s)[0], bspline.gauss_legendre(24, s, 1.0)[0]]), \
+        np.concatenate([bspline.gauss_legendre(24, 0.0, s)[1], bspline.gauss_legendre(24, s, 1.0)[1]])
+    grids = [g1, ga] + ([g1] if dim == 3 else [])
+    wts = [w1, wa] + ([w1] if dim == 3 else [])
+    mesh = np.meshgrid(*grids, indexing="ij")
+    pts = np.stack([m_.ravel() for m_ in mesh], axis=1)
+    ww = np.ones(len(pts))
+    for k in range(dim):
+        ww = ww * np.meshgrid(*wts, indexing="ij")[k].ravel()
+    vol = 0.5 * np.pi * (r_out ** 2 - r_in ** 2) * (h if dim == 3 else 1.0)
+    assert abs((F.detDF(pts) * ww).sum() - vol) < 1e-12 * vol
