@@ -75,12 +75,23 @@ typedef struct {
 
 /* Trial space B_h (degree deg[k], elems[k] uniform elements, C^{deg-1}, Sec. 2.3)
  * and interpolation space B~_h (interp_deg / interp_elems; 0 = same as trial;
- * Sec. 4.2).  Open uniform knot vectors on [0,1]: n_k = elems[k] + deg[k]. */
+ * Sec. 4.2).  Open uniform knot vectors on [0,1]: n_k = elems[k] + deg[k].
+ *
+ * Multipatch domains (Sec. 3.6): interfaces[k] lists n_interfaces[k] patch-interface
+ * parameters in direction k (host array, read during kl_create; NULL / 0 = none).  Each must
+ * be an interior breakpoint j/elems[k] of the trial mesh and of the interpolation mesh.  The
+ * trial space is C^0 there (knot multiplicity deg[k]: n_k grows by deg[k] - 1 per interface)
+ * and the interpolation space C^{-1} (multiplicity interp_deg[k] + 1: n~_k grows by
+ * interp_deg[k]), as in the examples of Sec. 6.2 and 6.3; its two Greville abscissae at an
+ * interface are evaluated from the left and from the right, and so is det DF of a NURBS map
+ * with a C^0 knot there.  KL_ERR_INVALID_ARG for a value that is not such a breakpoint. */
 typedef struct {
     int deg[3];
     int elems[3];
     int interp_deg[3];
     int interp_elems[3];
+    int n_interfaces[3];
+    const double* interfaces[3];
 } kl_space;
 
 /* Covariance kernels (Sec. 3.1 names the exponential and Gaussian kernels with
@@ -301,7 +312,8 @@ void kl_mlp_destroy(kl_mlp m);
  * count that is a multiple of the coarse one (nested uniform knots), so each coarse spline is a
  * fine spline (knot insertion); per direction Q_k = L_f^T P_k L_c^{-T} with P_k from collocation
  * at the fine Greville points, applied as one contraction per direction.  v_dev: N_c x nvec,
- * y_dev: N_f x nvec, leading dimensions N_c and N_f.  Synchronous on `stream` (the factors
+ * y_dev: N_f x nvec, leading dimensions N_c and N_f; spaces with patch interfaces are rejected
+ * (KL_ERR_INVALID_ARG).  Synchronous on `stream` (the factors
  * are uploaded per call and released once the contractions have run). */
 kl_status kl_prolong(kl_handle coarse, kl_handle fine, const double* v_dev, double* y_dev, int nvec, void* stream);
 

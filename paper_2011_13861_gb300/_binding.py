@@ -24,7 +24,8 @@ class KLGeometry(ctypes.Structure):
 
 class KLSpace(ctypes.Structure):
     _fields_ = [("deg", ctypes.c_int * 3), ("elems", ctypes.c_int * 3), ("interp_deg", ctypes.c_int * 3),
-                ("interp_elems", ctypes.c_int * 3)]
+                ("interp_elems", ctypes.c_int * 3), ("n_interfaces", ctypes.c_int * 3),
+                ("interfaces", ctypes.c_void_p * 3)]
 
 
 class KLKernel(ctypes.Structure):
@@ -178,12 +179,13 @@ class KLProblem:
 
     dim, p, ne: spatial dimension, trial degree and element count per direction;
     kernel: 'exp' | 'gauss' | 'exp_sep' | 'poly';  pt, net: interpolation space (default = trial);
-    lo, hi: box map.  All vectors are float64 CUDA tensors of shape (N,) or (N, nvec)
+    lo, hi: box map; nurbs: NURBS map; interfaces: per direction, patch-interface parameters of a
+    multipatch domain (C^0 trial and C^{-1} interpolation space there).  All vectors are float64 CUDA tensors of shape (N,) or (N, nvec)
     (column-major blocks are handled by passing the transposed storage, see _block).
     """
 
     def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None, lo=None, hi=None,
-                 nurbs=None):
+                 nurbs=None, interfaces=None):
         lib = load()
         g = KLGeometry(dim, KL_GEOM_BOX, (ctypes.c_double * 3)(*_per_dir(lo, dim, 0.0)),
                        (ctypes.c_double * 3)(*_per_dir(hi, dim, 1.0)))
@@ -208,6 +210,15 @@ class KLProblem:
             g.ctrl = rec.ctypes.data
         sp = KLSpace((ctypes.c_int * 3)(*_per_dir(p, dim)), (ctypes.c_int * 3)(*_per_dir(ne, dim)),
                      (ctypes.c_int * 3)(*_per_dir(pt, dim)), (ctypes.c_int * 3)(*_per_dir(net, dim)))
+        if interfaces is not None:
+            # interfaces: per direction a sequence of patch-interface parameters (Sec. 3.6)
+            for k in range(dim):
+                vals = [float(x) for x in interfaces[k]] if k < len(interfaces) else []
+                if vals:
+                    arr = (ctypes.c_double * len(vals))(*vals)
+                    keep.append(arr)
+                    sp.n_interfaces[k] = len(vals)
+                    sp.interfaces[k] = ctypes.cast(arr, ctypes.c_void_p).value
         kk = KLKernel(KERNEL_KINDS[kernel] if isinstance(kernel, str) else int(kernel), float(sigma), float(L))
         h = ctypes.c_void_p()
         _check(lib.kl_create(ctypes.byref(g), ctypes.byref(sp), ctypes.byref(kk), ctypes.byref(h)))

@@ -453,7 +453,13 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         const int p = space->deg[k], ne = space->elems[k];
         const int pt = space->interp_deg[k] > 0 ? space->interp_deg[k] : p;
         const int net = space->interp_elems[k] > 0 ? space->interp_elems[k] : ne;
-        kl_status st = build_direction(p, ne, pt, net, &h->dir[k]);
+        std::vector<double> itf;
+        if (space->n_interfaces[k] < 0 || (space->n_interfaces[k] > 0 && !space->interfaces[k])) {
+            delete h;
+            return fail(KL_ERR_INVALID_ARG, "patch interfaces: negative count or null array");
+        }
+        if (space->n_interfaces[k] > 0) itf.assign(space->interfaces[k], space->interfaces[k] + space->n_interfaces[k]);
+        kl_status st = build_direction(p, ne, pt, net, itf, &h->dir[k]);
         if (st != KL_OK) {
             delete h;
             return st;
@@ -491,16 +497,18 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     for (int64_t idx = 0; idx < Nt; ++idx) {
         int64_t r = idx;
         double xh[3] = {0.0, 0.0, 0.0};
+        int side[3] = {0, 0, 0};
         for (int k = 0; k < d; ++k) {
             const int64_t ik = r % h->nt[k];
             r /= h->nt[k];
             xh[k] = h->dir[k].xi[size_t(ik)];
+            side[k] = h->dir[k].side[size_t(ik)];
         }
         if (geom->kind == KL_GEOM_BOX) {
             for (int k = 0; k < d; ++k) h->X_host[size_t(idx) * 3 + k] = h->lo[k] + (h->hi[k] - h->lo[k]) * xh[k];
         } else {
             double X[3], detDF;
-            nurbs_map_point(nm, xh, X, &detDF);
+            nurbs_map_point(nm, xh, side, X, &detDF);
             if (!(detDF > 0.0) || !isfinite(detDF)) {
                 delete h;
                 return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");

@@ -39,13 +39,15 @@ void count_launches(int n);   // kernel-launch accounting (kl_kernel_launches)
 struct Direction {
     int p = 0, ne = 0, pt = 0, net = 0;
     int n = 0, nt = 0;
+    std::vector<double> itf;  // patch interfaces (C^0 trial, C^{-1} interpolation space)
     std::vector<double> xi;   // Greville abscissae of the interpolation space (nt)
+    std::vector<int> side;    // -1: xi[i] is evaluated from the left (a C^{-1} knot), else 0
     std::vector<double> C;    // C_k = B~_k^{-T} M_k L_k^{-T}, nt x n row-major
     std::vector<double> Linv; // L_k^{-1}, n x n row-major (lower triangular)
     std::vector<double> L;    // L_k, Z_k = L_k L_k^T, n x n row-major (lower triangular)
 };
 
-kl_status build_direction(int p, int ne, int pt, int net, Direction* out);
+kl_status build_direction(int p, int ne, int pt, int net, const std::vector<double>& interfaces, Direction* out);
 kl_status build_prolongation(const Direction& c, const Direction& f, std::vector<double>* Q);
 
 // tensor-product NURBS geometry map: knots per direction, control records (x, y, z, w),
@@ -57,7 +59,8 @@ struct NurbsMap {
     std::vector<double> knots[3];
     std::vector<double> ctrl;
 };
-void nurbs_map_point(const NurbsMap& m, const double* xh, double* X, double* detDF);
+// F(xh) and det DF(xh); side[k] < 0 takes the left limit in direction k (at a C^0 knot of the map)
+void nurbs_map_point(const NurbsMap& m, const double* xh, const int* side, double* X, double* detDF);
 
 // ----------------------------------------------------------------------------------------
 // device kernels (launchers)

@@ -40,6 +40,13 @@ int find_span(const std::vector<double>& t, int p, double x) {
     return lo;
 }
 
+// Span s with t[s] < x <= t[s+1] (the left limit at a knot x), clamped to the first non-empty span.
+int find_span_left(const std::vector<double>& t, int p, double x) {
+    int s = find_span(t, p, x);
+    while (s > p && t[size_t(s)] >= x) --s;
+    return s;
+}
+
 // The p+1 non-zero B-splines N_{s-p..s}(x) on span s, by the triangular scheme of
 // "left"/"right" knot distances (de Boor's recurrence written per span).
 void nonzero_basis(const std::vector<double>& t, int p, int s, double x, double* N) {
@@ -134,6 +141,24 @@ Space make_space(int p, int ne) {
     return s;
 }
 
+// open uniform knots with every interface (an interior breakpoint j / ne) raised to multiplicity
+// `mult`; false if a value is not such a breakpoint
+bool make_space_itf(int p, int ne, const std::vector<double>& itf, int mult, Space* out) {
+    Space s = make_space(p, ne);
+    for (double x : itf) {
+        const double j = std::round(x * ne);
+        if (!(j > 0.0 && j < double(ne)) || std::fabs(x * ne - j) > 1e-12) return false;
+        const double xv = j / double(ne);
+        int have = 0;
+        for (double y : s.t) have += (y == xv);
+        for (int r = have; r < mult; ++r) s.t.push_back(xv);
+    }
+    std::sort(s.t.begin(), s.t.end());
+    s.n = int(s.t.size()) - p - 1;
+    *out = s;
+    return true;
+}
+
 // int_0^1 Ba_i Bb_j over the union of the breakpoints of both spaces, q Gauss points each.
 std::vector<double> cross_mass(const Space& a, const Space& b, int q) {
     std::vector<double> br(a.t);
@@ -195,22 +220,31 @@ bool invert(std::vector<double>& A, int n) {
 
 }  // namespace
 
-kl_status build_direction(int p, int ne, int pt, int net, Direction* out) {
+kl_status build_direction(int p, int ne, int pt, int net, const std::vector<double>& interfaces, Direction* out) {
     if (p < 1 || ne < 1 || pt < 1 || net < 1) return fail(KL_ERR_INVALID_ARG, "degrees and element counts must be >= 1");
     if (ne + p > 4096 || net + pt > 4096) return fail(KL_ERR_INVALID_ARG, "more than 4096 functions in one direction");
+    if (interfaces.size() > 64) return fail(KL_ERR_INVALID_ARG, "more than 64 patch interfaces in one direction");
     Direction& d = *out;
     d.p = p; d.ne = ne; d.pt = pt; d.net = net;
-    Space trial = make_space(p, ne), interp = make_space(pt, net);
+    d.itf = interfaces;
+    // patch interfaces (Sec. 3.6): the trial space is C^0 there, the interpolation space C^{-1}
+    Space trial, interp;
+    if (!make_space_itf(p, ne, interfaces, p, &trial) || !make_space_itf(pt, net, interfaces, pt + 1, &interp))
+        return fail(KL_ERR_INVALID_ARG, "a patch interface must be an interior breakpoint of both meshes");
+    if (trial.n > 4096 || interp.n > 4096) return fail(KL_ERR_INVALID_ARG, "more than 4096 functions in one direction");
     d.n = trial.n;
     d.nt = interp.n;
     const int n = d.n, nt = d.nt;
 
-    // Greville abscissae of the interpolation space
+    // Greville abscissae of the interpolation space; at a C^{-1} knot the function whose support
+    // ends there is collocated from the left
     d.xi.assign(nt, 0.0);
+    d.side.assign(nt, 0);
     for (int i = 0; i < nt; ++i) {
         double s = 0.0;
         for (int r = 1; r <= pt; ++r) s += interp.t[i + r];
         d.xi[i] = s / pt;
+        if (interp.t[size_t(i + pt + 1)] == d.xi[i] && d.xi[i] > 0.0 && d.xi[i] < 1.0) d.side[i] = -1;
     }
     // Z_k (p+1 Gauss points per element) and its Cholesky factor
     std::vector<double> Z = cross_mass(trial, trial, p + 1);
@@ -242,7 +276,7 @@ kl_status build_direction(int p, int ne, int pt, int net, Direction* out) {
     // B~_k collocation (nt x nt) and its inverse
     std::vector<double> Bt(size_t(nt) * nt, 0.0), Nv(pt + 1);
     for (int i = 0; i < nt; ++i) {
-        int s = find_span(interp.t, pt, d.xi[i]);
+        int s = d.side[i] < 0 ? find_span_left(interp.t, pt, d.xi[i]) : find_span(interp.t, pt, d.xi[i]);
         nonzero_basis(interp.t, pt, s, d.xi[i], Nv.data());
         for (int r = 0; r <= pt; ++r) Bt[size_t(i) * nt + (s - pt + r)] = Nv[r];
     }
@@ -270,12 +304,13 @@ kl_status build_direction(int p, int ne, int pt, int net, Direction* out) {
 // F(xh) and det DF(xh) of a tensor-product NURBS map (Sec. 2.4): F = P / W with
 // P = sum_I N_I(xh) w_I P_I and W = sum_I N_I(xh) w_I; column j of DF is
 // (dP/dxh_j W - P dW/dxh_j) / W^2.  Directions beyond dim have one control point.
-void nurbs_map_point(const NurbsMap& m, const double* xh, double* X, double* detDF) {
+void nurbs_map_point(const NurbsMap& m, const double* xh, const int* side, double* X, double* detDF) {
     int span[3] = {0, 0, 0};
     double N[3][16], dN[3][16];
     for (int k = 0; k < 3; ++k) {
         if (k < m.dim) {
-            span[k] = find_span(m.knots[k], m.deg[k], xh[k]);
+            span[k] = (side && side[k] < 0) ? find_span_left(m.knots[k], m.deg[k], xh[k])
+                                            : find_span(m.knots[k], m.deg[k], xh[k]);
             nonzero_basis(m.knots[k], m.deg[k], span[k], xh[k], N[k]);
             nonzero_basis_derivative(m.knots[k], m.deg[k], span[k], xh[k], dN[k]);
         } else {
@@ -325,6 +360,8 @@ void nurbs_map_point(const NurbsMap& m, const double* xh, double* X, double* det
 // fine coefficients exactly (interpolation at the fine Greville points, Sec. 4.2).
 kl_status build_prolongation(const Direction& c, const Direction& f, std::vector<double>* Q) {
     if (c.p != f.p) return fail(KL_ERR_INVALID_ARG, "prolongation: the spaces must have the same degree");
+    if (!c.itf.empty() || !f.itf.empty())
+        return fail(KL_ERR_INVALID_ARG, "prolongation: spaces with patch interfaces are not supported");
     if (f.ne % c.ne != 0) return fail(KL_ERR_INVALID_ARG, "prolongation: the fine mesh must refine the coarse one");
     const int p = c.p;
     const Space tc = make_space(p, c.ne), tf = make_space(p, f.ne);

@@ -76,3 +76,45 @@ def warmstart_params(count, seed, L_range=(0.1, 2.0), r_in_range=(0.8, 1.2), r_o
         r_out = float(rng.uniform(*r_out_range))
         out.append({"kernel": kern, "L": L, "r_in": r_in, "r_out": r_out})
     return out
+
+
+def two_patch_annulus_net(r_in=1.0, r_out=2.0, height=1.0, dim=3, split=1.0 / 3.0):
+    """Control net of a half annulus (radius r_in..r_out, angle 0..pi, extruded to height for
+    dim = 3) made of two quarter-annulus patches joined with C^0 continuity at the angular
+    parameter `split`: degree 2 per direction, angular knots (0,0,0,split,split,1,1,1), the
+    angular control directions (1,0), (1,1), (0,1), (-1,1), (-1,0) with weights 1, sqrt(1/2), 1,
+    sqrt(1/2), 1.  Geometry data only: dict(deg, knots, ctrl, weights), direction 1 (radius)
+    fastest."""
+    kl = np.array([0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    ka = np.array([0.0, 0.0, 0.0, split, split, 1.0, 1.0, 1.0])
+    knots = [kl, ka] + ([kl] if dim == 3 else [])
+    radii = [r_in, 0.5 * (r_in + r_out), r_out]
+    dirs = [(1.0, 0.0), (1.0, 1.0), (0.0, 1.0), (-1.0, 1.0), (-1.0, 0.0)]
+    wang = [1.0, float(np.sqrt(0.5)), 1.0, float(np.sqrt(0.5)), 1.0]
+    zs = [0.0, 0.5 * height, height]
+    shape = ((3,) if dim == 3 else ()) + (5, 3)
+    ctrl = np.zeros(shape + (dim,))
+    wts = np.zeros(shape)
+    for idx in np.ndindex(*shape):
+        i, j = idx[-1], idx[-2]
+        pt = [radii[i] * dirs[j][0], radii[i] * dirs[j][1]]
+        if dim == 3:
+            pt.append(zs[idx[0]])
+        ctrl[idx] = pt
+        wts[idx] = wang[j]
+    return {"deg": [2] * dim, "knots": knots, "ctrl": ctrl, "weights": wts}
+
+
+def two_patch_bar_net(a=0.6, split=1.0 / 3.0, dim=2):
+    """Control net of a piecewise affine map of [0,1]^dim: direction 1 degree 1 with knots
+    (0,0,split,1,1) and control abscissae 0, a, 1 (two affine patches joined with C^0 continuity),
+    the other directions the identity (degree 1, one element).  Geometry data only."""
+    k1 = np.array([0.0, 0.0, split, 1.0, 1.0])
+    kid = np.array([0.0, 0.0, 1.0, 1.0])
+    xs = [0.0, a, 1.0]
+    shape = (2,) * (dim - 1) + (3,)
+    ctrl = np.zeros(shape + (dim,))
+    for idx in np.ndindex(*shape):
+        pt = [xs[idx[-1]]] + [float(idx[-2 - k]) for k in range(dim - 1)]
+        ctrl[idx] = pt
+    return {"deg": [1] * dim, "knots": [k1] + [kid] * (dim - 1), "ctrl": ctrl, "weights": np.ones(shape)}
