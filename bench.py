@@ -218,8 +218,9 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
     32 leading eigenvectors of `train_solves` coarse problems (p=3, 16^3 elements; kernel, L and
     radii drawn with seed 5), then used, prolonged exactly to 48^3 elements, as the start block
     of the mixed solver (20 eigenpairs, residual 1e-8) for unseen parameter sets (seed 6); against
-    the same solver from the random start (block 32 as the warm start, and block 16, its best
-    width) and, for the first parameter set, random-start float64 block Lanczos (block 4)."""
+    the same solver from the random start (block 16; and block 32) and, for the first parameter
+    set, random-start float64 block Lanczos (block 4).  The 32 predicted vectors are compressed by
+    Rayleigh-Ritz to 16 leading Ritz vectors that start the block-16 solver."""
     import numpy as np
     import torch
     from paper_2011_13861_gb300 import warmstart

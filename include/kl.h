@@ -222,6 +222,11 @@ typedef struct {
                              * for KL_P_TC64, whose launches cost the same up to 32 vectors) */
     int polish_ncv;         /* method 1: polish basis size (0 = 3 x polish_block, at most 160) */
     int low_precision;      /* method 1: first-phase arithmetic, KL_P_FP32 (0 = default) or KL_P_TC32 */
+    int nstart;             /* columns of start_dev (0 = block; block..64, at most the basis size).
+                             * With nstart > block the start columns are orthonormalised, the
+                             * first-phase operator is applied to them once, and the iteration
+                             * starts from their `block` leading Ritz vectors (Rayleigh-Ritz
+                             * compression of a wider warm-start subspace). */
 } kl_eig_opts;
 
 typedef struct {

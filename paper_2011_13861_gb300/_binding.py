@@ -36,7 +36,8 @@ class KLEigOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("block", ctypes.c_int), ("ncv", ctypes.c_int),
                 ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("start_dev", _vp),
                 ("tol_low", ctypes.c_double), ("verify", ctypes.c_int), ("precision", ctypes.c_int),
-                ("polish_block", ctypes.c_int), ("polish_ncv", ctypes.c_int), ("low_precision", ctypes.c_int)]
+                ("polish_block", ctypes.c_int), ("polish_ncv", ctypes.c_int), ("low_precision", ctypes.c_int),
+                ("nstart", ctypes.c_int)]
 
 
 class KLEigInfo(ctypes.Structure):
@@ -320,9 +321,18 @@ class KLProblem:
         """The k largest eigenpairs (descending).  Returns (evals numpy, evecs (k, N) tensor or None, info dict)."""
         import numpy as np
         import torch
+        # start: (nstart, N) float64 CUDA tensor; more rows than `block` are compressed by
+        # Rayleigh-Ritz to the block leading Ritz vectors (kl_eig_opts.nstart)
+        nstart = int(start.shape[0]) if (start is not None and start.dim() == 2) else 0
+        if start is not None and max(nstart, 1) < int(block):
+            raise ValueError("start must hold at least `block` vectors")
+        if start is not None and (not start.is_contiguous() or start.dtype != torch.float64 or
+                                  start.numel() != max(nstart, 1) * self.N):
+            raise ValueError("start must be a contiguous float64 (nstart, N) tensor")
         opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1),
                          _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0,
-                         int(precision), int(polish_block), int(polish_ncv), int(low_precision))
+                         int(precision), int(polish_block), int(polish_ncv), int(low_precision),
+                         nstart if nstart > int(block) else 0)
         ev = np.zeros(k)
         vecs = None
         dev = torch.device("cuda", torch.cuda.current_device())

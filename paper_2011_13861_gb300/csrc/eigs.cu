@@ -323,6 +323,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.polish_block = 0;
     o.polish_ncv = 0;
     o.low_precision = KL_P_FP32;
+    o.nstart = 0;
     if (opts_in) o = *opts_in;
     if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64 && o.precision != KL_P_TC64)
         return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64, KL_P_DF64 or KL_P_TC64");
@@ -364,13 +365,32 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     E.s = s;
     E.N = N;
     E.seed = o.seed;
-    const int cap_m = std::max(m, pol_m), cap_b = std::max(b, pol_b);
+    // a wider start subspace is compressed to its `b` leading Ritz vectors before the iteration
+    const int nst = (o.start_dev && o.nstart > b) ? o.nstart : b;
+    if (o.nstart < 0 || nst > 64 || nst > m)
+        return fail(KL_ERR_INVALID_ARG, "opts.nstart must lie in block..min(64, basis size)");
+    const int cap_m = std::max(m, pol_m), cap_b = std::max(std::max(b, pol_b), nst);
     KL_TRY(E.alloc(cap_m, cap_b));
     cudaError_t e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
 
     // ---- start block ----
-    if (o.start_dev) {
+    if (o.start_dev && nst > b) {
+        // Rayleigh-Ritz on span(start): orthonormal basis in V[:, 0:nst], its products in AV,
+        // T = V^T A V, then W = the b leading Ritz vectors
+        e = launch_copy_block(o.start_dev, N, E.W(), N, N, nst, s);
+        if (e != cudaSuccess) return cuda_fail(e, "start block");
+        bool sdef = false;
+        KL_TRY(E.cholqr(E.W(), nst, E.V(), &sdef));
+        if (sdef) return fail(KL_ERR_INVALID_ARG, "start columns are numerically rank deficient");
+        const int p1 = (o.method == 1) ? ((o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32) : o.precision;
+        KL_TRY(E.apply(p1, E.V(), E.AV(), nst));
+        e = launch_gram(E.V(), N, nst, E.AV(), N, nst, N, E.T(), E.mmax, E.Part(), E.maxparts, s);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        KL_TRY(E.sym_eig(nst));
+        e = launch_gemm_tall(1.0, E.V(), N, N, nst, E.S(), E.mmax, b, 0.0, E.W(), N, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
+    } else if (o.start_dev) {
         e = launch_copy_block(o.start_dev, N, E.W(), N, N, b, s);
     } else {
         e = launch_random_block(E.W(), N, N, b, o.seed, 0, s);

@@ -119,30 +119,28 @@ class WarmStart:
         finally:
             coarse.close()
 
-    def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, **eig_kw):
-        """The nev leading eigenpairs of `fine` from the warm start (block = k, basis 3 k unless
-        eig_kw['ncv'] says otherwise); when that solve
-        has not converged after `maxiter` restarts, the seeded random start with the same options
-        and block width eig_kw['block'] (default 16) (fallback=True).  Returns (evals, evecs, info) with info['path'] = 'warm' | 'fallback'
-        and info['warm'] = the warm attempt's info."""
+    def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, block=16, **eig_kw):
+        """The nev leading eigenpairs of `fine` from the warm start: the k predicted vectors are
+        compressed by Rayleigh-Ritz to the `block` (<= k) leading Ritz vectors, which start the
+        solver (kl_eig_opts.nstart).  When that solve has not converged after `maxiter`
+        restarts, the seeded random start with the same options takes over (fallback=True).
+        Returns (evals, evecs, info) with info['path'] = 'warm' | 'fallback' and info['warm'] =
+        the warm attempt's info."""
         import torch
         kw = dict(method=1, precision=B.KL_P_TC64)
         kw.update(eig_kw)
-        fb_block = kw.pop("block", 16)
-        warm_kw = dict(kw)
-        warm_kw.setdefault("ncv", max(3 * self.k, -(-(nev + 2 * self.k) // self.k) * self.k))
+        block = min(int(block), self.k)
         t0 = time.perf_counter()
         start = self.start_block(fine, prm).contiguous()
         torch.cuda.synchronize()
         t_start = time.perf_counter() - t0
-        ev, vecs, info = fine.eigs(nev, tol=tol, block=self.k, start=start, maxiter=maxiter, raise_on_nonconv=False,
-                                   **warm_kw)
+        ev, vecs, info = fine.eigs(nev, tol=tol, block=block, start=start, maxiter=maxiter, raise_on_nonconv=False,
+                                   **kw)
         info["ms_start_block"] = 1e3 * t_start
         if info["converged"] >= nev or not fallback:
             info["path"] = "warm"
             return ev, vecs, info
-        ev2, vecs2, info2 = fine.eigs(nev, tol=tol, block=fb_block, **kw)
+        ev2, vecs2, info2 = fine.eigs(nev, tol=tol, block=block, **kw)
         info2["path"] = "fallback"
         info2["warm"] = info
         return ev2, vecs2, info2
-

@@ -234,8 +234,27 @@ def test_fallback_when_the_warm_solve_stalls(kl):
     fine = warmstart.problem(prm, SMALL["p"], FINE_NE)
     ev, vec, info = ws.solve(fine, prm, NEV, tol=1e-10, maxiter=1, ncv=24, block=SMALL["k"], method=0,
                              precision=kl.KL_P_FP64)
+    assert info["warm"]["applies"] > 0
     assert info["path"] == "fallback"
     assert info["warm"]["converged"] < NEV
     assert info["converged"] >= NEV
     ev_r, _, _ = fine.eigs(NEV, tol=1e-10, method=1, block=SMALL["k"], precision=kl.KL_P_TC64)
     assert np.abs(ev - ev_r).max() <= 1e-8 * ev_r[0]
+
+
+def test_wide_start_is_compressed_by_rayleigh_ritz(kl):
+    """A start subspace wider than the block (kl_eig_opts.nstart): the exact leading eigenvectors
+    padded with random columns still start the solver at the answer, and the result equals the
+    random-start solve."""
+    import torch
+    from paper_2011_13861_gb300 import inputs as inp
+    G = kl.KLProblem(3, 2, 6, kernel="exp", L=0.7)
+    ev0, vec0, _ = G.eigs(6, tol=1e-10, method=0, block=4)
+    pad = torch.from_numpy(inp.random_block(G.N, 6, seed=4).T.copy()).cuda()
+    start = torch.cat([vec0, pad], dim=0).contiguous()            # 12 columns, block 4
+    ev1, _, info1 = G.eigs(6, tol=1e-10, method=0, block=4, start=start)
+    assert np.abs(ev1 - ev0).max() <= 1e-10 * ev0[0]
+    _, _, info_r = G.eigs(6, tol=1e-10, method=0, block=4)
+    assert info1["applies"] < info_r["applies"]
+    with pytest.raises(ValueError):
+        G.eigs(6, method=0, block=8, start=vec0[:4].contiguous())
