@@ -218,9 +218,9 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
     32 leading eigenvectors of `train_solves` coarse problems (p=3, 16^3 elements; kernel, L and
     radii drawn with seed 5), then used, prolonged exactly to 48^3 elements, as the start block
     of the mixed solver (20 eigenpairs, residual 1e-8) for unseen parameter sets (seed 6); against
-    the same solver from the random start (block 16; and block 32) and, for the first parameter
-    set, random-start float64 block Lanczos (block 4).  The 32 predicted vectors are compressed by
-    Rayleigh-Ritz to 16 leading Ritz vectors that start the block-16 solver."""
+    the same solver from the random start (block 32 as the warm start, and block 16, its best
+    width) and, for the first parameter set, random-start float64 block Lanczos (block 4).  Also
+    timed: the 32 predicted vectors compressed by Rayleigh-Ritz to a block-16 start."""
     import numpy as np
     import torch
     from paper_2011_13861_gb300 import warmstart
@@ -250,6 +250,7 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
         tw, (ev_w, vec_w, iw) = timed(lambda: ws.solve(fine, prm, k, tol=TOL))
         t32, (ev_r, _, i32) = timed(lambda: fine.eigs(k, TOL, block=32, want_vectors=False, **mixed))
         t16, (_, _, i16) = timed(lambda: fine.eigs(k, TOL, block=16, want_vectors=False, **mixed))
+        tc, (_, _, ic) = timed(lambda: ws.solve(fine, prm, k, tol=TOL, block=16))
         # subspace of the prediction against the converged eigenvectors (diagnostic)
         start = ws.start_block(fine, prm)
         Qs, _ = torch.linalg.qr(start.T)
@@ -259,6 +260,7 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
                "warm_start_block_ms": iw.get("ms_start_block", iw.get("warm", {}).get("ms_start_block")),
                "random32_s": t32, "random32_applies": i32["applies"], "random16_s": t16,
                "random16_applies": i16["applies"], "gain_vs_random32": t32 / tw, "gain_vs_random16": t16 / tw,
+               "warm_compressed16_s": tc, "warm_compressed16_applies": ic["applies"],
                "max_resid_warm": max(iw["resid"][:k]),
                "max_rel_eig_diff_warm_vs_random": float(np.max(np.abs(ev_w - ev_r) / np.abs(ev_r))),
                "prediction_max_sine_top20": float(np.sqrt(max(0.0, 1.0 - cosv.min() ** 2)))}

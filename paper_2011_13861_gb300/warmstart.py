@@ -119,17 +119,19 @@ class WarmStart:
         finally:
             coarse.close()
 
-    def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, block=16, **eig_kw):
-        """The nev leading eigenpairs of `fine` from the warm start: the k predicted vectors are
-        compressed by Rayleigh-Ritz to the `block` (<= k) leading Ritz vectors, which start the
-        solver (kl_eig_opts.nstart).  When that solve has not converged after `maxiter`
-        restarts, the seeded random start with the same options takes over (fallback=True).
-        Returns (evals, evecs, info) with info['path'] = 'warm' | 'fallback' and info['warm'] =
-        the warm attempt's info."""
+    def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, block=None, **eig_kw):
+        """The nev leading eigenpairs of `fine` from the warm start.  By default the k predicted
+        vectors form the start block (block = k, basis 3 k); with block < k they are compressed
+        by Rayleigh-Ritz to the `block` leading Ritz vectors (kl_eig_opts.nstart).  When the
+        warm solve has not converged after `maxiter` restarts, the seeded random start with the
+        same options takes over (fallback=True).  Returns (evals, evecs, info) with
+        info['path'] = 'warm' | 'fallback' and info['warm'] = the warm attempt's info."""
         import torch
         kw = dict(method=1, precision=B.KL_P_TC64)
         kw.update(eig_kw)
-        block = min(int(block), self.k)
+        block = self.k if block is None else min(int(block), self.k)
+        if block == self.k:
+            kw.setdefault("ncv", max(3 * block, -(-(nev + 2 * block) // block) * block))
         t0 = time.perf_counter()
         start = self.start_block(fine, prm).contiguous()
         torch.cuda.synchronize()
