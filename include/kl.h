@@ -300,7 +300,7 @@ kl_status kl_mlp_num_params(kl_mlp m, int64_t* n);
 kl_status kl_mlp_params(kl_mlp m, float* host, int direction);
 /* out_dev (batch x n_out) = network(x_dev (batch x n_in)).  Asynchronous on `stream`. */
 kl_status kl_mlp_forward(kl_mlp m, const float* x_dev, int batch, float* out_dev, void* stream);
-/* One forward and backward pass: per-sample losses to loss_dev (batch floats) and, when
+/* One forward and backward pass (batch <= 65535, k <= 64): per-sample losses to loss_dev (batch floats) and, when
  * grad_host is not NULL, the gradient of the batch-mean loss (same layout as the parameters;
  * synchronous then).  tgt_dev: batch x (k n), vector j of sample s at s*k*n + j*n; k n = n_out. */
 kl_status kl_mlp_loss_grad(kl_mlp m, const float* x_dev, const float* tgt_dev, int batch, int k, int n,
@@ -319,7 +319,8 @@ void kl_mlp_destroy(kl_mlp m);
  * at the fine Greville points, applied as one contraction per direction.  v_dev: N_c x nvec,
  * y_dev: N_f x nvec, leading dimensions N_c and N_f; spaces with patch interfaces are rejected
  * (KL_ERR_INVALID_ARG).  Synchronous on `stream` (the factors
- * are uploaded per call and released once the contractions have run). */
+ * are uploaded per call and released once the contractions have run); it uses the apply
+ * workspace of `fine`, so it must not overlap other calls on `fine`. */
 kl_status kl_prolong(kl_handle coarse, kl_handle fine, const double* v_dev, double* y_dev, int nvec, void* stream);
 
 /* The k (<= 64) largest eigenvalues of A~' (descending) to relative residual tol.

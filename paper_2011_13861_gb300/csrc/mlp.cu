@@ -705,6 +705,7 @@ kl_status forward_impl(kl_mlp m, const float* x, int batch, cudaStream_t s) {
 // loss of the current outputs against targets (float32, batch x k*n) and backward pass into m->G
 kl_status backward_impl(kl_mlp m, const float* tgt, int batch, int k, int n, float* loss_dev, cudaStream_t s) {
     if (k > 64) return fail(KL_ERR_INVALID_ARG, "warm-start loss: at most 64 vectors per sample");
+    if (batch > 65535) return fail(KL_ERR_INVALID_ARG, "warm-start loss: at most 65535 samples per batch");
     float* hf = static_cast<float*>(m->hf.ptr);
     bf16* hb = static_cast<bf16*>(m->hb.ptr);
     const float* out = hf + m->aoff[size_t(m->layers)];
