@@ -29,7 +29,7 @@ TOL = 1e-8
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 vector rate (nominal)
 # algorithmic float64 flops of one kernel evaluation (paper's convention: one flop per add,
 # subtract, multiply; FMA = 2): distance 3 sub + 3 mul + 2 add, pre-scaled coordinates carry 1/L
-# (the 9th flop of the survey's count is folded into set-up); sqrt by one Heron correction
+# (a 9th flop per evaluation, the scaling by 1/L, is folded into set-up); sqrt by one Heron correction
 # (mul, fma, mul, fma = 6); exp by Tang's method (fma, sub, fma, 4 fma + mul, fma = 16);
 # plus 2 flops per vector for the product.  The kernel is symmetric, so the method needs only half
 # of the evaluations (one per unordered pair): algorithmic flops per ordered pair = eval/2 + 2b.

@@ -18,7 +18,7 @@ ibq          the interpolation-based-quadrature discretisation written out
              densely (Sec. 4.1-4.4.1), the generalized eigenproblem, and the
              matrix-free application of Algorithm 1 step by step.
 kernels      the covariance kernels (Sec. 3.1; formulas fixed by the readings
-             listed in DESIGN.md).
+             stated there).
 galerkin     brute-force standard Galerkin with tensor Gauss quadrature on
              tiny meshes (Sec. 5.1) -- used to pin the IBQ exactness property.
 closed_form  closed-form eigenvalues of the 1D exponential kernel

@@ -2,7 +2,7 @@
 
 Sec. 3.1 names the exponential and the squared-exponential (Gaussian) kernel
 with variance sigma^2 and a correlation length, but prints no formula.  The
-readings used here (listed in the design doc):
+readings used here:
 
   exp       sigma^2 exp(-||x - x'||_2 / L)
   gauss     sigma^2 exp(-||x - x'||_2^2 / L^2)
