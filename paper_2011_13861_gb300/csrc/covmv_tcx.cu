@@ -1,0 +1,527 @@
+// Stage 5 of Algorithm 1 on the tensor cores (tcgen05, sm_103a) by exact fixed-point slicing,
+// for groups of up to 32 right-hand sides: z = Gamma u.  Two classes share one kernel:
+//   * float64 class (KL_P_TC64): kernel values in double-float (~48 bits), six 8-bit digits;
+//   * float32 class (KL_P_TC32): float32 kernel values (MUFU ex2/rsqrt), three 8-bit digits.
+//
+// Exact slicing.  Each kernel value g (scaled so |g| <= 1) is written as
+// g = sum_{s<S} a_s 2^(-8(s+1)) with integer digits (|a_0| <= 256, |a_s| <= 128 after, by
+// round-to-nearest digit extraction, every step exact), and each u value, after division by a
+// per-vector power of two sigma >= max|u|, as u/sigma = sum_{t<S} b_t 2^(-8(t+1)).  The digits
+// are stored as bfloat16 "slices" a_s 2^(-8s) and b_t 2^(-8t), which bfloat16 holds exactly.
+// The tensor core forms the slice products exactly and adds them in float32, one accumulator per
+// level d = s + t:
+//   float64 class: levels 0-3 (1, 2, 3, 4 products) are multiples of 2^-8d below 2^(24-8d)
+//     over 128 columns, hence exact in float32 whatever the tensor core's rounding; levels 4-5
+//     (11 products, relative size <= 2^-32) share a fifth accumulator whose rounding stays
+//     below ~2^-49 of the sum; products of levels >= 6 (relative size < 2^-48) are dropped;
+//   float32 class: levels 0-2 (1, 2, 3 products) are exact the same way; levels >= 3
+//     (relative size < 2^-24) are dropped.
+// Every 128 columns the accumulators are drained into double-float sums.  The result carries a
+// relative error of ~1e-14 (float64 class) or ~1e-7 (float32 class: the float32 kernel values
+// and the 24-bit fixed point), independent of the number of points, because no float32 sum
+// ever spans more than 128 columns.
+//
+// Pipeline and schedule (persistent tile ranges over (128-row block, 32-column chunk) tiles, one
+// CTA per SM, loader / producers / MMA issuer synchronised by mbarriers):
+//   * loader (one thread): bulk copy per 32-column chunk of a pre-staged image holding the
+//     column coordinates and the u slices (tcx_image_kernel);
+//   * producers (16 warps, four threads per row, 8 columns each): kernel values, S slices each,
+//     written K-major;
+//   * MMA issuer (one thread): one MMA per slice product and 16 columns into the level
+//     accumulators in tensor memory, double-buffered per 128-column drain block.
+// Every wait is bounded (~2 s), after which the CTA records KL_ERR_TIMEOUT, drains its own
+// asynchronous operations and returns.
+#include "df64.cuh"
+#include "kernel32.cuh"
+#include "tc_common.cuh"
+
+namespace kl {
+namespace {
+
+using namespace tc;
+using df::F2;
+
+constexpr int kRows = 128;                        // MMA M
+constexpr int kK = 16;                            // MMA K (16-bit inputs)
+constexpr int kChunk = 32;                        // columns per stage
+constexpr int kStages = 3;
+constexpr int kNB = 32;                           // MMA N: vectors per group
+constexpr int kDrainChunks = 4;                   // level accumulators drained every 128 columns
+constexpr int kProducers = 512;                   // warps 0-15
+constexpr int kThreads = kProducers + 64;         // + loader warp 16 + MMA warp 17
+constexpr int kLoaderWarp = kProducers / 32;
+constexpr int kMmaWarp = kLoaderWarp + 1;
+// tensor memory (512 columns): accumulator a of drain block parity dp at dp*256 + a*32
+constexpr int kTmemCols = 512;
+constexpr int kTmemBuf = 256;
+constexpr int kASub = kRows * kK * 2;             // 128 x 16 bf16: 4 KB
+constexpr int kASlice = kASub * (kChunk / kK);    // 8 KB
+constexpr int kBSub = kNB * kK * 2;               // 32 x 16 bf16: 1 KB
+constexpr int kBSlice = kBSub * (kChunk / kK);    // 2 KB
+constexpr uint32_t kIdesc = idesc_bf16(kRows, kNB);
+
+// per class: slices, products, accumulators, coordinate floats per column, shared-memory layout
+template <int CLS>
+struct Tx {
+    static constexpr int kSlices = CLS == 64 ? 6 : 3;
+    static constexpr int kProducts = CLS == 64 ? 21 : 6;
+    static constexpr int kAccs = CLS == 64 ? 5 : 3;
+    static constexpr int kCoords = CLS == 64 ? 6 : 3;         // double-float heads/tails, or float
+    static constexpr int kAStage = kASlice * kSlices;
+    static constexpr int kCoordBytes = kCoords * kChunk * 4;
+    static constexpr int kImg = kCoordBytes + kBSlice * kSlices;
+    static constexpr int kOffA = 0;
+    static constexpr int kOffImg = kOffA + kStages * kAStage;
+    static constexpr int kOffTab = kOffImg + kStages * kImg;  // 2^(-j/64) heads and tails
+    static constexpr int kOffBar = kOffTab + 128 * 4;
+    static constexpr int kBarLoaded = 0, kBarFull = kStages, kBarEmpty = 2 * kStages;
+    static constexpr int kBarBlkDone = 3 * kStages, kBarBlkFree = kBarBlkDone + 2;
+    static constexpr int kNumBars = kBarBlkFree + 2;
+    static constexpr int kOffTmem = kOffBar + 8 * kNumBars;
+    static constexpr int kSmemBytes = kOffTmem + 16;
+    static_assert(kImg % 16 == 0 && kOffImg % 16 == 0 && kOffBar % 8 == 0, "bulk-copy and mbarrier alignment");
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
+
+// the slice products (a_s, b_t) grouped by accumulator.  Float64 class: s + t <= 5, levels 0,
+// 1, 2, 3, then 4-5 together.  Float32 class: s + t <= 2, levels 0, 1, 2.
+template <int CLS>
+__device__ __forceinline__ void product(int q, int* s, int* t, int* acc, bool* first) {
+    constexpr int S[21] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+    constexpr int T[21] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+    *s = S[q];
+    *t = T[q];
+    *acc = q == 0 ? 0 : q < 3 ? 1 : q < 6 ? 2 : q < 10 ? 3 : 4;
+    *first = (q == 0 || q == 1 || q == 3 || q == 6 || q == 10);
+}
+
+// integer digit of x * scale by round-to-nearest (|x * scale| < 2^22), and the exact remainder
+__device__ __forceinline__ float digit(float& x, float scale) {
+    const float magic = 12582912.0f;   // 1.5 * 2^23
+    const float p = __fsub_rn(__fmaf_rn(x, scale, magic), magic);
+    x = __fmaf_rn(x, scale, -p);
+    return p;
+}
+
+// six slices a_s 2^(-8s) of a double-float g with |g| <= 1 (see the file comment); the tail
+// joins the remainder after the three head digits
+__device__ __forceinline__ void slices6(F2 g, float* out) {
+    float x = g.h;
+    out[0] = digit(x, 256.f);
+    out[1] = __fmul_rn(digit(x, 256.f), 0.00390625f);
+    out[2] = __fmul_rn(digit(x, 256.f), 1.52587890625e-05f);
+    x = __fmaf_rn(g.l, 16777216.f, x);   // remainder is in units of 2^-24
+    out[3] = __fmul_rn(digit(x, 256.f), 5.9604644775390625e-08f);
+    out[4] = __fmul_rn(digit(x, 256.f), 2.3283064365386963e-10f);
+    out[5] = __fmul_rn(digit(x, 256.f), 9.0949470177292824e-13f);
+}
+
+// three slices of a float g with |g| <= 1
+__device__ __forceinline__ void slices3(float g, float* out) {
+    float x = g;
+    out[0] = digit(x, 256.f);
+    out[1] = __fmul_rn(digit(x, 256.f), 0.00390625f);
+    out[2] = __fmul_rn(digit(x, 256.f), 1.52587890625e-05f);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
+// acc += x for a float x (exact two-sum into the head, tail accumulated)
+__device__ __forceinline__ void df_acc(F2& acc, float x) {
+    const F2 s = df::two_sum(acc.h, x);
+    acc.h = s.h;
+    acc.l = __fadd_rn(acc.l, s.l);
+}
+
+// sigma[v] = 2^e with 2^(e-1) <= max_c |u[v][c]| < 2^e (1 when the column is zero)
+template <typename TU>
+__global__ void tcx_scale_kernel(const TU* __restrict__ U, int64_t ldu, int64_t Nt, double* __restrict__ sigma) {
+    __shared__ double red[256];
+    const int v = blockIdx.x;
+    double m = 0.0;
+    for (int64_t c = threadIdx.x; c < Nt; c += blockDim.x) m = fmax(m, fabs(double(U[v * ldu + c])));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int e = 0;
+        const double mx = red[0];
+        if (mx > 0.0 && isfinite(mx)) {
+            frexp(mx, &e);
+            sigma[v] = ldexp(1.0, e);
+        } else {
+            sigma[v] = 1.0;
+        }
+    }
+}
+
+// Image of column chunk ch: coordinates (float64 class: double-float heads then tails from Pdf;
+// float32 class: the float32 coordinates P32; zero past Ntilde) and the u slices of the group in
+// the K-major operand layout (rows = vectors, zero past nv and Ntilde).
+template <int CLS, typename TU>
+__global__ void tcx_image_kernel(const float* __restrict__ P, int64_t ldp, int64_t Nt, const TU* __restrict__ U,
+                                 int64_t ldu, int nv, const double* __restrict__ sigma,
+                                 unsigned char* __restrict__ img, int64_t nchunks) {
+    using X = Tx<CLS>;
+    const int t = threadIdx.x;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        unsigned char* base = img + ch * X::kImg;
+        const int64_t c0 = ch * kChunk;
+        if (t < X::kCoords * kChunk) {
+            const int64_t c = c0 + (t % kChunk);
+            reinterpret_cast<float*>(base)[t] = c < Nt ? P[int64_t(t / kChunk) * ldp + c] : 0.f;
+        }
+        if (t < kNB * (kChunk / 8)) {
+            const int v = t / (kChunk / 8), g8 = t % (kChunk / 8);
+            const double inv = (v < nv) ? 1.0 / sigma[v] : 0.0;   // a power of two: exact
+            float sl[X::kSlices][8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t c = c0 + g8 * 8 + e;
+                double x = (v < nv && c < Nt) ? double(U[v * ldu + c]) * inv : 0.0;
+                double w = 1.0;
+#pragma unroll
+                for (int q = 0; q < X::kSlices; ++q) {
+                    const double p = rint(x * 256.0);
+                    x = fma(x, 256.0, -p);   // exact
+                    sl[q][e] = float(p * w);  // |p| <= 256: exact in bfloat16 after scaling
+                    w *= 0.00390625;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < X::kSlices; ++q)
+                *reinterpret_cast<uint4*>(base + X::kCoordBytes + q * kBSlice + kmajor_offset(v, g8 * 8, kBSub)) =
+                    make_uint4(pack_bf16(sl[q][0], sl[q][1]), pack_bf16(sl[q][2], sl[q][3]),
+                               pack_bf16(sl[q][4], sl[q][5]), pack_bf16(sl[q][6], sl[q][7]));
+        }
+    }
+}
+
+// part slot (b, seg) holds [kNB][kRows] doubles: sigma_v 2^-16 / gscale times the row sums
+template <int CLS, int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, const double* __restrict__ sigma,
+                 double* __restrict__ part, int64_t len, int64_t T, int maxseg, int* __restrict__ status) {
+    using X = Tx<CLS>;
+    constexpr int kSlices = X::kSlices, kAccs = X::kAccs, kAStage = X::kAStage, kImg = X::kImg;
+    constexpr int kOffA = X::kOffA, kOffImg = X::kOffImg, kOffTab = X::kOffTab, kOffBar = X::kOffBar;
+    constexpr int kOffTmem = X::kOffTmem, kCoordBytes = X::kCoordBytes;
+    constexpr int kBarLoaded = X::kBarLoaded, kBarFull = X::kBarFull, kBarEmpty = X::kBarEmpty;
+    constexpr int kBarBlkDone = X::kBarBlkDone, kBarBlkFree = X::kBarBlkFree;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + kOffBar;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffTmem);
+    float* stab = reinterpret_cast<float*>(smem + kOffTab);
+
+    if (tid < 128) stab[tid] = cp.tabdf[tid];
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(bar0 + 8 * (kBarLoaded + st), 1);
+            mbar_init(bar0 + 8 * (kBarFull + st), kProducers);
+            mbar_init(bar0 + 8 * (kBarEmpty + st), 1);
+        }
+        for (int p = 0; p < 2; ++p) {
+            mbar_init(bar0 + 8 * (kBarBlkDone + p), 1);
+            mbar_init(bar0 + 8 * (kBarBlkFree + p), kProducers);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t G = gridDim.x;
+    const int64_t t0 = tile_begin(blockIdx.x, T, G);
+    const int ntiles = int(tile_begin(int64_t(blockIdx.x) + 1, T, G) - t0);
+    const int64_t Nt = cp.Nt;
+    const float gscale = cp.gscale;
+    bool ok = true;
+
+    if (warp < kLoaderWarp) {
+        // ------------------------------ producers ------------------------------
+        const int r = tid & (kRows - 1), qd = tid / kRows;   // row in block; columns and vectors qd*8..qd*8+7
+        const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+        int seg = 0, nb = 0, qseg = 0;   // segment, drain block, chunk within the segment
+        int64_t rb = -1;
+        float rc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float* rsrc = CLS == 64 ? cp.Pdf : cp.P32;
+        F2 acc[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] = F2{0.f, 0.f};
+        bool pend = false, pend_seg_end = false;
+        int pend_nb = 0, pend_seg = 0;
+        int64_t pend_rb = 0;
+        // add drain block nb's level accumulators into the double-float sums; at a segment end
+        // write the row's sums to the segment's partial slot.  False if the wait gave up.
+        auto drain = [&](int dnb, bool dseg_end, int64_t drb, int dseg) -> bool {
+            const int dp = dnb & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarBlkDone + dp), uint32_t((dnb >> 1) & 1))))
+                return false;
+            fence_after_sync();
+            float L[kAccs][8];
+#pragma unroll
+            for (int a = 0; a < kAccs; ++a)
+                tmem_ld8(tmem + lane_base + uint32_t(dp * kTmemBuf + a * 32 + qd * 8), L[a]);
+            fence_before_sync();
+            mbar_arrive(bar0 + 8 * (kBarBlkFree + dp));
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+#pragma unroll
+                for (int a = 0; a < kAccs; ++a) df_acc(acc[v], L[a][v]);
+                acc[v] = df::fast_two_sum(acc[v].h, acc[v].l);
+            }
+            if (dseg_end) {
+                if (drb * kRows + r < Nt) {
+                    double* slot = part + (int64_t(blockIdx.x) * maxseg + dseg) * (int64_t(kNB) * kRows) + r;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const int vv = qd * 8 + v;
+                        if (vv < nv)
+                            slot[vv * kRows] = (double(acc[v].h) + double(acc[v].l)) *
+                                               (sigma[vv] * 1.52587890625e-05 / double(gscale));
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[v] = F2{0.f, 0.f};
+            }
+            return true;
+        };
+        for (int i = 0; i < ntiles; ++i) {
+            const int64_t t = t0 + i;
+            if (t / len != rb) {
+                rb = t / len;
+                const int64_t row = rb * kRows + r;
+#pragma unroll
+                for (int k = 0; k < X::kCoords; ++k) rc[k] = row < Nt ? rsrc[k * cp.ldp + row] : 0.f;
+            }
+            if (i == 0 || t % len == 0) qseg = 0;
+            const int st = i % kStages;
+            ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarLoaded + st), uint32_t((i / kStages) & 1)));
+            if (!ok) break;
+            const float* cc = reinterpret_cast<const float*>(smem + kOffImg + st * kImg) + qd * 8;
+            uint32_t w[kSlices][4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float o[2][kSlices];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if constexpr (CLS == 64) {
+                        const float c6[6] = {cc[e + h],           cc[kChunk + e + h],     cc[2 * kChunk + e + h],
+                                             cc[3 * kChunk + e + h], cc[4 * kChunk + e + h], cc[5 * kChunk + e + h]};
+                        F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
+                        g.h = __fmul_rn(g.h, gscale);
+                        g.l = __fmul_rn(g.l, gscale);
+                        slices6(g, o[h]);
+                    } else {
+                        const float x1 = cc[e + h], y1 = cc[kChunk + e + h], z1 = cc[2 * kChunk + e + h];
+                        const float g = kernel32<KIND>(rc[0] - x1, rc[1] - y1, rc[2] - z1, rc[0], rc[1], rc[2], x1,
+                                                       y1, z1, cp.poly_m);
+                        slices3(__fmul_rn(g, gscale), o[h]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(o[0][q], o[1][q]);
+            }
+            unsigned char* As = smem + kOffA + st * kAStage + kmajor_offset(r, qd * 8, kASub);
+#pragma unroll
+            for (int q = 0; q < kSlices; ++q)
+                *reinterpret_cast<uint4*>(As + q * kASlice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            fence_proxy_async();
+            mbar_arrive(bar0 + 8 * (kBarFull + st));
+
+            // drain the block that ended one tile ago (its MMAs have had this tile's evaluation
+            // time to finish; the accumulators are double-buffered, so the tensor core is already
+            // filling the other buffer)
+            if (pend) {
+                ok = drain(pend_nb, pend_seg_end, pend_rb, pend_seg);
+                if (!ok) break;
+                pend = false;
+            }
+            const bool seg_end = (i == ntiles - 1) || ((t + 1) % len == 0);
+            const bool blk_end = seg_end || (qseg % kDrainChunks == kDrainChunks - 1);
+            ++qseg;
+            if (blk_end) {
+                pend = true;
+                pend_nb = nb++;
+                pend_seg_end = seg_end;
+                pend_rb = rb;
+                pend_seg = seg;
+                if (seg_end) ++seg;
+            }
+        }
+        if (ok && pend) ok = drain(pend_nb, pend_seg_end, pend_rb, pend_seg);
+    } else if (warp == kLoaderWarp) {
+        // ------------------------------ loader ------------------------------
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < ntiles; ++i) {
+                const int st = i % kStages;
+                if (i >= kStages) {
+                    ok = mbar_wait(bar0 + 8 * (kBarEmpty + st), uint32_t(((i / kStages) - 1) & 1));
+                    if (!ok) break;
+                }
+                const int64_t ch = (t0 + i) % len;
+                bulk_load(sbase + kOffImg + st * kImg, img + ch * kImg, kImg, bar0 + 8 * (kBarLoaded + st));
+                issued = i + 1;
+            }
+            if (!ok) {
+                for (int i = issued - kStages; i < issued; ++i)
+                    if (i >= 0) mbar_wait(bar0 + 8 * (kBarLoaded + i % kStages), uint32_t((i / kStages) & 1));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            int nb = 0, qseg = 0, committed = 0;
+            for (int i = 0; i < ntiles; ++i) {
+                const int64_t t = t0 + i;
+                const int st = i % kStages;
+                const uint32_t ph = uint32_t((i / kStages) & 1);
+                const bool seg_begin = (i == 0) || (t % len == 0);
+                if (seg_begin) qseg = 0;
+                const bool blk_begin = seg_begin || (qseg % kDrainChunks == 0);
+                const bool seg_end = (i == ntiles - 1) || ((t + 1) % len == 0);
+                const bool blk_end = seg_end || (qseg % kDrainChunks == kDrainChunks - 1);
+                const int dp = nb & 1;
+                if (blk_begin && nb >= 2) {
+                    ok = mbar_wait(bar0 + 8 * (kBarBlkFree + dp), uint32_t(((nb >> 1) - 1) & 1));
+                    if (!ok) break;
+                }
+                ok = mbar_wait(bar0 + 8 * (kBarFull + st), ph);
+                if (!ok) break;
+                ok = mbar_wait(bar0 + 8 * (kBarLoaded + st), ph);
+                if (!ok) break;
+                fence_after_sync();
+                const uint32_t a0 = sbase + kOffA + st * kAStage;
+                const uint32_t b0 = sbase + kOffImg + st * kImg + kCoordBytes;
+#pragma unroll
+                for (int ks = 0; ks < kChunk / kK; ++ks) {
+#pragma unroll
+                    for (int q = 0; q < X::kProducts; ++q) {
+                        int s, u, a;
+                        bool first;
+                        product<CLS>(q, &s, &u, &a, &first);
+                        const uint32_t d = tmem + uint32_t(dp * kTmemBuf + a * 32);
+                        const bool fresh = first && ks == 0 && blk_begin;
+                        mma_bf16(d, make_desc(a0 + s * kASlice + ks * kASub, 128, 256),
+                                 make_desc(b0 + u * kBSlice + ks * kBSub, 128, 256), kIdesc, fresh ? 0u : 1u);
+                    }
+                }
+                mma_commit(bar0 + 8 * (kBarEmpty + st));
+                committed = i + 1;
+                if (blk_end) {
+                    mma_commit(bar0 + 8 * (kBarBlkDone + dp));
+                    ++nb;
+                }
+                ++qseg;
+            }
+            if (!ok && committed > 0) {
+                const int last = committed - 1;
+                mbar_wait(bar0 + 8 * (kBarEmpty + last % kStages), uint32_t((last / kStages) & 1));
+            }
+        }
+        __syncwarp();
+    }
+    fence_before_sync();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    fence_after_sync();
+    if (!ok && tid == 0) atomicExch(status, int(KL_ERR_TIMEOUT));
+    if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int CLS, int KIND>
+cudaError_t launch_kind(const CovParams& cp, const unsigned char* im, int g, const double* sigma, double* part,
+                        const Schedule& sc, int* status, cudaStream_t s) {
+    // the attribute is only ever set to this kernel's one value (safe from concurrent callers)
+    cudaError_t e = cudaFuncSetAttribute(covmv_tcx_kernel<CLS, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Tx<CLS>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    covmv_tcx_kernel<CLS, KIND><<<unsigned(sc.G), kThreads, Tx<CLS>::kSmemBytes, s>>>(cp, im, g, sigma, part, sc.len,
+                                                                                     sc.T, sc.maxseg, status);
+    return cudaGetLastError();
+}
+
+template <int CLS, typename TU>
+cudaError_t launch_tcx(const CovParams& cp, const TU* U, int64_t ldu, int nvec, double* Z, int64_t ldz, double scale2,
+                       const double* J, double* part, void* img, int* status, cudaStream_t s) {
+    using X = Tx<CLS>;
+    const int64_t Nt = cp.Nt;
+    if (Nt == 0 || nvec == 0) return cudaSuccess;
+    Schedule sc;
+    cudaError_t e = make_schedule(Nt, kRows, kChunk, 1, &sc);
+    if (e != cudaSuccess) return e;
+    unsigned char* im = static_cast<unsigned char*>(img);
+    const int64_t nchunks = sc.len;
+    double* sigma = reinterpret_cast<double*>(im + nchunks * X::kImg);
+    const int img_blocks = int(nchunks < 152 * 8 ? nchunks : 152 * 8);
+    const float* P = CLS == 64 ? cp.Pdf : cp.P32;
+    for (int v0 = 0; v0 < nvec; v0 += kNB) {
+        const int g = (nvec - v0) < kNB ? (nvec - v0) : kNB;
+        const TU* Ug = U + int64_t(v0) * ldu;
+        tcx_scale_kernel<TU><<<g, 256, 0, s>>>(Ug, ldu, Nt, sigma);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        tcx_image_kernel<CLS, TU><<<img_blocks, 6 * kChunk, 0, s>>>(P, cp.ldp, Nt, Ug, ldu, g, sigma, im, nchunks);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        switch (cp.kind) {
+            case KL_K_EXP: e = launch_kind<CLS, KL_K_EXP>(cp, im, g, sigma, part, sc, status, s); break;
+            case KL_K_GAUSS: e = launch_kind<CLS, KL_K_GAUSS>(cp, im, g, sigma, part, sc, status, s); break;
+            case KL_K_EXP_SEPARABLE:
+                e = launch_kind<CLS, KL_K_EXP_SEPARABLE>(cp, im, g, sigma, part, sc, status, s);
+                break;
+            default: e = launch_kind<CLS, KL_K_POLY_TEST>(cp, im, g, sigma, part, sc, status, s);
+        }
+        if (e != cudaSuccess) return e;
+        const int64_t tot = Nt * g;
+        int blocks = int((tot + 255) / 256);
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        slot_reduce<kRows, kNB><<<blocks, 256, 0, s>>>(part, Nt, g, sc.len, sc.T, sc.G, sc.maxseg,
+                                                       Z + int64_t(v0) * ldz, ldz, scale2, J);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        count_launches(4);
+    }
+    return cudaSuccess;
+}
+
+size_t part_doubles(int64_t Nt) {
+    Schedule sc;
+    if (Nt <= 0 || make_schedule(Nt, kRows, kChunk, 1, &sc) != cudaSuccess) return 0;
+    return size_t(sc.G) * size_t(sc.maxseg) * kNB * kRows;
+}
+
+}  // namespace
+
+size_t covmv_tc64_part_doubles(int64_t Nt) { return part_doubles(Nt); }
+size_t covmv_tc_part_doubles(int64_t Nt) { return part_doubles(Nt); }
+
+// image bytes followed by the 32 per-vector scales
+size_t covmv_tc64_image_bytes(int64_t Nt) {
+    return size_t((Nt + kChunk - 1) / kChunk) * Tx<64>::kImg + kNB * sizeof(double);
+}
+size_t covmv_tc_image_bytes(int64_t Nt) {
+    return size_t((Nt + kChunk - 1) / kChunk) * Tx<32>::kImg + kNB * sizeof(double);
+}
+
+cudaError_t launch_covmv_tc64(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
+                              double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s) {
+    return launch_tcx<64, double>(cp, U, ldu, nvec, Z, ldz, scale2, J, part, img, status, s);
+}
+
+cudaError_t launch_covmv_tc(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
+                            double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s) {
+    return launch_tcx<32, float>(cp, U, ldu, nvec, Z, ldz, scale2, J, part, img, status, s);
+}
+
+}  // namespace kl

@@ -22,7 +22,7 @@ def cube_exp(kl):
     return P, G
 
 
-@pytest.mark.parametrize("prec", [0, 2], ids=["fp64", "df64"])
+@pytest.mark.parametrize("prec", [0, 2, 4], ids=["fp64", "df64", "tc64"])
 def test_stage5_sampled_rows_at_39k_points(kl, cube_exp, prec):
     import torch
     P, G = cube_exp
@@ -33,6 +33,21 @@ def test_stage5_sampled_rows_at_39k_points(kl, cube_exp, prec):
     rows = np.concatenate([rows, [0, P.Nt - 1]])
     ref = P.stage5(X, u, row_index=rows)
     assert rel(z[rows], ref) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [1, 3], ids=["fp32", "tc32"])
+def test_stage5_float32_class_at_39k_points(kl, cube_exp, prec):
+    """The float32-class products keep float32 accuracy at full size: no float32 sum in the
+    tensor-core kernel spans more than 128 columns, so the error does not grow with the number
+    of points (a version that accumulated whole column ranges in tensor memory reached 4e-4)."""
+    import torch
+    P, G = cube_exp
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, 4, seed=22)
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=prec).cpu().numpy().T
+    rows = np.random.default_rng(6).choice(P.Nt, size=64, replace=False)
+    ref = P.stage5(X, u, row_index=rows)
+    assert rel(z[rows], ref) < 2e-6
 
 
 def test_contractions_at_39k_points(kl, cube_exp):
