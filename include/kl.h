@@ -118,14 +118,16 @@ typedef struct {
  *              (matvec rel. error ~1e-14) at several times the float64 pipe's throughput on
  *              GB300; contractions in float64.
  *   KL_P_TC32  float32-accurate stage 5 on the tensor cores (tcgen05): float32 kernel values
- *              split into three bfloat16 terms, products accumulated in float32 in tensor
- *              memory (relative error ~1e-6, like KL_P_FP32); contractions in float32.
+ *              and u (scaled per vector by a power of two) cut into three exact 8-bit bfloat16
+ *              slices each; the six slice products of the three leading levels are summed
+ *              exactly in tensor memory and drained every 128 columns (relative error ~1e-6,
+ *              like KL_P_FP32, at any size); contractions in float32.
  *              Calls that launch it synchronise the stream once to read a device status
  *              word (KL_ERR_TIMEOUT if a bounded wait inside the kernel gave up).
  *   KL_P_TC64  float64-class stage 5 on the tensor cores: double-float kernel values and the
  *              float64 u (scaled per vector by a power of two) cut into six exact 8-bit
  *              bfloat16 slices each; the 21 slice products of weight >= 2^-48 are summed in
- *              tensor memory, the three leading levels exactly (drained every 128 columns),
+ *              tensor memory, the four leading levels exactly (drained every 128 columns),
  *              so the product matches KL_P_DF64 (matvec rel. error ~1e-14); contractions in
  *              float64.  Same status-word synchronisation as KL_P_TC32.  No counterpart in
  *              the paper, which evaluates the kernel and sums in float64 (Sec. 4.4). */

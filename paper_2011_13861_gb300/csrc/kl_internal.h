@@ -93,14 +93,15 @@ cudaError_t launch_covmv32(const CovParams& cp, const float* U, int64_t ldu, int
                            int64_t ldz, double scale2, const double* J, double* part, int splits,
                            cudaStream_t s);
 int covmv_splits(int64_t Nt, int nvec, bool fp32);
-// tensor-core (tcgen05) float32-accurate stage 5 for groups of 32 vectors; `part` holds
+// tensor-core (tcgen05) float32-class stage 5 (exact 3-digit slicing, covmv_tcx.cu) for groups of
+// 32 vectors; `part` holds
 // covmv_tc_part_doubles doubles, `img` covmv_tc_image_bytes bytes; `status` is a device int that
 // a CTA sets to KL_ERR_TIMEOUT when a bounded wait gives up
 cudaError_t launch_covmv_tc(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
                             double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
 size_t covmv_tc_part_doubles(int64_t Nt);
 size_t covmv_tc_image_bytes(int64_t Nt);
-// tensor-core float64-class stage 5 (exact bfloat16 slicing, see covmv_tc64.cu) for groups of
+// tensor-core float64-class stage 5 (exact bfloat16 slicing, see covmv_tcx.cu) for groups of
 // 32 vectors; `part` holds covmv_tc64_part_doubles doubles, `img` covmv_tc64_image_bytes bytes
 cudaError_t launch_covmv_tc64(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
                               double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
