@@ -212,8 +212,7 @@ typedef struct {
     int maxiter;            /* maximum restarts (0 = 1000) */
     uint64_t seed;
     const double* start_dev;
-    double tol_low;         /* method 1: switch-over residual (0 = 1e-6 for a KL_P_FP32 first phase before a
-                             * KL_P_TC64 polish, else 1e-5) */
+    double tol_low;         /* method 1: switch-over residual (0 = 1e-6 before a KL_P_TC64 polish, else 1e-5) */
     int verify;             /* final residuals ||A~'y - theta y|| / |theta|:
                              * 1 = from the operator products of the basis, carried through every
                              *     restart (A~'Y = (A~'V) S; no extra application);

@@ -21,12 +21,13 @@
 // and the 24-bit fixed point), independent of the number of points, because no float32 sum
 // ever spans more than 128 columns.
 //
-// Pipeline and schedule (persistent tile ranges over (128-row block, 32-column chunk) tiles, one
-// CTA per SM, loader / producers / MMA issuer synchronised by mbarriers):
+// Pipeline and schedule (persistent tile ranges over (128-row block, 32-column chunk) tiles,
+// loader / producers / MMA issuer synchronised by mbarriers):
 //   * loader (one thread): bulk copy per 32-column chunk of a pre-staged image holding the
 //     column coordinates and the u slices (tcx_image_kernel);
-//   * producers (16 warps, four threads per row, 8 columns each): kernel values, S slices each,
-//     written K-major;
+//   * producers (float64 class: 16 warps, four threads per row, 8 columns each; float32 class:
+//     8 warps, two threads per row, 16 columns each, two CTAs per SM): kernel values, S slices
+//     each, written K-major;
 //   * MMA issuer (one thread): one MMA per slice product and 16 columns into the level
 //     accumulators in tensor memory, double-buffered per 128-column drain block.
 // Every wait is bounded (~2 s), after which the CTA records KL_ERR_TIMEOUT, drains its own
@@ -47,13 +48,6 @@ constexpr int kChunk = 32;                        // columns per stage
 constexpr int kStages = 3;
 constexpr int kNB = 32;                           // MMA N: vectors per group
 constexpr int kDrainChunks = 4;                   // level accumulators drained every 128 columns
-constexpr int kProducers = 512;                   // warps 0-15
-constexpr int kThreads = kProducers + 64;         // + loader warp 16 + MMA warp 17
-constexpr int kLoaderWarp = kProducers / 32;
-constexpr int kMmaWarp = kLoaderWarp + 1;
-// tensor memory (512 columns): accumulator a of drain block parity dp at dp*256 + a*32
-constexpr int kTmemCols = 512;
-constexpr int kTmemBuf = 256;
 constexpr int kASub = kRows * kK * 2;             // 128 x 16 bf16: 4 KB
 constexpr int kASlice = kASub * (kChunk / kK);    // 8 KB
 constexpr int kBSub = kNB * kK * 2;               // 32 x 16 bf16: 1 KB
@@ -63,6 +57,18 @@ constexpr uint32_t kIdesc = idesc_bf16(kRows, kNB);
 // per class: slices, products, accumulators, coordinate floats per column, shared-memory layout
 template <int CLS>
 struct Tx {
+    // producers: float64 class 16 warps (four threads per row, 8 columns and 8 vectors each),
+    // float32 class 8 warps (two threads per row, 16 each), then the loader warp and the MMA warp
+    static constexpr int kProducers = CLS == 64 ? 512 : 256;
+    static constexpr int kThreads = kProducers + 64;
+    static constexpr int kLoaderWarp = kProducers / 32;
+    static constexpr int kMmaWarp = kLoaderWarp + 1;
+    static constexpr int kVpt = 32 / (kProducers / 128);      // columns (and vectors) per thread
+    // tensor memory: accumulator a of drain-block parity dp at dp * kTmemBuf + a * 32; the float32
+    // class needs 192 columns, so two of its CTAs share an SM
+    static constexpr int kTmemCols = CLS == 64 ? 512 : 256;
+    static constexpr int kTmemBuf = kTmemCols / 2;
+    static constexpr int kCtasPerSm = CLS == 64 ? 1 : 2;
     static constexpr int kSlices = CLS == 64 ? 6 : 3;
     static constexpr int kProducts = CLS == 64 ? 21 : 6;
     static constexpr int kAccs = CLS == 64 ? 5 : 3;
@@ -204,7 +210,7 @@ __global__ void tcx_image_kernel(const float* __restrict__ P, int64_t ldp, int64
 
 // part slot (b, seg) holds [kNB][kRows] doubles: sigma_v 2^-16 / gscale times the row sums
 template <int CLS, int KIND>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Tx<CLS>::kThreads, Tx<CLS>::kCtasPerSm)
 covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, const double* __restrict__ sigma,
                  double* __restrict__ part, int64_t len, int64_t T, int maxseg, int* __restrict__ status) {
     using X = Tx<CLS>;
@@ -213,6 +219,8 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
     constexpr int kOffTmem = X::kOffTmem, kCoordBytes = X::kCoordBytes;
     constexpr int kBarLoaded = X::kBarLoaded, kBarFull = X::kBarFull, kBarEmpty = X::kBarEmpty;
     constexpr int kBarBlkDone = X::kBarBlkDone, kBarBlkFree = X::kBarBlkFree;
+    constexpr int kProducers = X::kProducers, kLoaderWarp = X::kLoaderWarp, kMmaWarp = X::kMmaWarp;
+    constexpr int kVpt = X::kVpt, kTmemCols = X::kTmemCols, kTmemBuf = X::kTmemBuf;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_u32(smem);
@@ -248,15 +256,15 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
 
     if (warp < kLoaderWarp) {
         // ------------------------------ producers ------------------------------
-        const int r = tid & (kRows - 1), qd = tid / kRows;   // row in block; columns and vectors qd*8..qd*8+7
+        const int r = tid & (kRows - 1), qd = tid / kRows;   // row in block; columns and vectors qd*kVpt..
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
         int seg = 0, nb = 0, qseg = 0;   // segment, drain block, chunk within the segment
         int64_t rb = -1;
         float rc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float* rsrc = CLS == 64 ? cp.Pdf : cp.P32;
-        F2 acc[8];
+        F2 acc[kVpt];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) acc[v] = F2{0.f, 0.f};
+        for (int v = 0; v < kVpt; ++v) acc[v] = F2{0.f, 0.f};
         bool pend = false, pend_seg_end = false;
         int pend_nb = 0, pend_seg = 0;
         int64_t pend_rb = 0;
@@ -267,31 +275,34 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
             if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarBlkDone + dp), uint32_t((dnb >> 1) & 1))))
                 return false;
             fence_after_sync();
-            float L[kAccs][8];
 #pragma unroll
-            for (int a = 0; a < kAccs; ++a)
-                tmem_ld8(tmem + lane_base + uint32_t(dp * kTmemBuf + a * 32 + qd * 8), L[a]);
+            for (int g8 = 0; g8 < kVpt / 8; ++g8) {
+                float L[kAccs][8];
+#pragma unroll
+                for (int a = 0; a < kAccs; ++a)
+                    tmem_ld8(tmem + lane_base + uint32_t(dp * kTmemBuf + a * 32 + qd * kVpt + g8 * 8), L[a]);
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+#pragma unroll
+                    for (int a = 0; a < kAccs; ++a) df_acc(acc[g8 * 8 + v], L[a][v]);
+                    acc[g8 * 8 + v] = df::fast_two_sum(acc[g8 * 8 + v].h, acc[g8 * 8 + v].l);
+                }
+            }
             fence_before_sync();
             mbar_arrive(bar0 + 8 * (kBarBlkFree + dp));
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-#pragma unroll
-                for (int a = 0; a < kAccs; ++a) df_acc(acc[v], L[a][v]);
-                acc[v] = df::fast_two_sum(acc[v].h, acc[v].l);
-            }
             if (dseg_end) {
                 if (drb * kRows + r < Nt) {
                     double* slot = part + (int64_t(blockIdx.x) * maxseg + dseg) * (int64_t(kNB) * kRows) + r;
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        const int vv = qd * 8 + v;
+                    for (int v = 0; v < kVpt; ++v) {
+                        const int vv = qd * kVpt + v;
                         if (vv < nv)
                             slot[vv * kRows] = (double(acc[v].h) + double(acc[v].l)) *
                                                (sigma[vv] * 1.52587890625e-05 / double(gscale));
                     }
                 }
 #pragma unroll
-                for (int v = 0; v < 8; ++v) acc[v] = F2{0.f, 0.f};
+                for (int v = 0; v < kVpt; ++v) acc[v] = F2{0.f, 0.f};
             }
             return true;
         };
@@ -307,34 +318,51 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
             const int st = i % kStages;
             ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarLoaded + st), uint32_t((i / kStages) & 1)));
             if (!ok) break;
-            const float* cc = reinterpret_cast<const float*>(smem + kOffImg + st * kImg) + qd * 8;
-            uint32_t w[kSlices][4];
+            const float* img_c = reinterpret_cast<const float*>(smem + kOffImg + st * kImg);
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                float o[2][kSlices];
+            for (int g8 = 0; g8 < kVpt / 8; ++g8) {
+                // the 8 columns qd*kVpt + g8*8 .. +7; the float32 class reads their coordinates as
+                // float4 pairs, the float64 class value by value (fewer live registers)
+                const int c0 = qd * kVpt + g8 * 8;
+                float cv[3][8];
+                if constexpr (CLS == 32) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if constexpr (CLS == 64) {
-                        const float c6[6] = {cc[e + h],           cc[kChunk + e + h],     cc[2 * kChunk + e + h],
-                                             cc[3 * kChunk + e + h], cc[4 * kChunk + e + h], cc[5 * kChunk + e + h]};
-                        F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
-                        g.h = __fmul_rn(g.h, gscale);
-                        g.l = __fmul_rn(g.l, gscale);
-                        slices6(g, o[h]);
-                    } else {
-                        const float x1 = cc[e + h], y1 = cc[kChunk + e + h], z1 = cc[2 * kChunk + e + h];
-                        const float g = kernel32<KIND>(rc[0] - x1, rc[1] - y1, rc[2] - z1, rc[0], rc[1], rc[2], x1,
-                                                       y1, z1, cp.poly_m);
-                        slices3(__fmul_rn(g, gscale), o[h]);
+                    for (int k = 0; k < 3; ++k) {
+                        const float4 a = *reinterpret_cast<const float4*>(img_c + k * kChunk + c0);
+                        const float4 b = *reinterpret_cast<const float4*>(img_c + k * kChunk + c0 + 4);
+                        cv[k][0] = a.x; cv[k][1] = a.y; cv[k][2] = a.z; cv[k][3] = a.w;
+                        cv[k][4] = b.x; cv[k][5] = b.y; cv[k][6] = b.z; cv[k][7] = b.w;
                     }
                 }
+                uint32_t w[kSlices][4];
 #pragma unroll
-                for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(o[0][q], o[1][q]);
+                for (int e = 0; e < 8; e += 2) {
+                    float o[2][kSlices];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if constexpr (CLS == 64) {
+                            const float* cc = img_c + c0 + e + h;
+                            const float c6[6] = {cc[0],          cc[kChunk],     cc[2 * kChunk],
+                                                 cc[3 * kChunk], cc[4 * kChunk], cc[5 * kChunk]};
+                            F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
+                            g.h = __fmul_rn(g.h, gscale);
+                            g.l = __fmul_rn(g.l, gscale);
+                            slices6(g, o[h]);
+                        } else {
+                            const float x1 = cv[0][e + h], y1 = cv[1][e + h], z1 = cv[2][e + h];
+                            const float g = kernel32<KIND>(rc[0] - x1, rc[1] - y1, rc[2] - z1, rc[0], rc[1], rc[2],
+                                                           x1, y1, z1, cp.poly_m);
+                            slices3(__fmul_rn(g, gscale), o[h]);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(o[0][q], o[1][q]);
+                }
+                unsigned char* As = smem + kOffA + st * kAStage + kmajor_offset(r, c0, kASub);
+#pragma unroll
+                for (int q = 0; q < kSlices; ++q)
+                    *reinterpret_cast<uint4*>(As + q * kASlice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
             }
-            unsigned char* As = smem + kOffA + st * kAStage + kmajor_offset(r, qd * 8, kASub);
-#pragma unroll
-            for (int q = 0; q < kSlices; ++q)
-                *reinterpret_cast<uint4*>(As + q * kASlice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
             fence_proxy_async();
             mbar_arrive(bar0 + 8 * (kBarFull + st));
 
@@ -446,8 +474,8 @@ cudaError_t launch_kind(const CovParams& cp, const unsigned char* im, int g, con
     cudaError_t e = cudaFuncSetAttribute(covmv_tcx_kernel<CLS, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Tx<CLS>::kSmemBytes);
     if (e != cudaSuccess) return e;
-    covmv_tcx_kernel<CLS, KIND><<<unsigned(sc.G), kThreads, Tx<CLS>::kSmemBytes, s>>>(cp, im, g, sigma, part, sc.len,
-                                                                                     sc.T, sc.maxseg, status);
+    covmv_tcx_kernel<CLS, KIND><<<unsigned(sc.G), Tx<CLS>::kThreads, Tx<CLS>::kSmemBytes, s>>>(
+        cp, im, g, sigma, part, sc.len, sc.T, sc.maxseg, status);
     return cudaGetLastError();
 }
 
@@ -458,7 +486,7 @@ cudaError_t launch_tcx(const CovParams& cp, const TU* U, int64_t ldu, int nvec, 
     const int64_t Nt = cp.Nt;
     if (Nt == 0 || nvec == 0) return cudaSuccess;
     Schedule sc;
-    cudaError_t e = make_schedule(Nt, kRows, kChunk, 1, &sc);
+    cudaError_t e = make_schedule(Nt, kRows, kChunk, X::kCtasPerSm, &sc);
     if (e != cudaSuccess) return e;
     unsigned char* im = static_cast<unsigned char*>(img);
     const int64_t nchunks = sc.len;
@@ -495,16 +523,17 @@ cudaError_t launch_tcx(const CovParams& cp, const TU* U, int64_t ldu, int nvec, 
     return cudaSuccess;
 }
 
+template <int CLS>
 size_t part_doubles(int64_t Nt) {
     Schedule sc;
-    if (Nt <= 0 || make_schedule(Nt, kRows, kChunk, 1, &sc) != cudaSuccess) return 0;
+    if (Nt <= 0 || make_schedule(Nt, kRows, kChunk, Tx<CLS>::kCtasPerSm, &sc) != cudaSuccess) return 0;
     return size_t(sc.G) * size_t(sc.maxseg) * kNB * kRows;
 }
 
 }  // namespace
 
-size_t covmv_tc64_part_doubles(int64_t Nt) { return part_doubles(Nt); }
-size_t covmv_tc_part_doubles(int64_t Nt) { return part_doubles(Nt); }
+size_t covmv_tc64_part_doubles(int64_t Nt) { return part_doubles<64>(Nt); }
+size_t covmv_tc_part_doubles(int64_t Nt) { return part_doubles<32>(Nt); }
 
 // image bytes followed by the 32 per-vector scales
 size_t covmv_tc64_image_bytes(int64_t Nt) {

@@ -412,8 +412,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         // the float32 operator's error is relative to |lambda_1|, the residual test to |theta_i|:
         // before a tensor-core polish (whose launches cost as much as ~8 float32 block
         // applications) the float32 phase goes one decade further
-        const double tl = o.tol_low > 0.0 ? o.tol_low
-                                          : ((o.precision == KL_P_TC64 && o.low_precision != KL_P_TC32) ? 1e-6 : 1e-5);
+        const double tl = o.tol_low > 0.0 ? o.tol_low : (o.precision == KL_P_TC64 ? 1e-6 : 1e-5);
         const int pb = std::min(pol_b, m);
         const int lowp = (o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32;
         Phase P1{lowp, b, m, keep, std::max(tl, tol), false, maxrestart, pb};
