@@ -218,9 +218,10 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
     32 leading eigenvectors of `train_solves` coarse problems (p=3, 16^3 elements; kernel, L and
     radii drawn with seed 5), then used, prolonged exactly to 48^3 elements, as the start block
     of the mixed solver (20 eigenpairs, residual 1e-8) for unseen parameter sets (seed 6); against
-    the same solver from the random start (block 32 as the warm start, and block 16, its best
-    width) and, for the first parameter set, random-start float64 block Lanczos (block 4).  Also
-    timed: the 32 predicted vectors compressed by Rayleigh-Ritz to a block-16 start."""
+    the same solver from the random start (block 32, basis 96 and the tensor-core float32 first
+    phase as the warm start; and block 16 with the scalar float32 first phase, the best random-start
+    configuration) and, for the first parameter set, random-start float64 block Lanczos (block 4).
+    Also timed: the 32 predicted vectors compressed by Rayleigh-Ritz to a block-16 start."""
     import numpy as np
     import torch
     from paper_2011_13861_gb300 import warmstart
@@ -247,8 +248,12 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
     for i, prm in enumerate(inputs.warmstart_params(n_eval, seed=6)):
         fine = warmstart.problem(prm, 3, 48)
         mixed = dict(method=1, precision=kl.KL_P_TC64)
+        # workspaces of every width and precision allocated before any timed solve
+        for nv, pr in ((32, kl.KL_P_TC32), (32, kl.KL_P_FP32), (16, kl.KL_P_FP32), (32, kl.KL_P_TC64)):
+            fine.apply(torch.zeros((nv, fine.N), dtype=torch.float64, device="cuda"), precision=pr)
         tw, (ev_w, vec_w, iw) = timed(lambda: ws.solve(fine, prm, k, tol=TOL))
-        t32, (ev_r, _, i32) = timed(lambda: fine.eigs(k, TOL, block=32, want_vectors=False, **mixed))
+        t32, (ev_r, _, i32) = timed(lambda: fine.eigs(k, TOL, block=32, ncv=96, low_precision=kl.KL_P_TC32,
+                                                      want_vectors=False, **mixed))
         t16, (_, _, i16) = timed(lambda: fine.eigs(k, TOL, block=16, want_vectors=False, **mixed))
         tc, (_, _, ic) = timed(lambda: ws.solve(fine, prm, k, tol=TOL, block=16))
         # subspace of the prediction against the converged eigenvectors (diagnostic)

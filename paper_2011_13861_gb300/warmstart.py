@@ -121,7 +121,8 @@ class WarmStart:
 
     def solve(self, fine, prm, nev, tol=1e-8, maxiter=40, fallback=True, block=None, **eig_kw):
         """The nev leading eigenpairs of `fine` from the warm start.  By default the k predicted
-        vectors form the start block (block = k, basis 3 k); with block < k they are compressed
+        vectors form the start block (block = k, basis 3 k, tensor-core float32 first phase for
+        blocks wider than 16); with block < k they are compressed
         by Rayleigh-Ritz to the `block` leading Ritz vectors (kl_eig_opts.nstart).  When the
         warm solve has not converged after `maxiter` restarts, the seeded random start with the
         same options takes over (fallback=True).  Returns (evals, evecs, info) with
@@ -132,6 +133,11 @@ class WarmStart:
         block = self.k if block is None else min(int(block), self.k)
         if block == self.k:
             kw.setdefault("ncv", max(3 * block, -(-(nev + 2 * block) // block) * block))
+        if block > 16:
+            # a tensor-core float32 launch costs the same for up to 32 vectors: for wide start
+            # blocks it is the cheaper first phase (the scalar float32 kernel's cost grows with the
+            # block width)
+            kw.setdefault("low_precision", B.KL_P_TC32)
         t0 = time.perf_counter()
         start = self.start_block(fine, prm).contiguous()
         torch.cuda.synchronize()
