@@ -219,7 +219,9 @@ typedef struct {
                              * 2 = from a fresh application with the float64 kernel;
                              * 0 = the Lanczos estimates */
     int precision;          /* accurate-phase arithmetic: KL_P_FP64 (0, default), KL_P_DF64 or KL_P_TC64;
-                             * method 0: every application, method 1: the polish */
+                             * method 0: every application, method 1: the polish.  Method 0 also
+                             * takes KL_P_FP32 or KL_P_TC32 (float32-class results: tolerances of
+                             * ~1e-5 and above, e.g. training data for the warm start) */
     int polish_block;       /* method 1: width of the polish block (k..48; 0 = k, or max(k, 32)
                              * for KL_P_TC64, whose launches cost the same up to 32 vectors) */
     int polish_ncv;         /* method 1: polish basis size (0 = 3 x polish_block, at most 160) */

@@ -325,10 +325,14 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.low_precision = KL_P_FP32;
     o.nstart = 0;
     if (opts_in) o = *opts_in;
-    if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64 && o.precision != KL_P_TC64)
-        return fail(KL_ERR_INVALID_ARG, "opts.precision must be KL_P_FP64, KL_P_DF64 or KL_P_TC64");
-    const int b = std::max(1, o.block);
     if (o.method != 0 && o.method != 1) return fail(KL_ERR_INVALID_ARG, "method must be 0 or 1");
+    // float32-class arithmetic throughout is allowed for the plain method (results accurate to
+    // the float32 operator: residual tolerances of about 1e-5 and above, e.g. training data)
+    const bool f32_plain = (o.method == 0 && (o.precision == KL_P_FP32 || o.precision == KL_P_TC32));
+    if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64 && o.precision != KL_P_TC64 && !f32_plain)
+        return fail(KL_ERR_INVALID_ARG,
+                    "opts.precision must be KL_P_FP64, KL_P_DF64 or KL_P_TC64 (or KL_P_FP32 / KL_P_TC32 with method 0)");
+    const int b = std::max(1, o.block);
     if (b > 64) return fail(KL_ERR_INVALID_ARG, "block size above 64");
     const int64_t N = h->N;
     int m = o.ncv > 0 ? o.ncv : std::max(2 * k + 1, k + 3 * b);
@@ -438,7 +442,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     }
 
     // a bounded wait that gave up inside a tensor-core kernel invalidates the solve
-    if (o.precision == KL_P_TC64) KL_TRY(check_device_status(h, s));
+    if (o.precision == KL_P_TC64 || o.precision == KL_P_TC32) KL_TRY(check_device_status(h, s));
 
     // ---- outputs ----
     for (int i = 0; i < k; ++i) evals_host[i] = theta[i];
