@@ -568,8 +568,8 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     const std::vector<double>& J = h->J_host;
     std::vector<float> Jf(static_cast<size_t>(Nt));
     for (int64_t i = 0; i < Nt; ++i) Jf[size_t(i)] = float(J[size_t(i)]);
-    std::vector<double> tab(64);
-    for (int j = 0; j < 64; ++j) tab[j] = exp2(double(j) / 64.0);
+    std::vector<double> tab(1024);   // 2^(j/1024) for the float64 exponential (Tang's method)
+    for (int j = 0; j < 1024; ++j) tab[j] = exp2(double(j) / 1024.0);
 
     kl_status st = KL_OK;
     auto chk = [&](kl_status s2) {
