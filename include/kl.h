@@ -342,6 +342,12 @@ kl_status kl_to_bspline(kl_handle h, const double* vprime_dev, double* v_dev, in
 
 /* Number of CUDA kernels this library has launched since it was loaded (all handles, all
  * threads); for tracing and launch accounting. */
+/* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an
+ * mbarrier that nothing completes, with the bounded-wait helper of the tensor-core kernels,
+ * gives up after `seconds` (0 < seconds <= 2) and reports it.  Returns KL_ERR_TIMEOUT, the
+ * status a stalled tensor-core pipeline returns; the context stays usable.  Synchronous. */
+kl_status kl_wait_selftest(double seconds, void* stream);
+
 uint64_t kl_kernel_launches(void);
 
 const char* kl_last_error(void);

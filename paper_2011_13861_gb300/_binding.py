@@ -92,6 +92,7 @@ SIGNATURES = {
                                     ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
     "kl_mlp_destroy": (None, [_vp]),
     "kl_prolong": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
     "kl_destroy": (None, [_vp]),
@@ -475,3 +476,10 @@ def prolong(coarse, fine, v, stream=None):
     out = torch.empty((vb.shape[0], fine.N), dtype=torch.float64, device=vb.device)
     _check(load().kl_prolong(coarse._h, fine._h, _ptr(vb), _ptr(out), int(vb.shape[0]), _stream(stream)))
     return out if v.dim() > 1 else out.reshape(-1)
+
+
+def wait_selftest(seconds=0.05, stream=None):
+    """kl_wait_selftest: status code of a bounded wait that nothing completes (KL_ERR_TIMEOUT
+    expected) and the library's message."""
+    st = load().kl_wait_selftest(float(seconds), _stream(stream))
+    return st, load().kl_last_error().decode()

@@ -20,6 +20,8 @@
 // residual estimates of the wanted pairs (a few hundred bytes).
 #include <math.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <chrono>
 #include <vector>
@@ -233,6 +235,9 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                 KL_CUDA(cudaMemcpyAsync(th.data(), E.Theta(), nc * sizeof(double), cudaMemcpyDeviceToHost, E.s));
                 KL_CUDA(cudaMemcpyAsync(rs.data(), E.Est(), nc * sizeof(double), cudaMemcpyDeviceToHost, E.s));
                 KL_CUDA(cudaStreamSynchronize(E.s));
+                for (int i = 0; i < nc; ++i)
+                    if (!std::isfinite(th[i]) || !std::isfinite(rs[i]))
+                        return fail(KL_ERR_NUMERIC, "non-finite Ritz values (NaN or Inf in the start block or the operator)");
                 bool ok = (nc == k);
                 for (int i = 0; i < nc && ok; ++i) ok = rs[i] <= P.tol * fabs(th[i]);
                 if (ok) {
@@ -274,6 +279,9 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         KL_CUDA(cudaMemcpyAsync(theta.data(), E.Theta(), j * sizeof(double), cudaMemcpyDeviceToHost, E.s));
         KL_CUDA(cudaMemcpyAsync(est.data(), E.Est(), nk * sizeof(double), cudaMemcpyDeviceToHost, E.s));
         KL_CUDA(cudaStreamSynchronize(E.s));
+        for (int i = 0; i < std::min(k, nk); ++i)
+            if (!std::isfinite(theta[i]) || !std::isfinite(est[i]))
+                return fail(KL_ERR_NUMERIC, "non-finite Ritz values (NaN or Inf in the start block or the operator)");
         bool ok = true;
         for (int i = 0; i < k; ++i) ok = ok && (est[i] <= P.tol * fabs(theta[i]));
         const bool last = (it >= P.maxrestart);
@@ -379,6 +387,18 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     if (e != cudaSuccess) return cuda_fail(e, "memset");
 
     // ---- start block ----
+    if (o.start_dev) {
+        // a caller's start block with NaN or Inf is an error, not a rank-deficient block to replace
+        e = launch_copy_block(o.start_dev, N, E.W(), N, N, nst, s);
+        if (e == cudaSuccess) e = launch_gram(E.W(), N, nst, E.W(), N, nst, N, E.G(), nst, E.Part(), E.maxparts, s);
+        if (e != cudaSuccess) return cuda_fail(e, "start block");
+        std::vector<double> g(size_t(nst) * nst);
+        KL_CUDA(cudaMemcpyAsync(g.data(), E.G(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        KL_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nst; ++i)
+            if (!std::isfinite(g[size_t(i) * nst + i]))
+                return fail(KL_ERR_NUMERIC, "the start block contains NaN or Inf");
+    }
     if (o.start_dev && nst > b) {
         // Rayleigh-Ritz on span(start): orthonormal basis in V[:, 0:nst], its products in AV,
         // T = V^T A V, then W = the b leading Ritz vectors

@@ -69,11 +69,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait for the phase with the given parity; false on timeout (~2 s at 2 GHz)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait for the phase with the given parity; false after max_clocks SM clocks
+// (default ~2 s at 2 GHz)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long max_clocks = 4000000000ll) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 4000000000ll) return false;
+        if (clock64() - t0 > max_clocks) return false;
     }
     return true;
 }
