@@ -126,8 +126,8 @@ class WarmStart:
         vectors form the start block (block = k, basis 3 k, tensor-core float32 first phase for
         blocks wider than 16); with block < k they are compressed
         by Rayleigh-Ritz to the `block` leading Ritz vectors (kl_eig_opts.nstart).  When the
-        warm solve has not converged after `maxiter` restarts, the seeded random start with the
-        same options takes over (fallback=True).  Returns (evals, evecs, info) with
+        warm solve has not converged after `maxiter` restarts, or the prediction holds NaN or
+        Inf, the seeded random start with the same options takes over (fallback=True).  Returns (evals, evecs, info) with
         info['path'] = 'warm' | 'fallback' and info['warm'] = the warm attempt's info."""
         import torch
         kw = dict(method=1, precision=B.KL_P_TC64)
@@ -144,8 +144,14 @@ class WarmStart:
         start = self.start_block(fine, prm).contiguous()
         torch.cuda.synchronize()
         t_start = time.perf_counter() - t0
-        ev, vecs, info = fine.eigs(nev, tol=tol, block=block, start=start, maxiter=maxiter, raise_on_nonconv=False,
-                                   **kw)
+        try:
+            ev, vecs, info = fine.eigs(nev, tol=tol, block=block, start=start, maxiter=maxiter,
+                                       raise_on_nonconv=False, **kw)
+        except B.KLError as err:
+            # a prediction with NaN or Inf (KL_ERR_NUMERIC) is a failed warm start, not a failed solve
+            if not fallback or B.STATUS.get(err.status) != "KL_ERR_NUMERIC":
+                raise
+            info = {"converged": -1, "error": str(err)}
         info["ms_start_block"] = 1e3 * t_start
         if info["converged"] >= nev or not fallback:
             info["path"] = "warm"

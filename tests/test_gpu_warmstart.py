@@ -279,3 +279,18 @@ def test_float32_class_plain_solve(kl, prec):
     assert np.abs(ev1 - ev0).max() <= 1e-5 * ev0[0], np.abs(ev1 - ev0).max() / ev0[0]
     s = np.linalg.svd(V0[:6].cpu().numpy() @ V1[:6].cpu().numpy().T, compute_uv=False)
     assert np.sqrt(max(0.0, 1.0 - s.min() ** 2)) < 1e-3, s
+
+
+def test_fallback_when_the_prediction_is_not_finite(kl):
+    """A network whose output is NaN (a poisoned bias) makes the warm start fail with
+    KL_ERR_NUMERIC inside the solver; the random-start solve takes over."""
+    from paper_2011_13861_gb300 import warmstart
+    ws = warmstart.WarmStart(seed=9, **SMALL)
+    Ws, bs = ws.net.get_params()
+    bs[-1][3] = np.nan
+    ws.net.set_params(Ws, bs)
+    prm = {"kernel": "exp", "L": 0.8, "r_in": 1.0, "r_out": 2.0}
+    fine = warmstart.problem(prm, SMALL["p"], FINE_NE)
+    ev, _, info = ws.solve(fine, prm, NEV, tol=1e-8)
+    assert info["path"] == "fallback" and "NUMERIC" in info["warm"]["error"]
+    assert info["converged"] >= NEV
