@@ -1,4 +1,5 @@
 // C ABI entry points, handle set-up and the operator application of Algorithm 1.
+#include <algorithm>
 #include <math.h>
 
 #include <atomic>
@@ -551,13 +552,31 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
             P[size_t(c) * Nt + i] = x * s64;
             Pf[size_t(c) * Nt + i] = float(x * s32);
         }
+    // double-float coordinates in grid form: heads on the grid q = 2^(E-23), where every scaled
+    // coordinate is below 2^E in magnitude, tails the float remainders (|tail| <= q/2).  Head
+    // differences are then exact, which the kernels' point differences rely on.  The
+    // stationary kernels see differences only, so their points are first centred on the
+    // bounding box (one more bit for domains away from the origin).
+    double ctr[3] = {0.0, 0.0, 0.0};
+    if (kind != KL_K_POLY_TEST && Nt > 0)
+        for (int c = 0; c < 3; ++c) {
+            const auto b = P.begin() + ptrdiff_t(c) * Nt;
+            const auto mm = std::minmax_element(b, b + Nt);
+            ctr[c] = 0.5 * (*mm.first + *mm.second);
+        }
+    double pmax = 0.0;
+    for (int c = 0; c < 3; ++c)
+        for (int64_t i = 0; i < Nt; ++i) pmax = fmax(pmax, fabs(P[size_t(c) * Nt + i] - ctr[c]));
+    int pe = 0;
+    if (pmax > 0.0) frexp(pmax, &pe);
+    const double q = ldexp(1.0, pe - 23);
     std::vector<float> Pdf(size_t(Nt) * 6);
     for (int c = 0; c < 3; ++c)
         for (int64_t i = 0; i < Nt; ++i) {
-            const double x = P[size_t(c) * Nt + i];
-            const float xh = float(x);
-            Pdf[size_t(c) * Nt + i] = xh;
-            Pdf[size_t(3 + c) * Nt + i] = float(x - double(xh));
+            const double x = P[size_t(c) * Nt + i] - ctr[c];
+            const double xh = rint(x / q) * q;   // at most 2^23 grid steps: exact in float
+            Pdf[size_t(c) * Nt + i] = float(xh);
+            Pdf[size_t(3 + c) * Nt + i] = float(x - xh);
         }
     std::vector<float> tabdf(128);
     for (int j = 0; j < 64; ++j) {

@@ -7,11 +7,12 @@
 // g = sum_{s<S} a_s 2^(-8(s+1)) with integer digits (|a_0| <= 256, |a_s| <= 128 after, by
 // round-to-nearest digit extraction, every step exact), and each u value, after division by a
 // per-vector power of two sigma >= max|u|, as u/sigma = sum_{t<S} b_t 2^(-8(t+1)).  The digits
-// are stored as bfloat16 "slices" a_s 2^(-8s) and b_t 2^(-8t), which bfloat16 holds exactly.
+// are stored as bfloat16 "slices" a_s 2^(-8(s+1)) and b_t 2^(-8t), which bfloat16 holds exactly.
 // The tensor core forms the slice products exactly and adds them in float32, one accumulator per
 // level d = s + t:
-//   float64 class: levels 0-3 (1, 2, 3, 4 products) are multiples of 2^-8d below 2^(24-8d)
-//     over 128 columns, hence exact in float32 whatever the tensor core's rounding; levels 4-5
+//   float64 class: levels 0-3 (1, 2, 3, 4 products) are multiples of 2^-8(d+1) and, summed over
+//     128 columns, below 2^23 of that unit, hence exact in float32 whatever the tensor core's
+//     rounding; levels 4-5
 //     (11 products, relative size <= 2^-32) share a fifth accumulator whose rounding stays
 //     below ~2^-49 of the sum; products of levels >= 6 (relative size < 2^-48) are dropped;
 //   float32 class: levels 0-2 (1, 2, 3 products) are exact the same way; levels >= 3
@@ -101,33 +102,33 @@ __device__ __forceinline__ void product(int q, int* s, int* t, int* acc, bool* f
     *first = (q == 0 || q == 1 || q == 3 || q == 6 || q == 10);
 }
 
-// integer digit of x * scale by round-to-nearest (|x * scale| < 2^22), and the exact remainder
-__device__ __forceinline__ float digit(float& x, float scale) {
-    const float magic = 12582912.0f;   // 1.5 * 2^23
-    const float p = __fsub_rn(__fmaf_rn(x, scale, magic), magic);
-    x = __fmaf_rn(x, scale, -p);
+// x rounded to the grid 2^-k (|x| < 2^(22-k)) by the shifter 1.5 * 2^(23-k), and the exact
+// remainder: the slice a 2^-k of digit a
+__device__ __forceinline__ float digit(float& x, float shifter) {
+    const float p = __fsub_rn(__fadd_rn(x, shifter), shifter);
+    x = __fsub_rn(x, p);
     return p;
 }
 
-// six slices a_s 2^(-8s) of a double-float g with |g| <= 1 (see the file comment); the tail
-// joins the remainder after the three head digits
+// six slices a_s 2^(-8(s+1)) of a double-float g with |g| <= 1 (see the file comment); the
+// tail joins the remainder after the three head digits
 __device__ __forceinline__ void slices6(F2 g, float* out) {
     float x = g.h;
-    out[0] = digit(x, 256.f);
-    out[1] = __fmul_rn(digit(x, 256.f), 0.00390625f);
-    out[2] = __fmul_rn(digit(x, 256.f), 1.52587890625e-05f);
-    x = __fmaf_rn(g.l, 16777216.f, x);   // remainder is in units of 2^-24
-    out[3] = __fmul_rn(digit(x, 256.f), 5.9604644775390625e-08f);
-    out[4] = __fmul_rn(digit(x, 256.f), 2.3283064365386963e-10f);
-    out[5] = __fmul_rn(digit(x, 256.f), 9.0949470177292824e-13f);
+    out[0] = digit(x, 49152.f);                     // 1.5 * 2^15: grid 2^-8
+    out[1] = digit(x, 192.f);                       // grid 2^-16
+    out[2] = digit(x, 0.75f);                       // grid 2^-24
+    x = __fadd_rn(x, g.l);                          // |x| <= 2^-25 after three digits
+    out[3] = digit(x, 0.0029296875f);               // 1.5 * 2^-9: grid 2^-32
+    out[4] = digit(x, 1.1444091796875e-05f);        // 1.5 * 2^-17: grid 2^-40
+    out[5] = digit(x, 4.4703483581542969e-08f);     // 1.5 * 2^-25: grid 2^-48
 }
 
 // three slices of a float g with |g| <= 1
 __device__ __forceinline__ void slices3(float g, float* out) {
     float x = g;
-    out[0] = digit(x, 256.f);
-    out[1] = __fmul_rn(digit(x, 256.f), 0.00390625f);
-    out[2] = __fmul_rn(digit(x, 256.f), 1.52587890625e-05f);
+    out[0] = digit(x, 49152.f);
+    out[1] = digit(x, 192.f);
+    out[2] = digit(x, 0.75f);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -208,7 +209,7 @@ __global__ void tcx_image_kernel(const float* __restrict__ P, int64_t ldp, int64
     }
 }
 
-// part slot (b, seg) holds [kNB][kRows] doubles: sigma_v 2^-16 / gscale times the row sums
+// part slot (b, seg) holds [kNB][kRows] doubles: sigma_v 2^-8 / gscale times the row sums
 template <int CLS, int KIND>
 __global__ void __launch_bounds__(Tx<CLS>::kThreads, Tx<CLS>::kCtasPerSm)
 covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, const double* __restrict__ sigma,
@@ -298,7 +299,7 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
                         const int vv = qd * kVpt + v;
                         if (vv < nv)
                             slot[vv * kRows] = (double(acc[v].h) + double(acc[v].l)) *
-                                               (sigma[vv] * 1.52587890625e-05 / double(gscale));
+                                               (sigma[vv] * 0.00390625 / double(gscale));
                     }
                 }
 #pragma unroll
@@ -345,14 +346,16 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
                             const float c6[6] = {cc[0],          cc[kChunk],     cc[2 * kChunk],
                                                  cc[3 * kChunk], cc[4 * kChunk], cc[5 * kChunk]};
                             F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
-                            g.h = __fmul_rn(g.h, gscale);
-                            g.l = __fmul_rn(g.l, gscale);
+                            if (KIND == KL_K_POLY_TEST) {   // the other kernels have gscale = 1
+                                g.h = __fmul_rn(g.h, gscale);
+                                g.l = __fmul_rn(g.l, gscale);
+                            }
                             slices6(g, o[h]);
                         } else {
                             const float x1 = cv[0][e + h], y1 = cv[1][e + h], z1 = cv[2][e + h];
                             const float g = kernel32<KIND>(rc[0] - x1, rc[1] - y1, rc[2] - z1, rc[0], rc[1], rc[2],
                                                            x1, y1, z1, cp.poly_m);
-                            slices3(__fmul_rn(g, gscale), o[h]);
+                            slices3(KIND == KL_K_POLY_TEST ? __fmul_rn(g, gscale) : g, o[h]);
                         }
                     }
 #pragma unroll

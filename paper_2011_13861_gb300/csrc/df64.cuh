@@ -106,6 +106,17 @@ struct ExpTable {
     float h[64], l[64];
 };
 
+// bit pattern of a float
+KL_HD int float_bits(float x) {
+#if defined(__CUDA_ARCH__)
+    return __float_as_int(x);
+#else
+    int b;
+    __builtin_memcpy(&b, &x, 4);
+    return b;
+#endif
+}
+
 // e^(-x) for a double-float x >= 0, Tang's method: n = round(64 x / ln2), j = n mod 64,
 // m = n div 64, r = x - n ln2/64 (|r| <= ln2/128) in double-float, e^(-x) = 2^-m 2^(-j/64) e^(-r),
 // e^(-r) - 1 by its Taylor polynomial (degree 5).  Arguments above 44 are clamped (the
@@ -116,12 +127,15 @@ KL_HD F2 exp_neg(F2 x, const float* tab_h, const float* tab_l) {
     const float c2 = 4.9915911404241342e-07f;         // next 24 bits
     const float c3 = 2.5728046402313451e-14f;         // remainder (|ln2/64 - c1 - c2 - c3| < 2e-22)
     const float inv_step = 92.332482616893656f;       // 64 / ln2
+    const float shifter = 12582912.f;                 // 1.5 * 2^23: x + shifter keeps round(x) in its low bits
     if (x.h > 44.f) x = F2{44.f, 0.f};
-    float nf = rintf(mul(x.h, inv_step));
-    int n = int(nf);
-    // r = x - n*(c1 + c2 + c3) in double-float
-    float a = fma_(-nf, c1, x.h);                     // exact (Sterbenz)
-    F2 t = two_sum(a, x.l);                           // x.l joins the head exactly
+    const float tn = fma_(x.h, inv_step, shifter);
+    const float nf = sub(tn, shifter);
+    const int n = float_bits(tn) - 0x4B400000;        // 0 <= n <= 4063
+    // r = x - n*(c1 + c2 + c3) in double-float.  a is exact (Sterbenz) and, unless zero, a
+    // multiple of ulp(x.h) (n*c1 lies on a grid of 2^-18), so |a| >= |x.l| and Fast2Sum is exact.
+    float a = fma_(-nf, c1, x.h);
+    F2 t = fast_two_sum(a, x.l);
     F2 q = two_prod(nf, c2);
     F2 b = two_sum(t.h, -q.h);
     float bl = add(add(b.l, t.l), -add(q.l, mul(nf, c3)));
@@ -132,7 +146,7 @@ KL_HD F2 exp_neg(F2 x, const float* tab_h, const float* tab_l) {
     float f = fma_(c, 1.0f / 120.0f, 1.0f / 24.0f);
     f = fma_(c, f, 1.0f / 6.0f);
     float u = mul(mul(c2p.h, c), f);                  // s^3/6 + ... (float accuracy suffices)
-    F2 h = two_sum(c, mul(0.5f, c2p.h));
+    F2 h = fast_two_sum(c, mul(0.5f, c2p.h));          // |c| <= ln2/128, so |c| >= c^2/2
     float lo = add(add(h.l, fma_(c, sl, sl)), fma_(0.5f, c2p.l, u));
     F2 P = fast_two_sum(h.h, lo);                     // e^s - 1
     // 2^(-j/64) * (1 + P)
@@ -145,25 +159,39 @@ KL_HD F2 exp_neg(F2 x, const float* tab_h, const float* tab_l) {
     R = fast_two_sum(R.h, R.l);
     // 2^-m, m = n >> 6 in [0, 63]
     const int m = n >> 6;
+    const int sbits = (127 - m) << 23;
 #if defined(__CUDA_ARCH__)
-    const float scale = __int_as_float((127 - m) << 23);
+    const float scale = __int_as_float(sbits);
 #else
     float scale;
-    {
-        unsigned bits = unsigned(127 - m) << 23;
-        __builtin_memcpy(&scale, &bits, 4);
-    }
+    __builtin_memcpy(&scale, &sbits, 4);
 #endif
     return F2{mul(R.h, scale), mul(R.l, scale)};
+}
+
+// |a|^2 + |b|^2 + |c|^2 of three normalised double-floats: exact head squares, their sum by
+// Fast2Sum on ordered (non-negative) operands, and one tail of the product errors, the cross
+// terms 2 h l and the two sums' errors (the l^2 terms are below 2^-48 of the result).
+KL_HD F2 sum_sq3(F2 a, F2 b, F2 c) {
+    const F2 pa = two_prod(a.h, a.h), pb = two_prod(b.h, b.h), pc = two_prod(c.h, c.h);
+    const float ea = fma_(add(a.h, a.h), a.l, pa.l);
+    const float eb = fma_(add(b.h, b.h), b.l, pb.l);
+    const float ec = fma_(add(c.h, c.h), c.l, pc.l);
+    const F2 s1 = fast_two_sum(fmaxf(pa.h, pb.h), fminf(pa.h, pb.h));
+    const F2 s2 = fast_two_sum(fmaxf(s1.h, pc.h), fminf(s1.h, pc.h));
+    const float t = add(add(s1.l, s2.l), add(add(ea, eb), ec));
+    return fast_two_sum(s2.h, t);
 }
 
 #if defined(__CUDACC__)
 // ---- kernel values Gamma(x_k, x_l) in double-float (device only) ----
 
+// a - b for two coordinates in the grid form of the double-float coordinate arrays: each
+// head is a multiple of one power of two q with |head| <= 2^23 q, and each tail has |tail| <= q/2.
+// The heads' difference (at most 2^24 q) is then exact, and unless it is zero it is at least q
+// >= |al - bl|, so one Fast2Sum normalises the result.
 __device__ __forceinline__ F2 diff(float ah, float al, float bh, float bl) {
-    F2 s = two_sum(ah, -bh);
-    float e = add(s.l, sub(al, bl));
-    return fast_two_sum(s.h, e);
+    return fast_two_sum(sub(ah, bh), sub(al, bl));
 }
 
 template <int KIND>
@@ -173,7 +201,8 @@ __device__ __forceinline__ F2 kernel_df(const float* r, const float* c, int pm, 
     if (KIND == KL_K_POLY_TEST) {
         F2 f{1.f, 0.f};
         for (int k = 0; k < 3; ++k) {
-            F2 p = mul(F2{r[k], r[3 + k]}, F2{c[k], c[3 + k]});
+            // grid-form coordinates are not normalised: renormalise before multiplying
+            F2 p = mul(two_sum(r[k], r[3 + k]), two_sum(c[k], c[3 + k]));
             f = mul(f, add(p, F2{1.f, 0.f}));
         }
         F2 g{1.f, 0.f};
@@ -187,7 +216,7 @@ __device__ __forceinline__ F2 kernel_df(const float* r, const float* c, int pm, 
         F2 s = add(add(abs(dx), abs(dy)), abs(dz));
         return exp_neg(s, th, tl);
     }
-    F2 s = add(add(sqr(dx), sqr(dy)), sqr(dz));
+    F2 s = sum_sq3(dx, dy, dz);
     if (KIND == KL_K_GAUSS) return exp_neg(s, th, tl);
     float seed;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(seed) : "f"(fmaxf(s.h, 1e-30f)));

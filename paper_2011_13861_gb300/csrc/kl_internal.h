@@ -79,7 +79,8 @@ struct CovParams {
     const double* P64;     // 3 x ldp, coordinates (pre-scaled for EXP/GAUSS/EXP_SEPARABLE)
     const float* P32;      // 3 x ldp, float coordinates pre-scaled for base-2 exponentials
     const double* tab;     // 1024-entry table 2^(j/1024)
-    const float* Pdf;      // 6 x ldp: x, y, z heads then x, y, z tails (double-float coordinates)
+    const float* Pdf;      // 6 x ldp: x, y, z heads then tails (double-float coordinates in grid
+                           // form: heads on one power-of-two grid q, |tail| <= q/2)
     const float* tabdf;    // 2^(-j/64), j = 0..63: 64 heads then 64 tails
     float gscale = 1.f;    // power of two with gscale * |Gamma| <= 1 (tensor-core float64-class path)
 };
