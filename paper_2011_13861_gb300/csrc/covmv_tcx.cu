@@ -323,7 +323,7 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
 #pragma unroll
             for (int g8 = 0; g8 < kVpt / 8; ++g8) {
                 // the 8 columns qd*kVpt + g8*8 .. +7; the float32 class reads their coordinates as
-                // float4 pairs, the float64 class value by value (fewer live registers)
+                // float4 pairs, the float64 class as float2 pairs per two columns (fewer live registers)
                 const int c0 = qd * kVpt + g8 * 8;
                 float cv[3][8];
                 if constexpr (CLS == 32) {
@@ -339,12 +339,18 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
 #pragma unroll
                 for (int e = 0; e < 8; e += 2) {
                     float o[2][kSlices];
+                    float2 cp2[CLS == 64 ? 6 : 1];
+                    if constexpr (CLS == 64) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k)
+                            cp2[k] = *reinterpret_cast<const float2*>(img_c + k * kChunk + c0 + e);
+                    }
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if constexpr (CLS == 64) {
-                            const float* cc = img_c + c0 + e + h;
-                            const float c6[6] = {cc[0],          cc[kChunk],     cc[2 * kChunk],
-                                                 cc[3 * kChunk], cc[4 * kChunk], cc[5 * kChunk]};
+                            float c6[6];
+#pragma unroll
+                            for (int k = 0; k < 6; ++k) c6[k] = h ? cp2[k].y : cp2[k].x;
                             F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
                             if (KIND == KL_K_POLY_TEST) {   // the other kernels have gscale = 1
                                 g.h = __fmul_rn(g.h, gscale);
