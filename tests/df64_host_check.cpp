@@ -1,0 +1,68 @@
+// Host build of the double-float header's arithmetic (exp, sum of squares, grid-form point
+// differences) checked against long double.  Prints one JSON object of maximum errors.
+#include <cmath>
+#include <cstdio>
+#include <random>
+
+#include "df64.cuh"
+
+using namespace kl::df;
+
+static long double val(F2 a) { return (long double)a.h + (long double)a.l; }
+static F2 split(long double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (long double)h)};
+}
+
+int main() {
+    float th[64], tl[64];
+    for (int j = 0; j < 64; ++j) {
+        const long double t = exp2l(-(long double)j / 64);
+        th[j] = (float)t;
+        tl[j] = (float)(t - (long double)th[j]);
+    }
+    std::mt19937_64 rng(2011);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+
+    // e^-x for x in [0, 44]: uniform, small, and log-spread arguments
+    double exp_rel = 0, exp_abs = 0;
+    int exp_unnormalised = 0;
+    for (int i = 0; i < 300000; ++i) {
+        const long double x = (i % 3 == 0) ? U(rng) * 44 : (i % 3 == 1 ? U(rng) * 0.02 : std::pow(10.0, -8 + 9.6 * U(rng)));
+        const F2 xf = split(x);
+        const long double ref = expl(-val(xf));
+        const F2 r = exp_neg(xf, th, tl);
+        exp_rel = std::fmax(exp_rel, (double)fabsl((val(r) - ref) / ref));
+        exp_abs = std::fmax(exp_abs, (double)fabsl(val(r) - ref));
+        if (r.h != 0.f && std::fabs(r.l) > std::ldexp(1.0f, std::ilogb(r.h) - 24)) ++exp_unnormalised;
+    }
+
+    // grid-form coordinates in [-8, 8): heads on q = 2^-20, tails the remainders
+    const double q = std::ldexp(1.0, 3 - 23);
+    int inexact_heads = 0;
+    double diff_abs = 0, sq_rel = 0;
+    for (int i = 0; i < 300000; ++i) {
+        const double scale = (i % 3 == 0) ? 1e-7 : (i % 3 == 1 ? 1e-3 : 1.0);
+        F2 d[3];
+        long double s = 0;
+        for (int k = 0; k < 3; ++k) {
+            const double a = U(rng) * 16 - 8;
+            double b = a + (U(rng) * 2 - 1) * scale;
+            if (std::fabs(b) >= 8) b = a;
+            const double ah = std::rint(a / q) * q, bh = std::rint(b / q) * q;
+            const float al = (float)(a - ah), bl = (float)(b - bh);
+            const float hd = sub((float)ah, (float)bh);
+            if ((double)hd != ah - bh) ++inexact_heads;
+            d[k] = fast_two_sum(hd, sub(al, bl));   // the device difference of two grid-form points
+            const long double exact = ((long double)ah + al) - ((long double)bh + bl);
+            diff_abs = std::fmax(diff_abs, (double)fabsl(val(d[k]) - exact));
+            s += val(d[k]) * val(d[k]);
+        }
+        const F2 ss = sum_sq3(d[0], d[1], d[2]);
+        if (s > 0) sq_rel = std::fmax(sq_rel, (double)fabsl((val(ss) - s) / s));
+    }
+    std::printf("{\"exp_rel\": %.6e, \"exp_abs\": %.6e, \"exp_unnormalised\": %d, \"inexact_heads\": %d, "
+                "\"diff_abs\": %.6e, \"sum_sq_rel\": %.6e}\n",
+                exp_rel, exp_abs, exp_unnormalised, inexact_heads, diff_abs, sq_rel);
+    return 0;
+}
