@@ -340,14 +340,34 @@ kl_status kl_eigs(kl_handle h, int k, double tol, const kl_eig_opts* opts, doubl
 kl_status kl_to_bspline(kl_handle h, const double* vprime_dev, double* v_dev, int nvec, int64_t ld,
                         void* stream);
 
-/* Number of CUDA kernels this library has launched since it was loaded (all handles, all
- * threads); for tracing and launch accounting. */
+/* Host only (no device use): the univariate set-up of one parametric direction exactly as
+ * kl_create builds it, for inspection and for testing without a GPU.
+ *   deg, elems               trial space (Sec. 2.3: open uniform knots, C^{deg-1})
+ *   interp_deg, interp_elems interpolation space (Sec. 4.2); 0 = same as the trial space
+ *   n_interfaces, interfaces patch interfaces in this direction, as in kl_space (Sec. 3.6)
+ * On KL_OK, *n and *nt hold the numbers of trial and interpolation functions, and each
+ * output that is not NULL is filled (caller-owned host arrays):
+ *   greville  nt doubles: Greville abscissae of the interpolation space (Sec. 4.2)
+ *   side      nt ints: -1 where the abscissa is evaluated as a left limit (C^{-1} knot), else 0
+ *   L         n*n doubles, row-major: the lower Cholesky factor of Z_k = L_k L_k^T (Sec. 4.1)
+ *   C         nt*n doubles, row-major: C_k = B~_k^{-T} M_k L_k^{-T} (Sec. 4.2-4.4), the folded
+ *             factor the forward contraction applies
+ * Call once with NULL outputs to learn n and nt.  Errors: KL_ERR_INVALID_ARG for the argument
+ * rules of kl_create, a null n/nt, or a negative interface count (or a null array with a
+ * positive one); KL_ERR_NUMERIC for an indefinite mass matrix or a singular collocation
+ * matrix.  Outputs are not written on error. */
+kl_status kl_direction_factors(int deg, int elems, int interp_deg, int interp_elems, int n_interfaces,
+                               const double* interfaces, int* n, int* nt, double* greville, int* side,
+                               double* L, double* C);
+
 /* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an
  * mbarrier that nothing completes, with the bounded-wait helper of the tensor-core kernels,
  * gives up after `seconds` (0 < seconds <= 2) and reports it.  Returns KL_ERR_TIMEOUT, the
  * status a stalled tensor-core pipeline returns; the context stays usable.  Synchronous. */
 kl_status kl_wait_selftest(double seconds, void* stream);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all handles, all
+ * threads); for tracing and launch accounting. */
 uint64_t kl_kernel_launches(void);
 
 const char* kl_last_error(void);

@@ -92,6 +92,9 @@ SIGNATURES = {
                                     ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _vp, _vp]),
     "kl_mlp_destroy": (None, [_vp]),
     "kl_prolong": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "kl_direction_factors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            _vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _vp,
+                                            _vp, _vp, _vp]),
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
@@ -476,6 +479,27 @@ def prolong(coarse, fine, v, stream=None):
     out = torch.empty((vb.shape[0], fine.N), dtype=torch.float64, device=vb.device)
     _check(load().kl_prolong(coarse._h, fine._h, _ptr(vb), _ptr(out), int(vb.shape[0]), _stream(stream)))
     return out if v.dim() > 1 else out.reshape(-1)
+
+
+def direction_factors(deg, elems, interp_deg=0, interp_elems=0, interfaces=()):
+    """kl_direction_factors (host only, no GPU): the set-up of one direction as kl_create builds
+    it -- Greville abscissae and sides of the interpolation space, the Cholesky factor L_k of
+    Z_k, and the folded factor C_k = B~_k^-T M_k L_k^-T -- as NumPy arrays."""
+    import numpy as np
+    lib = load()
+    itf = np.ascontiguousarray(np.asarray(interfaces, dtype=np.float64).reshape(-1))
+    itf_p = ctypes.c_void_p(itf.ctypes.data) if itf.size else None
+    n, nt = ctypes.c_int(0), ctypes.c_int(0)
+    args = (int(deg), int(elems), int(interp_deg), int(interp_elems), int(itf.size), itf_p)
+    _check(lib.kl_direction_factors(*args, ctypes.byref(n), ctypes.byref(nt), None, None, None, None))
+    xi = np.zeros(nt.value)
+    side = np.zeros(nt.value, dtype=np.int32)
+    L = np.zeros((n.value, n.value))
+    C = np.zeros((nt.value, n.value))
+    _check(lib.kl_direction_factors(*args, ctypes.byref(n), ctypes.byref(nt),
+                                    ctypes.c_void_p(xi.ctypes.data), ctypes.c_void_p(side.ctypes.data),
+                                    ctypes.c_void_p(L.ctypes.data), ctypes.c_void_p(C.ctypes.data)))
+    return {"n": n.value, "nt": nt.value, "greville": xi, "side": side, "L": L, "C": C}
 
 
 def wait_selftest(seconds=0.05, stream=None):

@@ -301,6 +301,34 @@ kl_status build_direction(int p, int ne, int pt, int net, const std::vector<doub
 }
 
 
+}  // namespace kl
+
+// host-only view of one direction's set-up (the factors kl_create uploads)
+extern "C" kl_status kl_direction_factors(int deg, int elems, int interp_deg, int interp_elems, int n_interfaces,
+                                          const double* interfaces, int* n, int* nt, double* greville,
+                                          int* side, double* L, double* C) {
+    using namespace kl;
+    if (!n || !nt) return fail(KL_ERR_INVALID_ARG, "kl_direction_factors: null n or nt");
+    if (n_interfaces < 0 || (n_interfaces > 0 && !interfaces))
+        return fail(KL_ERR_INVALID_ARG, "patch interfaces: negative count or null array");
+    const int pt = interp_deg > 0 ? interp_deg : deg;
+    const int net = interp_elems > 0 ? interp_elems : elems;
+    std::vector<double> itf;
+    if (n_interfaces > 0) itf.assign(interfaces, interfaces + n_interfaces);
+    Direction d;
+    const kl_status st = build_direction(deg, elems, pt, net, itf, &d);
+    if (st != KL_OK) return st;
+    *n = d.n;
+    *nt = d.nt;
+    if (greville) std::copy(d.xi.begin(), d.xi.end(), greville);
+    if (side) std::copy(d.side.begin(), d.side.end(), side);
+    if (L) std::copy(d.L.begin(), d.L.end(), L);
+    if (C) std::copy(d.C.begin(), d.C.end(), C);
+    return KL_OK;
+}
+
+namespace kl {
+
 // F(xh) and det DF(xh) of a tensor-product NURBS map (Sec. 2.4): F = P / W with
 // P = sum_I N_I(xh) w_I P_I and W = sum_I N_I(xh) w_I; column j of DF is
 // (dP/dxh_j W - P dW/dxh_j) / W^2.  Directions beyond dim have one control point.
