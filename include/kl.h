@@ -360,6 +360,17 @@ kl_status kl_direction_factors(int deg, int elems, int interp_deg, int interp_el
                                const double* interfaces, int* n, int* nt, double* greville, int* side,
                                double* L, double* C);
 
+/* Host only (no device use): the mapped Greville grid and J exactly as kl_create builds them
+ * (Sec. 2.4 map, Sec. 4.2 Greville abscissae, J = sqrt(det DF) as in Sec. 4.4.1; one-sided at
+ * patch interfaces, Sec. 3.6), for inspection and for testing without a GPU.  geom and space
+ * as for kl_create.  On KL_OK *Ntilde holds the number of points and each output that is not
+ * NULL is filled (caller-owned host arrays): X Ntilde*3 doubles, point-major (x, y, z of point
+ * i at 3i; unused coordinates 0), points in the paper's vec order (direction 1 fastest);
+ * J Ntilde doubles.  Call once with NULL outputs to learn Ntilde.  Errors: those of kl_create
+ * for the geometry and the space (KL_ERR_INVALID_ARG, KL_ERR_NUMERIC); outputs are not
+ * written on error. */
+kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* space, int64_t* Ntilde, double* X, double* J);
+
 /* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an
  * mbarrier that nothing completes, with the bounded-wait helper of the tensor-core kernels,
  * gives up after `seconds` (0 < seconds <= 2) and reports it.  Returns KL_ERR_TIMEOUT, the

@@ -95,6 +95,8 @@ SIGNATURES = {
     "kl_direction_factors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             _vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _vp,
                                             _vp, _vp, _vp]),
+    "kl_mapped_points": (ctypes.c_int, [ctypes.POINTER(KLGeometry), ctypes.POINTER(KLSpace),
+                                        ctypes.POINTER(_c_int64), _vp, _vp]),
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
@@ -179,6 +181,44 @@ def _per_dir(v, dim, default=0):
     return v[:3]
 
 
+def _geometry_and_space(dim, p, ne, pt=None, net=None, lo=None, hi=None, nurbs=None, interfaces=None):
+    """kl_geometry and kl_space structs for the arguments of KLProblem, and the host arrays
+    they point into (keep them alive while the structs are used)."""
+    g = KLGeometry(dim, KL_GEOM_BOX, (ctypes.c_double * 3)(*_per_dir(lo, dim, 0.0)),
+                   (ctypes.c_double * 3)(*_per_dir(hi, dim, 1.0)))
+    keep = []
+    if nurbs is not None:
+        import numpy as np
+        # nurbs: dict(deg=[...], knots=[...], ctrl=array (n_d, ..., n_1, dim), weights=array (n_d, ..., n_1))
+        g.kind = KL_GEOM_NURBS
+        deg = [int(x) for x in nurbs["deg"]]
+        knots = [np.ascontiguousarray(t, dtype=np.float64) for t in nurbs["knots"]]
+        ctrl = np.asarray(nurbs["ctrl"], dtype=np.float64)
+        wts = np.asarray(nurbs["weights"], dtype=np.float64)
+        rec = np.zeros(wts.shape + (4,))
+        rec[..., :ctrl.shape[-1]] = ctrl
+        rec[..., 3] = wts
+        rec = np.ascontiguousarray(rec.reshape(-1, 4))
+        keep += knots + [rec]
+        for k in range(dim):
+            g.deg[k] = deg[k]
+            g.nctrl[k] = len(knots[k]) - deg[k] - 1
+            g.knots[k] = knots[k].ctypes.data
+        g.ctrl = rec.ctypes.data
+    sp = KLSpace((ctypes.c_int * 3)(*_per_dir(p, dim)), (ctypes.c_int * 3)(*_per_dir(ne, dim)),
+                 (ctypes.c_int * 3)(*_per_dir(pt, dim)), (ctypes.c_int * 3)(*_per_dir(net, dim)))
+    if interfaces is not None:
+        # interfaces: per direction a sequence of patch-interface parameters (Sec. 3.6)
+        for k in range(dim):
+            vals = [float(x) for x in interfaces[k]] if k < len(interfaces) else []
+            if vals:
+                arr = (ctypes.c_double * len(vals))(*vals)
+                keep.append(arr)
+                sp.n_interfaces[k] = len(vals)
+                sp.interfaces[k] = ctypes.cast(arr, ctypes.c_void_p).value
+    return g, sp, keep
+
+
 class KLProblem:
     """One discretised KL problem on the GPU (a kl_handle).
 
@@ -192,38 +232,7 @@ class KLProblem:
     def __init__(self, dim, p, ne, kernel="exp", sigma=1.0, L=1.0, pt=None, net=None, lo=None, hi=None,
                  nurbs=None, interfaces=None):
         lib = load()
-        g = KLGeometry(dim, KL_GEOM_BOX, (ctypes.c_double * 3)(*_per_dir(lo, dim, 0.0)),
-                       (ctypes.c_double * 3)(*_per_dir(hi, dim, 1.0)))
-        keep = []
-        if nurbs is not None:
-            import numpy as np
-            # nurbs: dict(deg=[...], knots=[...], ctrl=array (n_d, ..., n_1, dim), weights=array (n_d, ..., n_1))
-            g.kind = KL_GEOM_NURBS
-            deg = [int(x) for x in nurbs["deg"]]
-            knots = [np.ascontiguousarray(t, dtype=np.float64) for t in nurbs["knots"]]
-            ctrl = np.asarray(nurbs["ctrl"], dtype=np.float64)
-            wts = np.asarray(nurbs["weights"], dtype=np.float64)
-            rec = np.zeros(wts.shape + (4,))
-            rec[..., :ctrl.shape[-1]] = ctrl
-            rec[..., 3] = wts
-            rec = np.ascontiguousarray(rec.reshape(-1, 4))
-            keep += knots + [rec]
-            for k in range(dim):
-                g.deg[k] = deg[k]
-                g.nctrl[k] = len(knots[k]) - deg[k] - 1
-                g.knots[k] = knots[k].ctypes.data
-            g.ctrl = rec.ctypes.data
-        sp = KLSpace((ctypes.c_int * 3)(*_per_dir(p, dim)), (ctypes.c_int * 3)(*_per_dir(ne, dim)),
-                     (ctypes.c_int * 3)(*_per_dir(pt, dim)), (ctypes.c_int * 3)(*_per_dir(net, dim)))
-        if interfaces is not None:
-            # interfaces: per direction a sequence of patch-interface parameters (Sec. 3.6)
-            for k in range(dim):
-                vals = [float(x) for x in interfaces[k]] if k < len(interfaces) else []
-                if vals:
-                    arr = (ctypes.c_double * len(vals))(*vals)
-                    keep.append(arr)
-                    sp.n_interfaces[k] = len(vals)
-                    sp.interfaces[k] = ctypes.cast(arr, ctypes.c_void_p).value
+        g, sp, keep = _geometry_and_space(dim, p, ne, pt, net, lo, hi, nurbs, interfaces)
         kk = KLKernel(KERNEL_KINDS[kernel] if isinstance(kernel, str) else int(kernel), float(sigma), float(L))
         h = ctypes.c_void_p()
         _check(lib.kl_create(ctypes.byref(g), ctypes.byref(sp), ctypes.byref(kk), ctypes.byref(h)))
@@ -500,6 +509,22 @@ def direction_factors(deg, elems, interp_deg=0, interp_elems=0, interfaces=()):
                                     ctypes.c_void_p(xi.ctypes.data), ctypes.c_void_p(side.ctypes.data),
                                     ctypes.c_void_p(L.ctypes.data), ctypes.c_void_p(C.ctypes.data)))
     return {"n": n.value, "nt": nt.value, "greville": xi, "side": side, "L": L, "C": C}
+
+
+def mapped_points(dim, p, ne, pt=None, net=None, lo=None, hi=None, nurbs=None, interfaces=None):
+    """kl_mapped_points (host only, no GPU): the mapped Greville grid X (Ntilde x 3, direction 1
+    fastest) and J = sqrt(det DF) that KLProblem(dim, p, ne, ...) would upload."""
+    import numpy as np
+    lib = load()
+    g, sp, keep = _geometry_and_space(dim, p, ne, pt, net, lo, hi, nurbs, interfaces)
+    Nt = ctypes.c_int64(0)
+    _check(lib.kl_mapped_points(ctypes.byref(g), ctypes.byref(sp), ctypes.byref(Nt), None, None))
+    X = np.zeros((Nt.value, 3))
+    J = np.zeros(Nt.value)
+    _check(lib.kl_mapped_points(ctypes.byref(g), ctypes.byref(sp), ctypes.byref(Nt),
+                                ctypes.c_void_p(X.ctypes.data), ctypes.c_void_p(J.ctypes.data)))
+    del keep
+    return X, J
 
 
 def wait_selftest(seconds=0.05, stream=None):

@@ -410,38 +410,7 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     if (kernel->kind == KL_K_POLY_TEST && (kernel->L < 1.0 || kernel->L > 8.0))
         return fail(KL_ERR_INVALID_ARG, "polynomial test kernel needs 1 <= m = L <= 8");
     NurbsMap nm;
-    if (geom->kind == KL_GEOM_BOX) {
-        for (int k = 0; k < d; ++k)
-            if (!(geom->hi[k] > geom->lo[k]) || !isfinite(geom->lo[k]) || !isfinite(geom->hi[k]))
-                return fail(KL_ERR_INVALID_ARG, "box extent must be positive");
-    } else {
-        // NURBS map: open knot vectors on [0, 1], positive weights (host data, copied here)
-        nm.dim = d;
-        size_t nrec = 1;
-        for (int k = 0; k < d; ++k) {
-            const int p = geom->deg[k], n = geom->nctrl[k];
-            if (p < 1 || p > 15 || n < p + 1 || n > 4096 || !geom->knots[k])
-                return fail(KL_ERR_INVALID_ARG, "NURBS map: need 1 <= deg <= 15, nctrl >= deg + 1, knots");
-            nm.deg[k] = p;
-            nm.n[k] = n;
-            nm.knots[k].assign(geom->knots[k], geom->knots[k] + n + p + 1);
-            const std::vector<double>& t = nm.knots[k];
-            for (size_t i = 0; i + 1 < t.size(); ++i)
-                if (!(t[i] <= t[i + 1]) || !isfinite(t[i]))
-                    return fail(KL_ERR_INVALID_ARG, "NURBS map: knots must be finite and non-decreasing");
-            for (int i = 0; i <= p; ++i)
-                if (t[size_t(i)] != 0.0 || t[t.size() - 1 - size_t(i)] != 1.0)
-                    return fail(KL_ERR_INVALID_ARG, "NURBS map: knot vectors must be open on [0, 1]");
-            nrec *= size_t(n);
-        }
-        if (!geom->ctrl) return fail(KL_ERR_INVALID_ARG, "NURBS map: null control points");
-        nm.ctrl.assign(geom->ctrl, geom->ctrl + 4 * nrec);
-        for (size_t i = 0; i < nrec; ++i) {
-            for (int r = 0; r < 4; ++r)
-                if (!isfinite(nm.ctrl[4 * i + r])) return fail(KL_ERR_INVALID_ARG, "NURBS map: non-finite control data");
-            if (!(nm.ctrl[4 * i + 3] > 0.0)) return fail(KL_ERR_INVALID_ARG, "NURBS map: weights must be positive");
-        }
-    }
+    KL_TRY(parse_geometry(geom, &nm));
 
     kl_handle h = new (std::nothrow) kl_handle_s();
     if (!h) return fail(KL_ERR_OOM, "host allocation failed");
@@ -449,22 +418,14 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
     h->kernel = *kernel;
     h->N = 1;
     h->Nt = 1;
-    double det = 1.0;
-    for (int k = 0; k < d; ++k) {
-        const int p = space->deg[k], ne = space->elems[k];
-        const int pt = space->interp_deg[k] > 0 ? space->interp_deg[k] : p;
-        const int net = space->interp_elems[k] > 0 ? space->interp_elems[k] : ne;
-        std::vector<double> itf;
-        if (space->n_interfaces[k] < 0 || (space->n_interfaces[k] > 0 && !space->interfaces[k])) {
-            delete h;
-            return fail(KL_ERR_INVALID_ARG, "patch interfaces: negative count or null array");
-        }
-        if (space->n_interfaces[k] > 0) itf.assign(space->interfaces[k], space->interfaces[k] + space->n_interfaces[k]);
-        kl_status st = build_direction(p, ne, pt, net, itf, &h->dir[k]);
+    {
+        const kl_status st = build_space(d, space, h->dir);
         if (st != KL_OK) {
             delete h;
             return st;
         }
+    }
+    for (int k = 0; k < d; ++k) {
         h->n[k] = h->dir[k].n;
         h->nt[k] = h->dir[k].nt;
         h->N *= h->n[k];
@@ -472,7 +433,6 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         if (geom->kind == KL_GEOM_BOX) {
             h->lo[k] = geom->lo[k];
             h->hi[k] = geom->hi[k];
-            det *= geom->hi[k] - geom->lo[k];
         }
     }
     if (h->Nt > 2147483647LL || h->N > 2147483647LL) {
@@ -490,34 +450,15 @@ kl_status kl_create(const kl_geometry* geom, const kl_space* space, const kl_ker
         if (f > h->ldw) h->ldw = f;
         if (b > h->ldw) h->ldw = b;
     }
-
-    // mapped Greville points X = F(xh) in vec order (direction 1 fastest) and J = sqrt(det DF)
-    const int64_t Nt = h->Nt;
-    h->X_host.assign(size_t(Nt) * 3, 0.0);
-    h->J_host.assign(size_t(Nt), sqrt(det));
-    for (int64_t idx = 0; idx < Nt; ++idx) {
-        int64_t r = idx;
-        double xh[3] = {0.0, 0.0, 0.0};
-        int side[3] = {0, 0, 0};
-        for (int k = 0; k < d; ++k) {
-            const int64_t ik = r % h->nt[k];
-            r /= h->nt[k];
-            xh[k] = h->dir[k].xi[size_t(ik)];
-            side[k] = h->dir[k].side[size_t(ik)];
-        }
-        if (geom->kind == KL_GEOM_BOX) {
-            for (int k = 0; k < d; ++k) h->X_host[size_t(idx) * 3 + k] = h->lo[k] + (h->hi[k] - h->lo[k]) * xh[k];
-        } else {
-            double X[3], detDF;
-            nurbs_map_point(nm, xh, side, X, &detDF);
-            if (!(detDF > 0.0) || !isfinite(detDF)) {
-                delete h;
-                return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");
-            }
-            for (int k = 0; k < 3; ++k) h->X_host[size_t(idx) * 3 + k] = X[k];
-            h->J_host[size_t(idx)] = sqrt(detDF);
+    {
+        // mapped Greville points X = F(xh) in vec order (direction 1 fastest) and J = sqrt(det DF)
+        const kl_status st = map_greville_points(geom, nm, h->dir, &h->X_host, &h->J_host);
+        if (st != KL_OK) {
+            delete h;
+            return st;
         }
     }
+    const int64_t Nt = h->Nt;
     // device copies: coordinates scaled per kernel kind
     const int kind = kernel->kind;
     const double L = kernel->L;

@@ -62,6 +62,14 @@ struct NurbsMap {
 // F(xh) and det DF(xh); side[k] < 0 takes the left limit in direction k (at a C^0 knot of the map)
 void nurbs_map_point(const NurbsMap& m, const double* xh, const int* side, double* X, double* detDF);
 
+// host set-up shared by kl_create and the host-only inspection entry points:
+// validate a geometry (for KL_GEOM_NURBS copy its map into *nm), build directions 0..dim-1 of a
+// space, and map the Greville grid (X: Ntilde x 3 row-major, direction 1 fastest; J = sqrt(det DF))
+kl_status parse_geometry(const kl_geometry* geom, NurbsMap* nm);
+kl_status build_space(int dim, const kl_space* space, Direction* dir);
+kl_status map_greville_points(const kl_geometry* geom, const NurbsMap& nm, const Direction* dir,
+                              std::vector<double>* X, std::vector<double>* J);
+
 // ----------------------------------------------------------------------------------------
 // device kernels (launchers)
 // ----------------------------------------------------------------------------------------

@@ -301,6 +301,96 @@ kl_status build_direction(int p, int ne, int pt, int net, const std::vector<doub
 }
 
 
+kl_status parse_geometry(const kl_geometry* geom, NurbsMap* nm) {
+    const int d = geom->dim;
+    if (d < 1 || d > 3) return fail(KL_ERR_INVALID_ARG, "dim must be 1, 2 or 3");
+    if (geom->kind != KL_GEOM_BOX && geom->kind != KL_GEOM_NURBS) return fail(KL_ERR_INVALID_ARG, "unsupported geometry kind");
+    if (geom->kind == KL_GEOM_BOX) {
+        for (int k = 0; k < d; ++k)
+            if (!(geom->hi[k] > geom->lo[k]) || !std::isfinite(geom->lo[k]) || !std::isfinite(geom->hi[k]))
+                return fail(KL_ERR_INVALID_ARG, "box extent must be positive");
+        return KL_OK;
+    }
+    // NURBS map: open knot vectors on [0, 1], positive weights (host data, copied here)
+    nm->dim = d;
+    size_t nrec = 1;
+    for (int k = 0; k < d; ++k) {
+        const int p = geom->deg[k], n = geom->nctrl[k];
+        if (p < 1 || p > 15 || n < p + 1 || n > 4096 || !geom->knots[k])
+            return fail(KL_ERR_INVALID_ARG, "NURBS map: need 1 <= deg <= 15, nctrl >= deg + 1, knots");
+        nm->deg[k] = p;
+        nm->n[k] = n;
+        nm->knots[k].assign(geom->knots[k], geom->knots[k] + n + p + 1);
+        const std::vector<double>& t = nm->knots[k];
+        for (size_t i = 0; i + 1 < t.size(); ++i)
+            if (!(t[i] <= t[i + 1]) || !std::isfinite(t[i]))
+                return fail(KL_ERR_INVALID_ARG, "NURBS map: knots must be finite and non-decreasing");
+        for (int i = 0; i <= p; ++i)
+            if (t[size_t(i)] != 0.0 || t[t.size() - 1 - size_t(i)] != 1.0)
+                return fail(KL_ERR_INVALID_ARG, "NURBS map: knot vectors must be open on [0, 1]");
+        nrec *= size_t(n);
+    }
+    if (!geom->ctrl) return fail(KL_ERR_INVALID_ARG, "NURBS map: null control points");
+    nm->ctrl.assign(geom->ctrl, geom->ctrl + 4 * nrec);
+    for (size_t i = 0; i < nrec; ++i) {
+        for (int r = 0; r < 4; ++r)
+            if (!std::isfinite(nm->ctrl[4 * i + r])) return fail(KL_ERR_INVALID_ARG, "NURBS map: non-finite control data");
+        if (!(nm->ctrl[4 * i + 3] > 0.0)) return fail(KL_ERR_INVALID_ARG, "NURBS map: weights must be positive");
+    }
+    return KL_OK;
+}
+
+kl_status build_space(int dim, const kl_space* space, Direction* dir) {
+    for (int k = 0; k < dim; ++k) {
+        const int p = space->deg[k], ne = space->elems[k];
+        const int pt = space->interp_deg[k] > 0 ? space->interp_deg[k] : p;
+        const int net = space->interp_elems[k] > 0 ? space->interp_elems[k] : ne;
+        std::vector<double> itf;
+        if (space->n_interfaces[k] < 0 || (space->n_interfaces[k] > 0 && !space->interfaces[k]))
+            return fail(KL_ERR_INVALID_ARG, "patch interfaces: negative count or null array");
+        if (space->n_interfaces[k] > 0) itf.assign(space->interfaces[k], space->interfaces[k] + space->n_interfaces[k]);
+        KL_TRY(build_direction(p, ne, pt, net, itf, &dir[k]));
+    }
+    return KL_OK;
+}
+
+kl_status map_greville_points(const kl_geometry* geom, const NurbsMap& nm, const Direction* dir,
+                              std::vector<double>* X, std::vector<double>* J) {
+    const int d = geom->dim;
+    int64_t Nt = 1;
+    double det = 1.0;
+    for (int k = 0; k < d; ++k) {
+        Nt *= dir[k].nt;
+        if (geom->kind == KL_GEOM_BOX) det *= geom->hi[k] - geom->lo[k];
+    }
+    if (Nt > 2147483647LL) return fail(KL_ERR_INVALID_ARG, "problem too large (more than 2^31-1 points)");
+    // mapped Greville points X = F(xh) in vec order (direction 1 fastest) and J = sqrt(det DF)
+    X->assign(size_t(Nt) * 3, 0.0);
+    J->assign(size_t(Nt), std::sqrt(det));
+    for (int64_t idx = 0; idx < Nt; ++idx) {
+        int64_t r = idx;
+        double xh[3] = {0.0, 0.0, 0.0};
+        int side[3] = {0, 0, 0};
+        for (int k = 0; k < d; ++k) {
+            const int64_t ik = r % dir[k].nt;
+            r /= dir[k].nt;
+            xh[k] = dir[k].xi[size_t(ik)];
+            side[k] = dir[k].side[size_t(ik)];
+        }
+        if (geom->kind == KL_GEOM_BOX) {
+            for (int k = 0; k < d; ++k) (*X)[size_t(idx) * 3 + k] = geom->lo[k] + (geom->hi[k] - geom->lo[k]) * xh[k];
+        } else {
+            double Xp[3], detDF;
+            nurbs_map_point(nm, xh, side, Xp, &detDF);
+            if (!(detDF > 0.0) || !std::isfinite(detDF))
+                return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");
+            for (int k = 0; k < 3; ++k) (*X)[size_t(idx) * 3 + k] = Xp[k];
+            (*J)[size_t(idx)] = std::sqrt(detDF);
+        }
+    }
+    return KL_OK;
+}
+
 }  // namespace kl
 
 // host-only view of one direction's set-up (the factors kl_create uploads)
@@ -324,6 +414,23 @@ extern "C" kl_status kl_direction_factors(int deg, int elems, int interp_deg, in
     if (side) std::copy(d.side.begin(), d.side.end(), side);
     if (L) std::copy(d.L.begin(), d.L.end(), L);
     if (C) std::copy(d.C.begin(), d.C.end(), C);
+    return KL_OK;
+}
+
+// host-only view of the mapped Greville grid and J (the points kl_create uploads)
+extern "C" kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* space, int64_t* Ntilde, double* X,
+                                      double* J) {
+    using namespace kl;
+    if (!geom || !space || !Ntilde) return fail(KL_ERR_INVALID_ARG, "null argument to kl_mapped_points");
+    NurbsMap nm;
+    KL_TRY(parse_geometry(geom, &nm));
+    Direction dir[3];
+    KL_TRY(build_space(geom->dim, space, dir));
+    std::vector<double> Xv, Jv;
+    KL_TRY(map_greville_points(geom, nm, dir, &Xv, &Jv));
+    *Ntilde = int64_t(Jv.size());
+    if (X) std::copy(Xv.begin(), Xv.end(), X);
+    if (J) std::copy(Jv.begin(), Jv.end(), J);
     return KL_OK;
 }
 

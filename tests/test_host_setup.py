@@ -1,13 +1,15 @@
-"""The library's host set-up of one direction (kl_direction_factors: knots, Greville abscissae,
-Gauss quadrature, Cholesky factor, collocation, folded factor C_k) against the oracle's
-matrices, on the CPU.  kl_create uploads exactly these arrays, so this pins stage a0 without
-a GPU; the GPU tests then check the operator built from them."""
+"""The library's host set-up against the oracle, on the CPU: one direction's factors
+(kl_direction_factors: knots, Greville abscissae, Gauss quadrature, Cholesky factor,
+collocation, folded factor C_k) and the mapped Greville grid with J (kl_mapped_points: box and
+NURBS maps, one-sided evaluation at patch interfaces).  kl_create uploads exactly these arrays,
+built by the same host code, so this pins the set-up without a GPU; the GPU tests then check
+the operator built from them."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import ibq
-from paper_2011_13861_gb300 import _binding, build
+from oracle import ibq, nurbs
+from paper_2011_13861_gb300 import _binding, build, inputs
 
 
 @pytest.fixture(scope="module")
@@ -60,3 +62,62 @@ def test_direction_factors_reject_bad_arguments(lib, args, needle):
     with pytest.raises(_binding.KLError) as e:
         _binding.direction_factors(*args)
     assert e.value.status == 1 and needle in str(e.value)
+
+
+def oracle_points(dim, p, ne, pt=None, net=None, lo=None, hi=None, geom=None, interfaces=None):
+    prob = ibq.Problem(dim, p, ne, pt=pt, net=net, lo=lo, hi=hi, geom=geom, interfaces=interfaces)
+    X, J = prob.points_and_J()
+    out = np.zeros((X.shape[0], 3))
+    out[:, :X.shape[1]] = X
+    return out, J
+
+
+@pytest.mark.parametrize("dim,p,ne,pt,net,lo,hi", [
+    (1, 2, 9, None, None, [-1.0], [2.0]),
+    (2, [2, 3], [5, 4], None, None, [0.0, -0.5], [1.0, 0.25]),
+    (3, 2, [3, 4, 2], [3, 2, 2], [2, 4, 3], [0.0, 0.0, 0.0], [1.0, 2.0, 0.5]),
+])
+def test_mapped_points_box(lib, dim, p, ne, pt, net, lo, hi):
+    X, J = _binding.mapped_points(dim, p, ne, pt, net, lo, hi)
+    Xo, Jo = oracle_points(dim, p, ne, pt, net, lo, hi)
+    np.testing.assert_allclose(X, Xo, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(J, Jo, rtol=1e-15, atol=0)
+
+
+def as_oracle_map(net):
+    return nurbs.NURBSMap(net["deg"], net["knots"], net["ctrl"], net["weights"])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mapped_points_quarter_annulus(lib, dim):
+    net = inputs.quarter_annulus_net(1.0, 2.0, 1.0, dim)
+    p, ne = [2, 3, 2][:dim], [6, 4, 3][:dim]
+    X, J = _binding.mapped_points(dim, p, ne, nurbs=net)
+    Xo, Jo = oracle_points(dim, p, ne, geom=nurbs.quarter_annulus(1.0, 2.0, 1.0, dim))
+    np.testing.assert_allclose(X, Xo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(J, Jo, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mapped_points_two_patch_annulus_one_sided(lib, dim):
+    # the map has a C0 knot at 1/3 in direction 2; the space has a patch interface there, so
+    # the two collocated abscissae take det DF from their own side (it jumps by 2 there)
+    net = inputs.two_patch_annulus_net(1.0, 2.0, 1.0, dim, 1.0 / 3.0)
+    p, ne = [2] * dim, [3, 6, 2][:dim]
+    itf = [(), (1.0 / 3.0,), ()][:dim]
+    X, J = _binding.mapped_points(dim, p, ne, nurbs=net, interfaces=itf)
+    Xo, Jo = oracle_points(dim, p, ne, geom=as_oracle_map(net), interfaces=itf)
+    np.testing.assert_allclose(X, Xo, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(J, Jo, rtol=1e-13, atol=0)
+    jumps = np.isclose(J[:-1] / J[1:], np.sqrt(2.0)) | np.isclose(J[1:] / J[:-1], np.sqrt(2.0))
+    assert jumps.any()
+
+
+def test_mapped_points_reject_bad_geometry(lib):
+    with pytest.raises(_binding.KLError):
+        _binding.mapped_points(2, 2, 4, lo=[0.0, 1.0], hi=[1.0, 1.0])
+    net = inputs.quarter_annulus_net(1.0, 2.0, 1.0, 2)
+    net = dict(net, weights=-np.asarray(net["weights"]))
+    with pytest.raises(_binding.KLError) as e:
+        _binding.mapped_points(2, 2, 4, nurbs=net)
+    assert "weights must be positive" in str(e.value)
