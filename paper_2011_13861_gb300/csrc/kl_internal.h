@@ -59,8 +59,16 @@ struct NurbsMap {
     std::vector<double> knots[3];
     std::vector<double> ctrl;
 };
-// F(xh) and det DF(xh); side[k] < 0 takes the left limit in direction k (at a C^0 knot of the map)
-void nurbs_map_point(const NurbsMap& m, const double* xh, const int* side, double* X, double* detDF);
+// the map's non-zero basis functions of direction k at one abscissa: span, values, derivatives
+// (directions k >= dim: the single function 1)
+struct MapBasis1D {
+    int span = 0;
+    double N[16] = {}, dN[16] = {};
+};
+void nurbs_basis_1d(const NurbsMap& m, int k, double x, int side, MapBasis1D* out);
+// F(xh) and det DF(xh) from the basis values of the three directions at xh (side < 0 in
+// nurbs_basis_1d takes the left limit, at a C^0 knot of the map)
+void nurbs_map_from_basis(const NurbsMap& m, const MapBasis1D* const b[3], double* X, double* detDF);
 
 // host set-up shared by kl_create and the host-only inspection entry points:
 // validate a geometry (for KL_GEOM_NURBS copy its map into *nm), build directions 0..dim-1 of a

@@ -367,21 +367,33 @@ kl_status map_greville_points(const kl_geometry* geom, const NurbsMap& nm, const
     // mapped Greville points X = F(xh) in vec order (direction 1 fastest) and J = sqrt(det DF)
     X->assign(size_t(Nt) * 3, 0.0);
     J->assign(size_t(Nt), std::sqrt(det));
+    // a NURBS map's basis values depend on one coordinate each: evaluate them once per
+    // direction and Greville abscissa (with its side), then form every point from them
+    std::vector<MapBasis1D> basis[3];
+    MapBasis1D unit;
+    if (geom->kind != KL_GEOM_BOX) {
+        nurbs_basis_1d(nm, 3, 0.0, 0, &unit);
+        for (int k = 0; k < d; ++k) {
+            basis[k].resize(size_t(dir[k].nt));
+            for (int i = 0; i < dir[k].nt; ++i)
+                nurbs_basis_1d(nm, k, dir[k].xi[size_t(i)], dir[k].side[size_t(i)], &basis[k][size_t(i)]);
+        }
+    }
     for (int64_t idx = 0; idx < Nt; ++idx) {
         int64_t r = idx;
         double xh[3] = {0.0, 0.0, 0.0};
-        int side[3] = {0, 0, 0};
+        const MapBasis1D* bk[3] = {&unit, &unit, &unit};
         for (int k = 0; k < d; ++k) {
             const int64_t ik = r % dir[k].nt;
             r /= dir[k].nt;
             xh[k] = dir[k].xi[size_t(ik)];
-            side[k] = dir[k].side[size_t(ik)];
+            if (geom->kind != KL_GEOM_BOX) bk[k] = &basis[k][size_t(ik)];
         }
         if (geom->kind == KL_GEOM_BOX) {
             for (int k = 0; k < d; ++k) (*X)[size_t(idx) * 3 + k] = geom->lo[k] + (geom->hi[k] - geom->lo[k]) * xh[k];
         } else {
             double Xp[3], detDF;
-            nurbs_map_point(nm, xh, side, Xp, &detDF);
+            nurbs_map_from_basis(nm, bk, Xp, &detDF);
             if (!(detDF > 0.0) || !std::isfinite(detDF))
                 return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");
             for (int k = 0; k < 3; ++k) (*X)[size_t(idx) * 3 + k] = Xp[k];
@@ -436,23 +448,27 @@ extern "C" kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* s
 
 namespace kl {
 
+// non-zero basis functions of direction k of the map at x, with their derivatives; side < 0
+// takes the left limit (at a C^0 knot of the map)
+void nurbs_basis_1d(const NurbsMap& m, int k, double x, int side, MapBasis1D* out) {
+    if (k >= m.dim) {
+        out->span = 0;
+        out->N[0] = 1.0;
+        out->dN[0] = 0.0;
+        return;
+    }
+    out->span = side < 0 ? find_span_left(m.knots[k], m.deg[k], x) : find_span(m.knots[k], m.deg[k], x);
+    nonzero_basis(m.knots[k], m.deg[k], out->span, x, out->N);
+    nonzero_basis_derivative(m.knots[k], m.deg[k], out->span, x, out->dN);
+}
+
 // F(xh) and det DF(xh) of a tensor-product NURBS map (Sec. 2.4): F = P / W with
 // P = sum_I N_I(xh) w_I P_I and W = sum_I N_I(xh) w_I; column j of DF is
 // (dP/dxh_j W - P dW/dxh_j) / W^2.  Directions beyond dim have one control point.
-void nurbs_map_point(const NurbsMap& m, const double* xh, const int* side, double* X, double* detDF) {
-    int span[3] = {0, 0, 0};
-    double N[3][16], dN[3][16];
-    for (int k = 0; k < 3; ++k) {
-        if (k < m.dim) {
-            span[k] = (side && side[k] < 0) ? find_span_left(m.knots[k], m.deg[k], xh[k])
-                                            : find_span(m.knots[k], m.deg[k], xh[k]);
-            nonzero_basis(m.knots[k], m.deg[k], span[k], xh[k], N[k]);
-            nonzero_basis_derivative(m.knots[k], m.deg[k], span[k], xh[k], dN[k]);
-        } else {
-            N[k][0] = 1.0;
-            dN[k][0] = 0.0;
-        }
-    }
+void nurbs_map_from_basis(const NurbsMap& m, const MapBasis1D* const bk[3], double* X, double* detDF) {
+    const double* N[3] = {bk[0]->N, bk[1]->N, bk[2]->N};
+    const double* dN[3] = {bk[0]->dN, bk[1]->dN, bk[2]->dN};
+    const int span[3] = {bk[0]->span, bk[1]->span, bk[2]->span};
     const int q0 = m.dim > 0 ? m.deg[0] : 0, q1 = m.dim > 1 ? m.deg[1] : 0, q2 = m.dim > 2 ? m.deg[2] : 0;
     double P[3] = {0, 0, 0}, W = 0.0, dP[3][3] = {{0}}, dW[3] = {0, 0, 0};
     for (int c = 0; c <= q2; ++c)
