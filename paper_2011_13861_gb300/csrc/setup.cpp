@@ -379,27 +379,27 @@ kl_status map_greville_points(const kl_geometry* geom, const NurbsMap& nm, const
                 nurbs_basis_1d(nm, k, dir[k].xi[size_t(i)], dir[k].side[size_t(i)], &basis[k][size_t(i)]);
         }
     }
-    for (int64_t idx = 0; idx < Nt; ++idx) {
-        int64_t r = idx;
-        double xh[3] = {0.0, 0.0, 0.0};
-        const MapBasis1D* bk[3] = {&unit, &unit, &unit};
-        for (int k = 0; k < d; ++k) {
-            const int64_t ik = r % dir[k].nt;
-            r /= dir[k].nt;
-            xh[k] = dir[k].xi[size_t(ik)];
-            if (geom->kind != KL_GEOM_BOX) bk[k] = &basis[k][size_t(ik)];
-        }
-        if (geom->kind == KL_GEOM_BOX) {
-            for (int k = 0; k < d; ++k) (*X)[size_t(idx) * 3 + k] = geom->lo[k] + (geom->hi[k] - geom->lo[k]) * xh[k];
-        } else {
-            double Xp[3], detDF;
-            nurbs_map_from_basis(nm, bk, Xp, &detDF);
-            if (!(detDF > 0.0) || !std::isfinite(detDF))
-                return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");
-            for (int k = 0; k < 3; ++k) (*X)[size_t(idx) * 3 + k] = Xp[k];
-            (*J)[size_t(idx)] = std::sqrt(detDF);
-        }
-    }
+    // points in vec order: direction 1 fastest (nested loops, no index division)
+    const int n0 = d > 0 ? dir[0].nt : 1, n1 = d > 1 ? dir[1].nt : 1, n2 = d > 2 ? dir[2].nt : 1;
+    int64_t idx = 0;
+    for (int i2 = 0; i2 < n2; ++i2)
+        for (int i1 = 0; i1 < n1; ++i1)
+            for (int i0 = 0; i0 < n0; ++i0, ++idx) {
+                const int ik[3] = {i0, i1, i2};
+                double* Xi = &(*X)[size_t(idx) * 3];
+                if (geom->kind == KL_GEOM_BOX) {
+                    for (int k = 0; k < d; ++k)
+                        Xi[k] = geom->lo[k] + (geom->hi[k] - geom->lo[k]) * dir[k].xi[size_t(ik[k])];
+                    continue;
+                }
+                const MapBasis1D* bk[3] = {&unit, &unit, &unit};
+                for (int k = 0; k < d; ++k) bk[k] = &basis[k][size_t(ik[k])];
+                double detDF;
+                nurbs_map_from_basis(nm, bk, Xi, &detDF);
+                if (!(detDF > 0.0) || !std::isfinite(detDF))
+                    return fail(KL_ERR_INVALID_ARG, "NURBS map: det DF <= 0 at a Greville point (map not invertible)");
+                (*J)[size_t(idx)] = std::sqrt(detDF);
+            }
     return KL_OK;
 }
 
@@ -466,33 +466,52 @@ void nurbs_basis_1d(const NurbsMap& m, int k, double x, int side, MapBasis1D* ou
 // P = sum_I N_I(xh) w_I P_I and W = sum_I N_I(xh) w_I; column j of DF is
 // (dP/dxh_j W - P dW/dxh_j) / W^2.  Directions beyond dim have one control point.
 void nurbs_map_from_basis(const NurbsMap& m, const MapBasis1D* const bk[3], double* X, double* detDF) {
-    const double* N[3] = {bk[0]->N, bk[1]->N, bk[2]->N};
-    const double* dN[3] = {bk[0]->dN, bk[1]->dN, bk[2]->dN};
-    const int span[3] = {bk[0]->span, bk[1]->span, bk[2]->span};
+    const double *N0 = bk[0]->N, *N1 = bk[1]->N, *N2 = bk[2]->N;
+    const double *dN0 = bk[0]->dN, *dN1 = bk[1]->dN, *dN2 = bk[2]->dN;
     const int q0 = m.dim > 0 ? m.deg[0] : 0, q1 = m.dim > 1 ? m.deg[1] : 0, q2 = m.dim > 2 ? m.deg[2] : 0;
-    double P[3] = {0, 0, 0}, W = 0.0, dP[3][3] = {{0}}, dW[3] = {0, 0, 0};
-    for (int c = 0; c <= q2; ++c)
-        for (int b = 0; b <= q1; ++b)
+    const int o0 = m.dim > 0 ? bk[0]->span - q0 : 0, o1 = m.dim > 1 ? bk[1]->span - q1 : 0,
+              o2 = m.dim > 2 ? bk[2]->span - q2 : 0;
+    // homogeneous sums H = sum_I N_I(xh) w_I (P_I, 1) and their derivatives dH[j] along xh_j,
+    // contracting direction 1, then 2, then 3 (the basis is a tensor product)
+    double H[4] = {0, 0, 0, 0}, dH[3][4] = {{0}};
+    for (int c = 0; c <= q2; ++c) {
+        double B[4] = {0, 0, 0, 0}, dB0[4] = {0, 0, 0, 0}, dB1[4] = {0, 0, 0, 0};
+        for (int b = 0; b <= q1; ++b) {
+            double A[4] = {0, 0, 0, 0}, dA[4] = {0, 0, 0, 0};
+            const double* row = &m.ctrl[4 * ((size_t(o2 + c) * m.n[1] + size_t(o1 + b)) * m.n[0] + size_t(o0))];
             for (int a = 0; a <= q0; ++a) {
-                const int i0 = (m.dim > 0 ? span[0] - q0 : 0) + a;
-                const int i1 = (m.dim > 1 ? span[1] - q1 : 0) + b;
-                const int i2 = (m.dim > 2 ? span[2] - q2 : 0) + c;
-                const double* cp = &m.ctrl[4 * ((size_t(i2) * m.n[1] + i1) * m.n[0] + i0)];
+                const double* cp = row + 4 * a;
                 const double w = cp[3];
-                const double val = N[0][a] * N[1][b] * N[2][c] * w;
-                const double der[3] = {dN[0][a] * N[1][b] * N[2][c] * w, N[0][a] * dN[1][b] * N[2][c] * w,
-                                       N[0][a] * N[1][b] * dN[2][c] * w};
-                W += val;
-                for (int r = 0; r < 3; ++r) P[r] += val * cp[r];
-                for (int j = 0; j < 3; ++j) {
-                    dW[j] += der[j];
-                    for (int r = 0; r < 3; ++r) dP[r][j] += der[j] * cp[r];
+                const double h[4] = {w * cp[0], w * cp[1], w * cp[2], w};
+                for (int r = 0; r < 4; ++r) {
+                    A[r] += N0[a] * h[r];
+                    dA[r] += dN0[a] * h[r];
                 }
             }
+            for (int r = 0; r < 4; ++r) {
+                B[r] += N1[b] * A[r];
+                dB0[r] += N1[b] * dA[r];
+                dB1[r] += dN1[b] * A[r];
+            }
+        }
+        for (int r = 0; r < 4; ++r) {
+            H[r] += N2[c] * B[r];
+            dH[0][r] += N2[c] * dB0[r];
+            dH[1][r] += N2[c] * dB1[r];
+            dH[2][r] += dN2[c] * B[r];
+        }
+    }
+    const double W = H[3];
+    const double P[3] = {H[0], H[1], H[2]};
+    const double dW[3] = {dH[0][3], dH[1][3], dH[2][3]};
+    double dP[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int j = 0; j < 3; ++j) dP[r][j] = dH[j][r];
+    const double iW = 1.0 / W, iW2 = iW * iW;
     double D[3][3];
     for (int r = 0; r < 3; ++r) {
-        X[r] = P[r] / W;
-        for (int j = 0; j < 3; ++j) D[r][j] = (dP[r][j] * W - P[r] * dW[j]) / (W * W);
+        X[r] = P[r] * iW;
+        for (int j = 0; j < 3; ++j) D[r][j] = (dP[r][j] * W - P[r] * dW[j]) * iW2;
     }
     if (m.dim == 1) {
         *detDF = D[0][0];
