@@ -89,7 +89,9 @@ KL_HD F2 sqr(F2 a) {
 }
 
 // sqrt(a), a >= 0: float32 reciprocal-square-root seed, one float32 Newton step, then one
-// double-float Heron correction r = r0 + (a - r0^2) y / 2.
+// double-float Heron correction r = r0 + (a - r0^2) y / 2.  The correction is about 2^-22 of
+// the root and y is good to about 2^-22.4 after the float step, so the root carries a relative
+// error of about 2^-44.5 (4e-14 measured on the host against long double).
 KL_HD F2 sqrt(F2 a, float rs_seed) {
     if (a.h <= 0.f) return F2{0.f, 0.f};
     float y = rs_seed;

@@ -61,8 +61,19 @@ int main() {
         const F2 ss = sum_sq3(d[0], d[1], d[2]);
         if (s > 0) sq_rel = std::fmax(sq_rel, (double)fabsl((val(ss) - s) / s));
     }
+    // sqrt of a double-float from a float seed with a relative error up to 2^-21 (the device
+    // seed is rsqrt.approx, good to about 2^-22.9)
+    double sqrt_rel = 0;
+    for (int i = 0; i < 300000; ++i) {
+        const long double a = std::pow(10.0, -12 + 16 * U(rng));
+        const F2 af = split(a);
+        const float seed = (float)(1.0 / std::sqrt((double)af.h)) * (float)(1.0 + (2 * U(rng) - 1) * std::ldexp(1.0, -21));
+        const F2 r = kl::df::sqrt(af, seed);
+        const long double ref = sqrtl(val(af));
+        sqrt_rel = std::fmax(sqrt_rel, (double)fabsl((val(r) - ref) / ref));
+    }
     std::printf("{\"exp_rel\": %.6e, \"exp_abs\": %.6e, \"exp_unnormalised\": %d, \"inexact_heads\": %d, "
-                "\"diff_abs\": %.6e, \"sum_sq_rel\": %.6e}\n",
-                exp_rel, exp_abs, exp_unnormalised, inexact_heads, diff_abs, sq_rel);
+                "\"diff_abs\": %.6e, \"sum_sq_rel\": %.6e, \"sqrt_rel\": %.6e}\n",
+                exp_rel, exp_abs, exp_unnormalised, inexact_heads, diff_abs, sq_rel, sqrt_rel);
     return 0;
 }

@@ -1,6 +1,7 @@
 """The double-float arithmetic of the stage-5 kernels (``csrc/df64.cuh``), built for the host and
 checked against long double: Tang's exponential over the kernels' argument range, the exact head
-difference of grid-form coordinates, and the fused sum of three squares.  The kernels run the
+difference of grid-form coordinates, the fused sum of three squares, and the square root from an
+approximate reciprocal-square-root seed.  The kernels run the
 same header on the GPU; the GPU parity tests check the whole product."""
 import json
 import os
@@ -40,3 +41,10 @@ def test_grid_form_heads_subtract_exactly(report):
 
 def test_sum_of_three_squares(report):
     assert report["sum_sq_rel"] < 5e-14
+
+
+def test_square_root_from_an_approximate_seed(report):
+    # one float Newton step leaves the seed good to about 2^-22.4 (its own roundings); the
+    # double-float Heron correction is about 2^-22 of the root and carries that relative error,
+    # so the root is good to about 2^-44.5 (4e-14), not to the 2^-48 of the representation
+    assert report["sqrt_rel"] < 6e-14
