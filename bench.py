@@ -35,8 +35,8 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 vector rate (nominal)
 # of the evaluations (one per unordered pair): algorithmic flops per ordered pair = eval/2 + 2b.
 FLOPS_PER_EVAL = {"exp": 8 + 6 + 16, "gauss": 8 + 16, "exp_sep": 3 + 2 + 16, "poly": 12}
 # DRAM bytes per launch of covmv64_sym_kernel<EXP, 4> at 39,304 points (ncu capture, see
-# profiles/stage5_fp64_sym_cube-p2-32^3-exp.md): 4.4 MB read + 136.0 MB written (partial slots)
-SYM64_NV4_TRAFFIC_BYTES = 4.391936e6 + 135.971584e6
+# profiles/stage5_fp64_sym_cube-p2-32^3-exp.md): 5.4 MB read + 136.3 MB written (partial slots)
+SYM64_NV4_TRAFFIC_BYTES = 5.377536e6 + 136.273408e6
 
 
 def parse():
