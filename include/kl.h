@@ -371,6 +371,16 @@ kl_status kl_direction_factors(int deg, int elems, int interp_deg, int interp_el
  * written on error. */
 kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* space, int64_t* Ntilde, double* X, double* J);
 
+/* Host only (no device use): the standard-form prolongation Q_k = L_f^T P_k L_c^{-T} of one
+ * direction (the factor kl_prolong applies; P_k = B~_f^{-1} B_c(x_f) interpolates every coarse
+ * B-spline at the fine Greville points, exact on nested spaces, Sec. 4.2 and 4.1), for
+ * inspection and testing without a GPU.  deg: degree of both spaces; elems_coarse, elems_fine:
+ * uniform element counts, elems_fine a multiple of elems_coarse.  On KL_OK *nc and *nf hold
+ * the numbers of coarse and fine functions and, if Q is not NULL, Q (nf*nc doubles, row-major,
+ * caller-owned) holds the factor.  Call once with Q = NULL to learn the sizes.  Errors:
+ * KL_ERR_INVALID_ARG for the rules of kl_create, a null nc/nf, or meshes that are not nested. */
+kl_status kl_prolongation_factor(int deg, int elems_coarse, int elems_fine, int* nc, int* nf, double* Q);
+
 /* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an
  * mbarrier that nothing completes, with the bounded-wait helper of the tensor-core kernels,
  * gives up after `seconds` (0 < seconds <= 2) and reports it.  Returns KL_ERR_TIMEOUT, the

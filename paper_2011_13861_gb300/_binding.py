@@ -97,6 +97,8 @@ SIGNATURES = {
                                             _vp, _vp, _vp]),
     "kl_mapped_points": (ctypes.c_int, [ctypes.POINTER(KLGeometry), ctypes.POINTER(KLSpace),
                                         ctypes.POINTER(_c_int64), _vp, _vp]),
+    "kl_prolongation_factor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int), _vp]),
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
@@ -509,6 +511,20 @@ def direction_factors(deg, elems, interp_deg=0, interp_elems=0, interfaces=()):
                                     ctypes.c_void_p(xi.ctypes.data), ctypes.c_void_p(side.ctypes.data),
                                     ctypes.c_void_p(L.ctypes.data), ctypes.c_void_p(C.ctypes.data)))
     return {"n": n.value, "nt": nt.value, "greville": xi, "side": side, "L": L, "C": C}
+
+
+def prolongation_factor(deg, elems_coarse, elems_fine):
+    """kl_prolongation_factor (host only, no GPU): Q_k = L_f^T P_k L_c^{-T} of one direction,
+    (n_fine x n_coarse), the factor kl_prolong applies."""
+    import numpy as np
+    lib = load()
+    nc, nf = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.kl_prolongation_factor(int(deg), int(elems_coarse), int(elems_fine), ctypes.byref(nc),
+                                      ctypes.byref(nf), None))
+    Q = np.zeros((nf.value, nc.value))
+    _check(lib.kl_prolongation_factor(int(deg), int(elems_coarse), int(elems_fine), ctypes.byref(nc),
+                                      ctypes.byref(nf), ctypes.c_void_p(Q.ctypes.data)))
+    return Q
 
 
 def mapped_points(dim, p, ne, pt=None, net=None, lo=None, hi=None, nurbs=None, interfaces=None):

@@ -429,6 +429,21 @@ extern "C" kl_status kl_direction_factors(int deg, int elems, int interp_deg, in
     return KL_OK;
 }
 
+// host-only view of the standard-form prolongation of one direction (the factor kl_prolong applies)
+extern "C" kl_status kl_prolongation_factor(int deg, int elems_coarse, int elems_fine, int* nc, int* nf, double* Q) {
+    using namespace kl;
+    if (!nc || !nf) return fail(KL_ERR_INVALID_ARG, "kl_prolongation_factor: null nc or nf");
+    Direction c, f;
+    KL_TRY(build_direction(deg, elems_coarse, deg, elems_coarse, {}, &c));
+    KL_TRY(build_direction(deg, elems_fine, deg, elems_fine, {}, &f));
+    std::vector<double> Qv;
+    KL_TRY(build_prolongation(c, f, &Qv));
+    *nc = c.n;
+    *nf = f.n;
+    if (Q) std::copy(Qv.begin(), Qv.end(), Q);
+    return KL_OK;
+}
+
 // host-only view of the mapped Greville grid and J (the points kl_create uploads)
 extern "C" kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* space, int64_t* Ntilde, double* X,
                                       double* J) {

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import ibq, nurbs
+from oracle import ibq, nurbs, prolong
 from paper_2011_13861_gb300 import _binding, build, inputs
 
 
@@ -121,3 +121,19 @@ def test_mapped_points_reject_bad_geometry(lib):
     with pytest.raises(_binding.KLError) as e:
         _binding.mapped_points(2, 2, 4, nurbs=net)
     assert "weights must be positive" in str(e.value)
+
+
+@pytest.mark.parametrize("p,ne_c,ne_f", [(1, 2, 6), (2, 4, 8), (3, 16, 48), (3, 5, 5), (4, 3, 9)])
+def test_prolongation_factor_matches_the_oracle(lib, p, ne_c, ne_f):
+    Q = _binding.prolongation_factor(p, ne_c, ne_f)
+    Qo = prolong.standard_form_map_1d(p, ne_c, ne_f)
+    assert Q.shape == Qo.shape
+    np.testing.assert_allclose(Q, Qo, rtol=0, atol=1e-12 * np.abs(Qo).max())
+    # nested spaces: Q has orthonormal columns (a standard-form vector keeps its norm)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(Q.shape[1]), rtol=0, atol=1e-12)
+
+
+def test_prolongation_factor_rejects_non_nested_meshes(lib):
+    with pytest.raises(_binding.KLError) as e:
+        _binding.prolongation_factor(2, 4, 6)
+    assert "refine" in str(e.value)
