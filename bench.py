@@ -48,15 +48,15 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--plain-block", type=int, default=4)
     ap.add_argument("--mixed-block", type=int, default=4)
-    ap.add_argument("--no-c4", action="store_true",
+    ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance quarter-annulus batch")
-    ap.add_argument("--no-c3", action="store_true",
+    ap.add_argument("--no-large-cube", action="store_true",
                     help="skip the 132,651-point Gaussian cube (mixed precision with blocks of 16)")
-    ap.add_argument("--no-c5", action="store_true", help="skip the learned warm start")
-    ap.add_argument("--c5-train-solves", type=int, default=2000,
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--warm-train-solves", type=int, default=2000,
                     help="coarse (16^3, p=3) training solves of the warm-start network (2000 = the full set)")
-    ap.add_argument("--c5-epochs", type=int, default=100)
-    ap.add_argument("--c5-eval", type=int, default=2, help="unseen parameter sets solved at 48^3")
+    ap.add_argument("--warm-epochs", type=int, default=100)
+    ap.add_argument("--warm-eval", type=int, default=2, help="unseen parameter sets solved at 48^3")
     return ap.parse_args()
 
 
@@ -174,7 +174,7 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-def measure_c4(kl, inputs):
+def measure_batched(kl, inputs):
     """64 seeded instances on the quarter annulus (quadratic NURBS map, radius 1..2, height 1),
     elements per direction 8..40, degree 2-3, exponential / Gaussian kernels, L log-uniform in
     [0.1, 2], 10 eigenpairs each: solved together (kl_eigs_batched: one batched stage-5 launch
@@ -213,7 +213,7 @@ def measure_c4(kl, inputs):
     return out
 
 
-def measure_c5(kl, inputs, train_solves, epochs, n_eval):
+def measure_warm_start(kl, inputs, train_solves, epochs, n_eval):
     """Learned warm start on the quarter annulus: a 4 x 256 bfloat16 network trained on the
     32 leading eigenvectors of `train_solves` coarse problems (p=3, 16^3 elements; kernel, L and
     radii drawn with seed 5), then used, prolonged exactly to 48^3 elements, as the start block
@@ -280,7 +280,7 @@ def measure_c5(kl, inputs, train_solves, epochs, n_eval):
     return out
 
 
-def measure_c3(kl, inputs, flush, stream):
+def measure_large_cube(kl, inputs, flush, stream):
     """Unit cube, p=3, 48^3 elements (132,651 points), Gaussian kernel L=0.3, 20 eigenpairs:
     the mixed form with blocks of 16 (float32 phase, tensor-core float64-class polish) against
     one plain float64 block-4 solve of the same problem on the same GPU."""
@@ -446,15 +446,15 @@ def main():
     e2e_t, e2e_info = e2e_once()
     e2e_value = world * e2e_info["applies"] * float(Nt) * Nt / e2e_t
 
-    c3 = None
-    if world == 1 and not args.no_c3:
-        c3 = measure_c3(kl, inputs, flush, stream)
-    c4 = None
-    if world == 1 and not args.no_c4:
-        c4 = measure_c4(kl, inputs)
-    c5 = None
-    if world == 1 and not args.no_c5:
-        c5 = measure_c5(kl, inputs, args.c5_train_solves, args.c5_epochs, args.c5_eval)
+    large_cube = None
+    if world == 1 and not args.no_large_cube:
+        large_cube = measure_large_cube(kl, inputs, flush, stream)
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = measure_batched(kl, inputs)
+    warm = None
+    if world == 1 and not args.no_warm_start:
+        warm = measure_warm_start(kl, inputs, args.warm_train_solves, args.warm_epochs, args.warm_eval)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -510,12 +510,12 @@ def main():
         "clocks": clk,
         "peaks_file": {k2: peaks.get(k2) for k2 in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
     }
-    if c3:
-        line["c3_mixed_with_blocks"] = c3
-    if c4:
-        line["c4_batched_instances"] = c4
-    if c5:
-        line["c5_learned_warm_start"] = c5
+    if large_cube:
+        line["cube_p3_48_gauss_mixed_blocks16"] = large_cube
+    if batched:
+        line["batched_annulus_instances_64"] = batched
+    if warm:
+        line["learned_warm_start"] = warm
     if cpu:
         line["cpu_baseline"] = cpu
     if rank == 0:
