@@ -4,14 +4,15 @@
 //   * float32 class (KL_P_TC32): float32 kernel values (MUFU ex2/rsqrt), three 8-bit digits.
 //
 // Exact slicing.  Each kernel value g (scaled so |g| <= 1) is written as
-// g = sum_{s<S} a_s 2^(-8(s+1)) with integer digits (|a_0| <= 256, |a_s| <= 128 after, by
-// round-to-nearest digit extraction, every step exact), and each u value, after division by a
+// g = sum_{s<S} a_s 2^(-8(s+1)) with integer digits (|a_0| <= 256, |a_s| <= 128 after by
+// round-to-nearest digit extraction, except |a_3| <= 256 where the double-float tail joins the
+// remainder; every step exact), and each u value, after division by a
 // per-vector power of two sigma >= max|u|, as u/sigma = sum_{t<S} b_t 2^(-8(t+1)).  The digits
 // are stored as bfloat16 "slices" a_s 2^(-8(s+1)) and b_t 2^(-8t), which bfloat16 holds exactly.
 // The tensor core forms the slice products exactly and adds them in float32, one accumulator per
 // level d = s + t:
 //   float64 class: levels 0-3 (1, 2, 3, 4 products) are multiples of 2^-8(d+1) and, summed over
-//     128 columns, below 2^23 of that unit, hence exact in float32 whatever the tensor core's
+//     128 columns, at most 2^24 of that unit, hence exact in float32 whatever the tensor core's
 //     rounding; levels 4-5
 //     (11 products, relative size <= 2^-32) share a fifth accumulator whose rounding stays
 //     below ~2^-49 of the sum; products of levels >= 6 (relative size < 2^-48) are dropped;
@@ -35,6 +36,7 @@
 // asynchronous operations and returns.
 #include "df64.cuh"
 #include "kernel32.cuh"
+#include "tc_slices.cuh"
 #include "tc_common.cuh"
 
 namespace kl {
@@ -102,45 +104,14 @@ __device__ __forceinline__ void product(int q, int* s, int* t, int* acc, bool* f
     *first = (q == 0 || q == 1 || q == 3 || q == 6 || q == 10);
 }
 
-// x rounded to the grid 2^-k (|x| < 2^(22-k)) by the shifter 1.5 * 2^(23-k), and the exact
-// remainder: the slice a 2^-k of digit a
-__device__ __forceinline__ float digit(float& x, float shifter) {
-    const float p = __fsub_rn(__fadd_rn(x, shifter), shifter);
-    x = __fsub_rn(x, p);
-    return p;
-}
-
-// six slices a_s 2^(-8(s+1)) of a double-float g with |g| <= 1 (see the file comment); the
-// tail joins the remainder after the three head digits
-__device__ __forceinline__ void slices6(F2 g, float* out) {
-    float x = g.h;
-    out[0] = digit(x, 49152.f);                     // 1.5 * 2^15: grid 2^-8
-    out[1] = digit(x, 192.f);                       // grid 2^-16
-    out[2] = digit(x, 0.75f);                       // grid 2^-24
-    x = __fadd_rn(x, g.l);                          // |x| <= 2^-25 after three digits
-    out[3] = digit(x, 0.0029296875f);               // 1.5 * 2^-9: grid 2^-32
-    out[4] = digit(x, 1.1444091796875e-05f);        // 1.5 * 2^-17: grid 2^-40
-    out[5] = digit(x, 4.4703483581542969e-08f);     // 1.5 * 2^-25: grid 2^-48
-}
-
-// three slices of a float g with |g| <= 1
-__device__ __forceinline__ void slices3(float g, float* out) {
-    float x = g;
-    out[0] = digit(x, 49152.f);
-    out[1] = digit(x, 192.f);
-    out[2] = digit(x, 0.75f);
-}
+using tcs::slices3;
+using tcs::slices6;
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
 }
 
-// acc += x for a float x (exact two-sum into the head, tail accumulated)
-__device__ __forceinline__ void df_acc(F2& acc, float x) {
-    const F2 s = df::two_sum(acc.h, x);
-    acc.h = s.h;
-    acc.l = __fadd_rn(acc.l, s.l);
-}
+using tcs::df_acc;
 
 // sigma[v] = 2^e with 2^(e-1) <= max_c |u[v][c]| < 2^e (1 when the column is zero)
 template <typename TU>
@@ -190,15 +161,11 @@ __global__ void tcx_image_kernel(const float* __restrict__ P, int64_t ldp, int64
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int64_t c = c0 + g8 * 8 + e;
-                double x = (v < nv && c < Nt) ? double(U[v * ldu + c]) * inv : 0.0;
-                double w = 1.0;
+                const double x = (v < nv && c < Nt) ? double(U[v * ldu + c]) * inv : 0.0;
+                float one[X::kSlices];
+                tcs::u_slices<X::kSlices>(x, one);
 #pragma unroll
-                for (int q = 0; q < X::kSlices; ++q) {
-                    const double p = rint(x * 256.0);
-                    x = fma(x, 256.0, -p);   // exact
-                    sl[q][e] = float(p * w);  // |p| <= 256: exact in bfloat16 after scaling
-                    w *= 0.00390625;
-                }
+                for (int q = 0; q < X::kSlices; ++q) sl[q][e] = one[q];
             }
 #pragma unroll
             for (int q = 0; q < X::kSlices; ++q)
