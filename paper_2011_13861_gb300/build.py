@@ -35,12 +35,18 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
+def dependencies():
+    """Every source and header the translation units include (csrc/ and include/): a change to
+    any of them makes libkl.so stale."""
+    return sources() + sorted(os.path.join(d, f) for d in (CSRC, INCLUDE) for f in os.listdir(d)
+                              if f.endswith((".h", ".cuh")))
+
+
 def build(verbose=False, force=False):
     """Compile every CUDA/C++ source of the library and link libkl.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(INCLUDE, "kl.h"),
-                                                        os.path.join(CSRC, "kl_internal.h")])
+    newest = max(os.path.getmtime(p) for p in dependencies())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     cc = nvcc()

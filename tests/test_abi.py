@@ -41,3 +41,12 @@ def test_product_does_not_import_the_oracle():
                 with open(os.path.join(dirpath, f)) as fh:
                     src = fh.read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_build_tracks_every_header():
+    # libkl.so is stale when any source or header changes, including the .cuh arithmetic headers
+    deps = set(build.dependencies())
+    for d in (os.path.join(ROOT, "paper_2011_13861_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for f in os.listdir(d):
+            if f.endswith((".cu", ".cpp", ".h", ".cuh")):
+                assert os.path.join(d, f) in deps, f
