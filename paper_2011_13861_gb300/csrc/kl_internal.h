@@ -207,7 +207,7 @@ struct kl_handle_s {
     float* fP = nullptr;      // 3 x Nt float coordinates scaled for ex2
     double* dJ = nullptr;     // Nt
     float* fJ = nullptr;      // Nt
-    double* dTab = nullptr;   // 64
+    double* dTab = nullptr;   // 1024: 2^(j/1024) for the float64 exponential
     float* dfP = nullptr;     // 6 x Nt double-float coordinates (pre-scaled like dP)
     float* dfTab = nullptr;   // 128: double-float 2^(-j/64)
     int* dStatus = nullptr;   // device status word of the kernels with bounded waits (0 = ok)
