@@ -1,6 +1,7 @@
 // Double-float ("df64") arithmetic: a value is the unevaluated sum hi + lo of two float32
 // numbers with |lo| <= ulp(hi)/2, giving about 48 significant bits (the point coordinates are
-// the exception: a grid form with larger tails, which only `diff` below reads).  Built from the
+// the exception: a grid form with larger tails, which `kernel_df` below differences exactly or
+// renormalises).  Built from the
 // error-free transformations of Knuth (TwoSum), Dekker (Fast2Sum) and the FMA-based exact
 // product; the exponential follows Tang's table-driven method.
 //
