@@ -26,5 +26,15 @@ closed_form  closed-form eigenvalues of the 1D exponential kernel
 
 Every function is pinned by a ``-m "not gpu"`` test in ``tests/`` against
 something other than itself (closed forms, textbook special cases,
-invariants, brute force).  No function here is "parity unpinned".
+invariants, brute force).  No function here is "parity unpinned".  Among them:
+
+* kernels.kernel_matrix in d >= 2 (Sec. 3.1): kernel values at offsets of known
+  Euclidean length (Pythagorean triples and quadruples) and the invariance of the
+  exp and gauss spectra under a 30-degree rotation of the domain, which the
+  separable kernel must not show
+  (test_kernel_values_at_pythagorean_offsets, test_euclidean_kernels_are_rotation_invariant);
+* mlp.forward / mlp.backward with the roundings off: the same network built from
+  torch.nn Linear and Tanh layers in float64 and its autograd gradients
+  (test_mlp_forward_and_backward_match_torch_nn); the bfloat16 rounding against
+  torch's conversion, Adam against torch.optim.Adam.
 """

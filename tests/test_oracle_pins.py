@@ -13,7 +13,7 @@ import pytest
 import scipy.linalg as sla
 from scipy.special import comb
 
-from oracle import bspline, closed_form, galerkin, ibq, nurbs
+from oracle import bspline, closed_form, galerkin, ibq, kernels, nurbs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -264,6 +264,61 @@ def test_cube_symmetry_multiplicities():
     assert abs(w[1] - w[2]) / w[0] < 1e-13 and abs(w[2] - w[3]) / w[0] < 1e-13
 
 
+def test_kernel_values_at_pythagorean_offsets():
+    """Kernel values at point pairs whose Euclidean distance is known exactly: offsets
+    (3, 4)/5, (3, 4, 12)/13 and (2, 3, 6)/7 have length 1 (Pythagorean triples and quadruples),
+    scaled by s.  exp must give e^{-s/L}, gauss e^{-s^2/L^2} and exp_sep e^{-s |o|_1/L}; an L1
+    or maximum norm, or a distance without the square root, fails the first two."""
+    for off in ([3.0, 4.0], [3.0, 4.0, 12.0], [2.0, 3.0, 6.0]):
+        off = np.array(off) / np.linalg.norm(off)
+        for s, L in ((0.5, 0.7), (1.3, 0.4), (2.0, 3.0)):
+            x0 = np.linspace(-0.3, 0.4, len(off))
+            X1, X2 = x0[None, :], (x0 + s * off)[None, :]
+            assert abs(kernels.kernel_matrix(X1, X2, "exp", 1.5, L)[0, 0] - 2.25 * math.exp(-s / L)) < 1e-15
+            assert abs(kernels.kernel_matrix(X2, X1, "gauss", 1.0, L)[0, 0] - math.exp(-(s / L) ** 2)) < 1e-15
+            l1 = s * np.abs(off).sum()
+            assert abs(kernels.kernel_matrix(X1, X2, "exp_sep", 1.0, L)[0, 0] - math.exp(-l1 / L)) < 1e-15
+
+
+def rotated_box_map(dim, lx, ly, lz=1.0, angle=math.pi / 6):
+    """The box [0,lx] x [0,ly] (x [0,lz]) rotated by `angle` in the x-y plane, written as a
+    degree-1 NURBS map with unit weights (an affine map, det DF = lx ly lz everywhere)."""
+    c, s = math.cos(angle), math.sin(angle)
+    t = np.array([0.0, 0.0, 1.0, 1.0])
+    if dim == 2:
+        ctrl = np.zeros((2, 2, 2))
+        for j in range(2):
+            for i in range(2):
+                x, y = lx * i, ly * j
+                ctrl[j, i] = [c * x - s * y, s * x + c * y]
+        return nurbs.NURBSMap([1, 1], [t, t], ctrl, np.ones((2, 2)))
+    ctrl = np.zeros((2, 2, 2, 3))
+    for k in range(2):
+        for j in range(2):
+            for i in range(2):
+                x, y = lx * i, ly * j
+                ctrl[k, j, i] = [c * x - s * y, s * x + c * y, lz * k]
+    return nurbs.NURBSMap([1, 1, 1], [t, t, t], ctrl, np.ones((2, 2, 2)))
+
+
+@pytest.mark.parametrize("dim,p,ne", [(2, 2, [5, 4]), (3, 2, [3, 3, 2])])
+def test_euclidean_kernels_are_rotation_invariant(dim, p, ne):
+    """Rotating the domain by 30 degrees leaves every Euclidean distance, det DF and hence the
+    spectra of the exp and gauss operators unchanged; the separable kernel measures the L1
+    distance, which a rotation changes, so its spectrum must move.  A kernel that used the L1 or
+    maximum norm in d >= 2 for exp or gauss fails the first check."""
+    lo, hi = [0.0] * dim, [1.0, 0.6, 0.8][:dim]
+    F = rotated_box_map(dim, *hi)
+    for kind, L, must_match in (("exp", 0.5, True), ("gauss", 0.4, True), ("exp_sep", 0.5, False)):
+        wb = np.linalg.eigvalsh(ibq.Problem(dim, p, ne, kernel=kind, L=L, lo=lo, hi=hi).dense_operator())
+        wr = np.linalg.eigvalsh(ibq.Problem(dim, p, ne, kernel=kind, L=L, geom=F).dense_operator())
+        dev = np.abs(wb - wr).max() / wb.max()
+        if must_match:
+            assert dev < 1e-13, (kind, dev)
+        else:
+            assert dev > 1e-4, (kind, dev)
+
+
 # ---------------------------------------------------------------------------------------------
 # NURBS geometry map (Sec. 2.4) used for the quarter-annulus instances
 # ---------------------------------------------------------------------------------------------
@@ -406,6 +461,47 @@ def test_projector_loss_closed_form_and_invariance():
     assert abs(mlp.projector_loss(rot, Vs, k)[0] - loss) < 1e-12 * loss
     exact = np.stack([(Vs[s] @ R).T.reshape(-1) for s in range(B)])
     assert abs(mlp.projector_loss(exact, Vs, k)[0]) < 1e-14   # cancellation of k - 2k + k
+
+
+def test_mlp_forward_and_backward_match_torch_nn():
+    """The float64 network (roundings off) against torch.nn: Linear layers with Tanh between
+    them and none after the last, same weights (torch stores W^T), float64; the gradients of the
+    projector loss from mlp.backward against torch autograd of the same loss.  A tanh on the
+    output layer, a bias applied before the activation's input is complete, or transposed
+    weights fail here."""
+    import torch
+    from oracle import mlp
+    rng = np.random.default_rng(11)
+    n, k, B = 7, 3, 5
+    sizes = [4, 16, 16, 16, k * n]
+    Ws, bs = _tiny_net(rng, sizes)
+    x = rng.standard_normal((B, 4))
+    Vs = np.stack([np.linalg.qr(rng.standard_normal((n, k)))[0] for _ in range(B)])
+    layers = []
+    for l, (W, b) in enumerate(zip(Ws, bs)):
+        lin = torch.nn.Linear(W.shape[0], W.shape[1], dtype=torch.float64)
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(W.T.copy()))
+            lin.bias.copy_(torch.from_numpy(b.copy()))
+        layers.append(lin)
+        if l < len(Ws) - 1:
+            layers.append(torch.nn.Tanh())
+    net = torch.nn.Sequential(*layers)
+    out_t = net(torch.from_numpy(x))
+    out, cache = mlp.forward(Ws, bs, x, rounding=False)
+    assert np.abs(out - out_t.detach().numpy()).max() < 1e-14 * max(1.0, np.abs(out).max())
+    # projector loss written with torch ops from its definition ||Y Y^T - V V^T||_F^2 / k
+    Y = out_t.reshape(B, k, n).transpose(1, 2)
+    Vt = torch.from_numpy(Vs)
+    loss_t = ((Y @ Y.transpose(1, 2) - Vt @ Vt.transpose(1, 2)) ** 2).sum(dim=(1, 2)).mean() / k
+    loss_t.backward()
+    loss, g = mlp.projector_loss(out, Vs, k)
+    assert abs(loss - loss_t.item()) < 1e-13 * abs(loss)
+    dWs, dbs = mlp.backward(Ws, bs, cache, g, rounding=False)
+    lins = [m for m in net if isinstance(m, torch.nn.Linear)]
+    for l, lin in enumerate(lins):
+        assert np.abs(dWs[l] - lin.weight.grad.numpy().T).max() < 1e-13 * np.abs(dWs[l]).max()
+        assert np.abs(dbs[l] - lin.bias.grad.numpy()).max() < 1e-13 * np.abs(dbs[l]).max()
 
 
 def test_mlp_gradient_finite_differences():
