@@ -167,17 +167,23 @@ kl_status kl_covmv(kl_handle h, int precision, const double* u_dev, int64_t ldu,
                    int64_t ldz, int nvec, void* stream);
 
 /* kl_covmv without any device allocation (the paper has no counterpart: this is a deployment
- * convenience).  For callers that cannot call cudaMalloc when they apply the operator -- code
- * recorded while a stream is captured into a CUDA graph, where allocation is not allowed, or
- * programs that allocate everything up front and forbid it later.  kl_covmv may grow the
- * handle's workspace; this call instead keeps its split partial sums in a fixed 32 MiB
- * file-scope device array that every GPU loading the library holds until exit.
+ * convenience).  For callers that cannot call cudaMalloc when they apply the operator: programs
+ * that take their whole device-memory budget at start-up and forbid allocation afterwards (for
+ * example a component running inside a host application that owns the device memory), or
+ * loops that cannot afford the implicit device synchronisation of cudaMalloc/cudaFree between
+ * steps.  kl_covmv may grow the handle's workspace; this call instead keeps its split partial
+ * sums in a fixed 32 MiB file-scope device array that every GPU loading the library holds until
+ * exit.
  *   - precision must be KL_P_FP64; u, z as for kl_covmv; the handle itself comes from
  *     kl_create, which does allocate, so create it beforehand.
  *   - Ntilde x min(nvec, 16) must not exceed 4 Mi (4,194,304) doubles, else KL_ERR_INVALID_ARG
- *     with nothing launched.
+ *     with nothing launched.  Near that limit fewer column splits fit in the array (at 16
+ *     vectors and 133k points only one), so the product runs on fewer CTAs and can be much
+ *     slower than kl_covmv; the result is the same.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *     with that device current; make that first call before any stream capture.  The address
+ *     is cached with the identity of its CUDA context and looked up again after the context
+ *     was destroyed and recreated (cudaDeviceReset).
  *   - All calls share the array: launches that overlap on the GPU (other streams, other host
  *     threads) race on it, so order them.  No part of it needs clearing between calls.
  * Results agree with kl_covmv to rounding (the split count may differ). */

@@ -64,7 +64,7 @@ cudaError_t launch_contract(const Tin* X, int64_t ldx, Tout* Y, int64_t ldy, con
     int64_t total = A * m * B * nvec;
     if (total == 0) return cudaSuccess;
     int64_t blocks = (total + kContractThreads - 1) / kContractThreads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > num_sms() * 16) blocks = num_sms() * 16;
     const size_t smem = size_t(n) * m * sizeof(Tc);
     count_launches(1);
     if (smem <= kFactorSmemMax)

@@ -320,7 +320,7 @@ size_t covmv_df_part_doubles(int64_t Nt, int nvec) {
 
 int covmv_df_splits(int64_t Nt) {
     const int64_t rowblocks = (Nt + kDfThreads - 1) / kDfThreads;
-    int64_t splits = (152 * 8 * 4 + rowblocks - 1) / rowblocks;
+    int64_t splits = (int64_t(num_sms()) * 8 * 4 + rowblocks - 1) / rowblocks;
     int64_t maxs = Nt / (4 * kDfTile);
     if (maxs < 1) maxs = 1;
     if (splits > maxs) splits = maxs;
@@ -357,7 +357,7 @@ cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, i
             count_launches(2);
             int64_t tot = Nt * g;
             int blocks = int((tot + 255) / 256);
-            if (blocks > 152 * 8) blocks = 152 * 8;
+            if (blocks > num_sms() * 8) blocks = num_sms() * 8;
             covmv_df_reduce<<<blocks, 256, 0, s>>>(part, nt_tiles, Nt, g, Z + int64_t(v0) * ldz, ldz, scale2, J);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
@@ -379,7 +379,7 @@ cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, i
         count_launches(2);
         int64_t tot = Nt * g;
         int blocks = int((tot + 255) / 256);
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         covmv_df_reduce<<<blocks, 256, 0, s>>>(part, used, Nt, g, Z + int64_t(v0) * ldz, ldz, scale2, J);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

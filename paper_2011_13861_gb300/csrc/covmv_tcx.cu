@@ -467,7 +467,7 @@ cudaError_t launch_tcx(const CovParams& cp, const TU* U, int64_t ldu, int nvec, 
     unsigned char* im = static_cast<unsigned char*>(img);
     const int64_t nchunks = sc.len;
     double* sigma = reinterpret_cast<double*>(im + nchunks * X::kImg);
-    const int img_blocks = int(nchunks < 152 * 8 ? nchunks : 152 * 8);
+    const int img_blocks = int(nchunks < int64_t(num_sms()) * 8 ? nchunks : int64_t(num_sms()) * 8);
     const float* P = CLS == 64 ? cp.Pdf : cp.P32;
     for (int v0 = 0; v0 < nvec; v0 += kNB) {
         const int g = (nvec - v0) < kNB ? (nvec - v0) : kNB;
@@ -489,7 +489,7 @@ cudaError_t launch_tcx(const CovParams& cp, const TU* U, int64_t ldu, int nvec, 
         if (e != cudaSuccess) return e;
         const int64_t tot = Nt * g;
         int blocks = int((tot + 255) / 256);
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
         slot_reduce<kRows, kNB><<<blocks, 256, 0, s>>>(part, Nt, g, sc.len, sc.T, sc.G, sc.maxseg,
                                                        Z + int64_t(v0) * ldz, ldz, scale2, J);
         e = cudaGetLastError();

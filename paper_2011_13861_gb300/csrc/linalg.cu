@@ -638,7 +638,7 @@ cudaError_t launch_chol_inv(double* G, int ldg, int b, double* Rinv, double* R, 
 
 cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64_t seed,
                                 uint64_t offset, cudaStream_t s) {
-    random_block_kernel<<<grid_for(N * b, 256, 152 * 4), 256, 0, s>>>(V, ldv, N, b, seed, offset);
+    random_block_kernel<<<grid_for(N * b, 256, num_sms() * 4), 256, 0, s>>>(V, ldv, N, b, seed, offset);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -702,7 +702,7 @@ cudaError_t launch_copy_block(const double* src, int64_t lds, double* dst, int64
 
 cudaError_t launch_to_float(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,
                             int cols, cudaStream_t s) {
-    to_float_kernel<<<grid_for(rows * cols, 256, 152 * 8), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+    to_float_kernel<<<grid_for(rows * cols, 256, num_sms() * 8), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,11 +1,11 @@
 """Launches the stage-5 kernel product alone, for kernel profiling (ncu) and timing.
 
-  python -m paper_2011_13861_gb300.profile --workload cube-p2-32^3-exp-L0.5 --precision fp64 --nvec 1 --reps 3
+  python profile_kernels.py --workload cube-p2-32^3-exp-L0.5 --precision fp64 --nvec 1 --reps 3
 
 Builds the handle, runs stages 1-4 once to obtain u, then calls kl_covmv `reps` times on the
 current stream and prints the CUDA-event time per call.
 
-  python -m paper_2011_13861_gb300.profile --mlp-train --batch 64 --reps 3
+  python profile_kernels.py --mlp-train --batch 64 --reps 3
 
 times training steps of the warm-start network (4 inputs, 4 x 256 tanh, 32 x 6,859 outputs) on
 seeded synthetic inputs and targets: one warm-up epoch, then `reps` epochs of 256 samples.
