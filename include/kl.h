@@ -387,6 +387,14 @@ kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* space, int64
  * KL_ERR_INVALID_ARG for the rules of kl_create, a null nc/nf, or meshes that are not nested. */
 kl_status kl_prolongation_factor(int deg, int elems_coarse, int elems_fine, int* nc, int* nf, double* Q);
 
+/* Measured throughput of the arithmetic pipes that bound the stage-5 kernels (no counterpart
+ * in the paper: the denominators of the roofline fractions that the benchmark reports).
+ * Runs four short microbenchmarks on the current device (about 0.1 s in total, synchronous)
+ * and writes, as operations per second for the whole GPU: rates_host[0] float64 FMA,
+ * [1] float32 FMA, [2] MUFU ex2 (float32), [3] MUFU rsqrt (float32).  n >= 4, else
+ * KL_ERR_INVALID_ARG. */
+kl_status kl_pipe_rates(double* rates_host, int n, void* stream);
+
 /* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an
  * mbarrier that nothing completes, with the bounded-wait helper of the tensor-core kernels,
  * gives up after `seconds` (0 < seconds <= 2) and reports it.  Returns KL_ERR_TIMEOUT, the

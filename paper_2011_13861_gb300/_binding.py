@@ -100,6 +100,7 @@ SIGNATURES = {
     "kl_prolongation_factor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), _vp]),
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
+    "kl_pipe_rates": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
     "kl_destroy": (None, [_vp]),
@@ -548,3 +549,11 @@ def wait_selftest(seconds=0.05, stream=None):
     expected) and the library's message."""
     st = load().kl_wait_selftest(float(seconds), _stream(stream))
     return st, load().kl_last_error().decode()
+
+
+def pipe_rates(stream=None):
+    """kl_pipe_rates: measured operations per second of the float64 FMA, float32 FMA, MUFU ex2
+    and MUFU rsqrt pipes of the current GPU (dict)."""
+    out = (ctypes.c_double * 4)()
+    _check(load().kl_pipe_rates(ctypes.cast(out, ctypes.c_void_p), 4, _stream(stream)))
+    return {"dfma_per_s": out[0], "ffma_per_s": out[1], "ex2_per_s": out[2], "rsqrt_per_s": out[3]}

@@ -1,0 +1,124 @@
+// Throughput of the arithmetic pipes that bound the stage-5 kernels: float64 FMA (DFMA),
+// float32 FMA (FFMA), and the special-function unit's ex2 and rsqrt (MUFU).  These measured
+// rates are the denominators of the roofline fractions the stage-5 kernels report (the kernels
+// are compute-bound: a few MB of points and vectors against Ntilde^2 kernel evaluations).
+//
+// Each kernel runs a persistent grid of full-occupancy CTAs; every thread advances 8 (float64)
+// or 16 (float32) independent dependency chains, unrolled so that the loop's own counter and
+// branch are a small fraction of the issued instructions.  The chains stay bounded and finite
+// (a contraction for FMA, x -> 2^-x and x -> 1/sqrt(x) for the MUFU functions) and their sum is
+// stored only under a condition the compiler cannot decide, so no operation is removed.
+#include "kl_internal.h"
+
+namespace kl {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float mufu_ex2(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+    float y;
+    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void __launch_bounds__(kThreads) dfma_rate_kernel(int iters, double a, double b, double* sink) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = 0.5 + 1e-3 * i + 1e-9 * threadIdx.x;
+#pragma unroll 4
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == -1.0) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) ffma_rate_kernel(int iters, float a, float b, double* sink) {
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = 0.5f + 1e-3f * i + 1e-7f * threadIdx.x;
+#pragma unroll 8
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i];
+    if (s == -1.f) sink[0] = s;
+}
+
+template <int FN>   // 0: ex2 of the negated value, 1: rsqrt
+__global__ void __launch_bounds__(kThreads) mufu_rate_kernel(int iters, float a, double* sink) {
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = a + 1e-3f * i + 1e-7f * threadIdx.x;
+#pragma unroll 4
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = FN == 0 ? mufu_ex2(-x[i]) : mufu_rsqrt(x[i]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i];
+    if (s == -1.f) sink[0] = s;
+}
+
+}  // namespace
+}  // namespace kl
+
+using namespace kl;
+
+extern "C" kl_status kl_pipe_rates(double* rates_host, int n, void* stream) {
+    if (!rates_host || n < 4) return fail(KL_ERR_INVALID_ARG, "kl_pipe_rates: rates_host needs 4 entries");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = num_sms() * (2048 / kThreads);
+    const double threads = double(grid) * kThreads;
+    DevBuf sink;
+    KL_TRY(ensure(sink, sizeof(double)));
+    double* snk = static_cast<double*>(sink.ptr);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // operations per launch: chains x iterations x threads
+    const int iters[4] = {2048, 32768, 8192, 4096};
+    const double ops[4] = {8.0 * iters[0] * threads, 16.0 * iters[1] * threads, 16.0 * iters[2] * threads,
+                           16.0 * iters[3] * threads};
+    int launches = 0;
+    for (int op = 0; op < 4 && e == cudaSuccess; ++op) {
+        float best = 0.f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // first launch is a warm-up
+            e = cudaEventRecord(e0, s);
+            if (e != cudaSuccess) break;
+            switch (op) {
+                case 0: dfma_rate_kernel<<<grid, kThreads, 0, s>>>(iters[0], 0.999999, 1e-7, snk); break;
+                case 1: ffma_rate_kernel<<<grid, kThreads, 0, s>>>(iters[1], 0.9999f, 1e-5f, snk); break;
+                case 2: mufu_rate_kernel<0><<<grid, kThreads, 0, s>>>(iters[2], 0.5f, snk); break;
+                default: mufu_rate_kernel<1><<<grid, kThreads, 0, s>>>(iters[3], 0.7f, snk); break;
+            }
+            ++launches;
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+        }
+        if (e == cudaSuccess) rates_host[op] = ops[op] / (double(best) * 1e-3);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    release(sink);
+    count_launches(launches);
+    if (e != cudaSuccess) return cuda_fail(e, "pipe-rate microbenchmark");
+    return KL_OK;
+}

@@ -5,6 +5,14 @@
 Builds the handle, runs stages 1-4 once to obtain u, then calls kl_covmv `reps` times on the
 current stream and prints the CUDA-event time per call.
 
+  python profile_kernels.py --contract --workload cube-p3-48^3-gauss-L0.3 --nvec 32 --reps 3
+
+times the forward (stages 1-4) and backward (stages 6-9) contractions alone.
+
+  python profile_kernels.py --peaks
+
+prints the measured float64/float32 FMA and MUFU ex2/rsqrt rates (kl_pipe_rates).
+
   python profile_kernels.py --mlp-train --batch 64 --reps 3
 
 times training steps of the warm-start network (4 inputs, 4 x 256 tanh, 32 x 6,859 outputs) on
@@ -36,6 +44,26 @@ def mlp_train(a):
     print(json.dumps({"mlp_train": {"batch": a.batch, "params": net.nparam, "ms_per_step": out}}))
 
 
+def contract(a):
+    w = inputs.WORKLOADS[a.workload]
+    G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    v = torch.from_numpy(inputs.random_block(G.N, a.nvec, seed=1).T.copy()).cuda()
+    z = torch.from_numpy(inputs.random_block(G.Nt, a.nvec, seed=2).T.copy()).cuda()
+    G.forward(v)
+    G.backward(z)
+    torch.cuda.synchronize()
+    out = {"forward": [], "backward": []}
+    for _ in range(a.reps):
+        for name, fn in (("forward", lambda: G.forward(v)), ("backward", lambda: G.backward(z))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out[name].append(e0.elapsed_time(e1))
+    print(json.dumps({"workload": a.workload, "nvec": a.nvec, "N": G.N, "Ntilde": G.Nt, "ms": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cube-p2-32^3-exp-L0.5")
@@ -51,12 +79,19 @@ def main():
     ap.add_argument("--polish-ncv", type=int, default=0)
     ap.add_argument("--low", default="fp32", choices=["fp32", "tc32"])
     ap.add_argument("--mlp-train", action="store_true", help="time training steps of the warm-start network")
+    ap.add_argument("--contract", action="store_true", help="time the forward and backward contractions")
+    ap.add_argument("--peaks", action="store_true", help="measured pipe rates (kl_pipe_rates)")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--accurate", default="df64", choices=["fp64", "df64", "tc64"],
                     help="accurate-phase arithmetic of --solve plain_df / mixed")
     a = ap.parse_args()
     if a.mlp_train:
         return mlp_train(a)
+    if a.contract:
+        return contract(a)
+    if a.peaks:
+        print(json.dumps(kl.pipe_rates()))
+        return
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     if a.solve:
