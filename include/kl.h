@@ -391,8 +391,9 @@ kl_status kl_prolongation_factor(int deg, int elems_coarse, int elems_fine, int*
  * in the paper: the denominators of the roofline fractions that the benchmark reports).
  * Runs four short microbenchmarks on the current device (about 0.1 s in total, synchronous)
  * and writes, as operations per second for the whole GPU: rates_host[0] float64 FMA,
- * [1] float32 FMA, [2] MUFU ex2 (float32), [3] MUFU rsqrt (float32).  n >= 4, else
- * KL_ERR_INVALID_ARG. */
+ * [1] float32 FMA, [2] MUFU ex2 (float32), [3] MUFU rsqrt (float32); with n >= 8 also the SM
+ * clock in MHz that each of the four timed launches ran at ([4..7], from the SM cycle counter
+ * and the global timer of one thread).  n >= 4, else KL_ERR_INVALID_ARG. */
 kl_status kl_pipe_rates(double* rates_host, int n, void* stream);
 
 /* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an

@@ -553,7 +553,8 @@ def wait_selftest(seconds=0.05, stream=None):
 
 def pipe_rates(stream=None):
     """kl_pipe_rates: measured operations per second of the float64 FMA, float32 FMA, MUFU ex2
-    and MUFU rsqrt pipes of the current GPU (dict)."""
-    out = (ctypes.c_double * 4)()
-    _check(load().kl_pipe_rates(ctypes.cast(out, ctypes.c_void_p), 4, _stream(stream)))
-    return {"dfma_per_s": out[0], "ffma_per_s": out[1], "ex2_per_s": out[2], "rsqrt_per_s": out[3]}
+    and MUFU rsqrt pipes of the current GPU, and the SM clock each launch ran at (dict)."""
+    out = (ctypes.c_double * 8)()
+    _check(load().kl_pipe_rates(ctypes.cast(out, ctypes.c_void_p), 8, _stream(stream)))
+    return {"dfma_per_s": out[0], "ffma_per_s": out[1], "ex2_per_s": out[2], "rsqrt_per_s": out[3],
+            "sm_mhz": {"dfma": out[4], "ffma": out[5], "ex2": out[6], "rsqrt": out[7]}}

@@ -3,8 +3,8 @@
 // rates are the denominators of the roofline fractions the stage-5 kernels report (the kernels
 // are compute-bound: a few MB of points and vectors against Ntilde^2 kernel evaluations).
 //
-// Each kernel runs a persistent grid of full-occupancy CTAs; every thread advances 8 (float64)
-// or 16 (float32) independent dependency chains, unrolled so that the loop's own counter and
+// Each kernel runs a persistent grid of full-occupancy CTAs; every thread advances 16
+// independent dependency chains, unrolled so that the loop's own counter and
 // branch are a small fraction of the issued instructions.  The chains stay bounded and finite
 // (a contraction for FMA, x -> 2^-x and x -> 1/sqrt(x) for the MUFU functions) and their sum is
 // stored only under a condition the compiler cannot decide, so no operation is removed.
@@ -27,18 +27,32 @@ __device__ __forceinline__ float mufu_rsqrt(float x) {
     return y;
 }
 
+// CTA 0's first thread records the SM clock counter and the global nanosecond timer around its
+// loop (sink[1..4]), from which the host derives the SM clock the launch ran at
+__device__ __forceinline__ void stamp(double* sink, int at) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long c = clock64();
+        unsigned long long ns;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(ns));
+        sink[1 + at] = double(c);
+        sink[3 + at] = double(ns);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) dfma_rate_kernel(int iters, double a, double b, double* sink) {
-    double x[8];
+    double x[16];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = 0.5 + 1e-3 * i + 1e-9 * threadIdx.x;
-#pragma unroll 4
+    for (int i = 0; i < 16; ++i) x[i] = 0.5 + 1e-3 * i + 1e-9 * threadIdx.x;
+    stamp(sink, 0);
+#pragma unroll 8
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], a, b);
+        for (int i = 0; i < 16; ++i) x[i] = fma(x[i], a, b);
     }
+    stamp(sink, 1);
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s += x[i];
+    for (int i = 0; i < 16; ++i) s += x[i];
     if (s == -1.0) sink[0] = s;
 }
 
@@ -46,11 +60,13 @@ __global__ void __launch_bounds__(kThreads) ffma_rate_kernel(int iters, float a,
     float x[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) x[i] = 0.5f + 1e-3f * i + 1e-7f * threadIdx.x;
+    stamp(sink, 0);
 #pragma unroll 8
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) x[i] = fmaf(x[i], a, b);
     }
+    stamp(sink, 1);
     float s = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) s += x[i];
@@ -62,11 +78,13 @@ __global__ void __launch_bounds__(kThreads) mufu_rate_kernel(int iters, float a,
     float x[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) x[i] = a + 1e-3f * i + 1e-7f * threadIdx.x;
+    stamp(sink, 0);
 #pragma unroll 4
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) x[i] = FN == 0 ? mufu_ex2(-x[i]) : mufu_rsqrt(x[i]);
     }
+    stamp(sink, 1);
     float s = 0.f;
 #pragma unroll
     for (int i = 0; i < 16; ++i) s += x[i];
@@ -84,14 +102,14 @@ extern "C" kl_status kl_pipe_rates(double* rates_host, int n, void* stream) {
     const int grid = num_sms() * (2048 / kThreads);
     const double threads = double(grid) * kThreads;
     DevBuf sink;
-    KL_TRY(ensure(sink, sizeof(double)));
+    KL_TRY(ensure(sink, 5 * sizeof(double)));
     double* snk = static_cast<double*>(sink.ptr);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     // operations per launch: chains x iterations x threads
-    const int iters[4] = {2048, 32768, 8192, 4096};
-    const double ops[4] = {8.0 * iters[0] * threads, 16.0 * iters[1] * threads, 16.0 * iters[2] * threads,
+    const int iters[4] = {1024, 32768, 8192, 4096};
+    const double ops[4] = {16.0 * iters[0] * threads, 16.0 * iters[1] * threads, 16.0 * iters[2] * threads,
                            16.0 * iters[3] * threads};
     int launches = 0;
     for (int op = 0; op < 4 && e == cudaSuccess; ++op) {
@@ -111,7 +129,12 @@ extern "C" kl_status kl_pipe_rates(double* rates_host, int n, void* stream) {
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+            if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) {
+                best = ms;
+                double st[5];
+                e = cudaMemcpy(st, snk, sizeof(st), cudaMemcpyDeviceToHost);
+                if (e == cudaSuccess && n >= 8 && st[4] > st[3]) rates_host[4 + op] = 1e3 * (st[2] - st[1]) / (st[4] - st[3]);
+            }
         }
         if (e == cudaSuccess) rates_host[op] = ops[op] / (double(best) * 1e-3);
     }
