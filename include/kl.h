@@ -207,6 +207,15 @@ kl_status kl_get_points(kl_handle h, double* X_host, double* J_host);
  *   method 1 (mixed):  the same iteration with KL_P_FP32 operator applications until the
  *                      residual estimates reach `tol_low`, then block Lanczos with the
  *                      float64 operator from the float32 Ritz vectors (float64 polish).
+ *   method 2 (LOBPCG): block LOBPCG (Knyazev's locally optimal block conjugate gradient,
+ *                      no preconditioner) on a block of max(k, block) vectors (default
+ *                      max(k, 32), at most 48): each step applies the operator to the residual
+ *                      block only and runs Rayleigh-Ritz on span[X, P, R], kept orthonormal in
+ *                      float64 with its products; every application in `precision`.
+ *   method 3 (mixed LOBPCG): method 2 with `low_precision` applications until the residuals
+ *                      reach `tol_low`, then `precision` from the float32 Ritz block.
+ *           For methods 2 and 3, start_dev holds the whole block (N x max(k, block)), ncv,
+ *           polish_block, polish_ncv and nstart are unused, and maxiter bounds the steps.
  *   block   b >= 1 (1 = classic single-vector Lanczos); ncv = basis size (0 = default
  *           max(2k+1, k + 3b) rounded up to a multiple of b; at most 160).
  *   start_dev: optional N x block start block (leading dimension N); NULL = seeded
@@ -386,6 +395,16 @@ kl_status kl_mapped_points(const kl_geometry* geom, const kl_space* space, int64
  * caller-owned) holds the factor.  Call once with Q = NULL to learn the sizes.  Errors:
  * KL_ERR_INVALID_ARG for the rules of kl_create, a null nc/nf, or meshes that are not nested. */
 kl_status kl_prolongation_factor(int deg, int elems_coarse, int elems_fine, int* nc, int* nf, double* Q);
+
+/* Workspace bound of the symmetric stage-5 kernels (float64, float32 and double-float blocks of
+ * up to 8 vectors), which evaluate each kernel value once for the pairs (k, l) and (l, k)
+ * (symmetry of Gamma, listed as future work in the paper's conclusions).  Their partial sums
+ * take one slot of min(nvec, 8) x Ntilde doubles per 256-point tile (one launch, a slot count
+ * growing with Ntilde) while that stays within `bytes` (default 512 MiB), and otherwise a
+ * banded schedule of several launches with a fixed 20 slots, so that the workspace stays linear
+ * in Ntilde (Sec. 5.4: matrix-free storage).  Both give the same sums up to rounding order.
+ * Process-wide; affects workspaces sized after the call.  bytes < 0: KL_ERR_INVALID_ARG. */
+kl_status kl_set_sym_slot_limit(int64_t bytes);
 
 /* Measured throughput of the arithmetic pipes that bound the stage-5 kernels (no counterpart
  * in the paper: the denominators of the roofline fractions that the benchmark reports).

@@ -101,6 +101,7 @@ SIGNATURES = {
                                               ctypes.POINTER(ctypes.c_int), _vp]),
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
     "kl_pipe_rates": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "kl_set_sym_slot_limit": (ctypes.c_int, [_c_int64]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
     "kl_destroy": (None, [_vp]),
@@ -558,3 +559,9 @@ def pipe_rates(stream=None):
     _check(load().kl_pipe_rates(ctypes.cast(out, ctypes.c_void_p), 8, _stream(stream)))
     return {"dfma_per_s": out[0], "ffma_per_s": out[1], "ex2_per_s": out[2], "rsqrt_per_s": out[3],
             "sm_mhz": {"dfma": out[4], "ffma": out[5], "ex2": out[6], "rsqrt": out[7]}}
+
+
+def set_sym_slot_limit(nbytes):
+    """kl_set_sym_slot_limit: largest partial-slot workspace (bytes) of the one-launch symmetric
+    stage-5 schedule; above it the banded schedule with a fixed slot count runs."""
+    _check(load().kl_set_sym_slot_limit(int(nbytes)))

@@ -95,6 +95,8 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32, bool tc64 = false) {
     size_t part = size_t(h->Nt) * groups;
     const size_t dfp = covmv_df_part_doubles(h->Nt, nvec);
     if (dfp > part) part = dfp;
+    const size_t symp = sym_part_doubles(h->Nt, nvec);   // symmetric float64 / float32 / double-float tiles
+    if (symp > part) part = symp;
     if (fp32) {
         const size_t tcp = covmv_tc_part_doubles(h->Nt);
         if (tcp > part) part = tcp;
@@ -710,3 +712,9 @@ void kl_destroy(kl_handle h) {
 }
 
 }  // extern "C"
+
+extern "C" kl_status kl_set_sym_slot_limit(int64_t bytes) {
+    if (bytes < 0) return fail(KL_ERR_INVALID_ARG, "kl_set_sym_slot_limit: negative byte count");
+    set_sym_slot_limit(bytes);
+    return KL_OK;
+}

@@ -100,20 +100,30 @@ covmv_df_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, double*
 }
 
 // ---- symmetric tiling: Gamma(x_k, x_l) = Gamma(x_l, x_k), so each kernel value is evaluated once
-// for both products.  Points are cut into tiles of 256; CTA (I, J), I <= J, evaluates the
-// 256 x 256 block once.  Thread t owns row I*256+t.  For I < J the block is walked in 32-column
-// chunks in a rotated order: at step s lane l evaluates the pair (row l, column (l+s) mod 32) of
-// the chunk, adds g*u_col to its row accumulator and g*u_row to a travelling column accumulator
-// that is handed to lane l-1 after every step, so after 32 steps lane l holds the warp's sum
-// for column l.  The 8 warps' column sums are combined in shared memory.  Row sums go to partial
-// slot J, column sums to slot I, so every output row receives exactly one partial per tile
-// index; the diagonal block (I, I) is evaluated in full, row side only, into slot I.
-constexpr int kSymTile = 256;
+// for both products.  Points are cut into tiles of 256 and each 256 x 256 block is evaluated
+// once; thread t owns row I*256+t.  Off the diagonal the block is walked in 32-column chunks in a
+// rotated order: at step s lane l evaluates the pair (row l, column (l+s) mod 32) of the chunk,
+// adds g*u_col to its row accumulator and g*u_row to a travelling column accumulator that is
+// handed to lane l-1 after every step, so after 32 steps lane l holds the warp's sum for column l.
+// The 8 warps' column sums are combined in shared memory.  The diagonal block (I, I) is
+// evaluated in full, row side only.  Schedules (SymPlan): BAND = false, CTA b takes the pair
+// (I, J), I <= J, of the triangular index b, row sums to slot J and column sums to slot I, so
+// every output row receives exactly one partial per tile index; BAND = true, CTA (I, s) walks its
+// bands of the launch, adding column sums into slot S + (d - d0) and its row sums into slot s.
+constexpr int kSymTile = kSymTileSize;
 
-template <int KIND, int NV>
+__device__ __forceinline__ void sym_decode_tri_df(int64_t bidx, int* I, int* J) {
+    int j = int((sqrt(8.0 * double(bidx) + 1.0) - 1.0) * 0.5);
+    while (int64_t(j) * (j + 1) / 2 > bidx) --j;
+    while (int64_t(j + 1) * (j + 2) / 2 <= bidx) ++j;
+    *J = j;
+    *I = int(bidx - int64_t(j) * (j + 1) / 2);
+}
+
+template <int KIND, int NV, bool BAND>
 __global__ void __launch_bounds__(kSymTile)
 covmv_df_sym_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, double* __restrict__ part,
-                    int nt_tiles, int nv) {
+                    int nv, SymBand bd) {
     extern __shared__ float smem_sym[];
     float* sc = smem_sym;                                   // [6][256] column coordinates
     float2* su = reinterpret_cast<float2*>(smem_sym + 6 * kSymTile);   // [256][NV] column u
@@ -122,13 +132,14 @@ covmv_df_sym_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, dou
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid < 128) stab[tid] = cp.tabdf[tid];
 
-    // triangular decode of the tile pair: b = J (J + 1) / 2 + I, I <= J
-    const int64_t bidx = blockIdx.x;
-    int J = int((sqrt(8.0 * double(bidx) + 1.0) - 1.0) * 0.5);
-    while (int64_t(J) * (J + 1) / 2 > bidx) --J;
-    while (int64_t(J + 1) * (J + 2) / 2 <= bidx) ++J;
-    const int I = int(bidx - int64_t(J) * (J + 1) / 2);
-    (void)nt_tiles;
+    int I, J0;
+    if (BAND) {
+        I = blockIdx.x;
+        J0 = 0;
+    } else {
+        sym_decode_tri_df(blockIdx.x, &I, &J0);
+    }
+    const int nsteps = BAND ? bd.nd : 1;
 
     const int64_t Nt = cp.Nt;
     const int64_t row = int64_t(I) * kSymTile + tid;
@@ -143,116 +154,140 @@ covmv_df_sym_kernel(CovParams cp, const double* __restrict__ U, int64_t ldu, dou
         const float uh = __double2float_rn(u);
         ur[v] = make_float2(uh, __double2float_rn(u - double(uh)));
     }
-    // stage the column tile J
-    {
-        const int64_t c = int64_t(J) * kSymTile + tid;
-        const bool cvalid = c < Nt;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) sc[k * kSymTile + tid] = cvalid ? cp.Pdf[k * cp.ldp + c] : 0.f;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            const double u = (cvalid && v < nv) ? U[v * ldu + c] : 0.0;
-            const float uh = __double2float_rn(u);
-            su[tid * NV + v] = make_float2(uh, __double2float_rn(u - double(uh)));
-        }
-    }
-    __syncthreads();
-
     float ah[NV], al[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         ah[v] = 0.f;
         al[v] = 0.f;
     }
-    if (I == J) {
-#pragma unroll 1
-        for (int j = 0; j < kSymTile; ++j) {
-            float cpj[6];
+    double rsum[NV];   // row sums across the blocks of a band launch
 #pragma unroll
-            for (int k = 0; k < 6; ++k) cpj[k] = sc[k * kSymTile + j];
-            const F2 g = kernel_df<KIND>(rp, cpj, cp.poly_m, stab, stab + 64);
+    for (int v = 0; v < NV; ++v) rsum[v] = 0.0;
+
+    for (int step = 0; step < nsteps; ++step) {
+        int J = J0, d = 0;
+        if (BAND && !sym_band_pair(bd, I, blockIdx.y, step, &J, &d)) continue;
+        const bool diag = BAND ? (d == 0) : (I == J);
+        const int cslot = BAND ? bd.S + (d - bd.d0) : I;
+        __syncthreads();
+        // stage the column tile J
+        {
+            const int64_t c = int64_t(J) * kSymTile + tid;
+            const bool cvalid = c < Nt;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sc[k * kSymTile + tid] = cvalid ? cp.Pdf[k * cp.ldp + c] : 0.f;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const float2 u = su[j * NV + v];
-                const float ph = df::mul(g.h, u.x);
-                float pe = df::fma_(g.h, u.x, -ph);
-                pe = df::fma_(g.h, u.y, pe);
-                pe = df::fma_(g.l, u.x, pe);
-                const F2 s = df::two_sum(ah[v], ph);
-                ah[v] = s.h;
-                al[v] = df::add(al[v], df::add(s.l, pe));
+                const double u = (cvalid && v < nv) ? U[v * ldu + c] : 0.0;
+                const float uh = __double2float_rn(u);
+                su[tid * NV + v] = make_float2(uh, __double2float_rn(u - double(uh)));
             }
         }
-    } else {
-        const int64_t col0 = int64_t(J) * kSymTile;
-#pragma unroll 1
-        for (int q = 0; q < kSymTile / 32; ++q) {
-            float ch[NV], cl[NV];   // travelling column accumulator
+        __syncthreads();
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                ch[v] = 0.f;
-                cl[v] = 0.f;
-            }
+        for (int v = 0; v < NV; ++v) {
+            ah[v] = 0.f;
+            al[v] = 0.f;
+        }
+        if (diag) {
 #pragma unroll 1
-            for (int s = 0; s < 32; ++s) {
-                const int j = q * 32 + ((lane + s) & 31);
+            for (int j = 0; j < kSymTile; ++j) {
                 float cpj[6];
 #pragma unroll
                 for (int k = 0; k < 6; ++k) cpj[k] = sc[k * kSymTile + j];
                 const F2 g = kernel_df<KIND>(rp, cpj, cp.poly_m, stab, stab + 64);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    // row side: g * u_col
                     const float2 u = su[j * NV + v];
-                    float ph = df::mul(g.h, u.x);
+                    const float ph = df::mul(g.h, u.x);
                     float pe = df::fma_(g.h, u.x, -ph);
                     pe = df::fma_(g.h, u.y, pe);
                     pe = df::fma_(g.l, u.x, pe);
-                    F2 sm = df::two_sum(ah[v], ph);
+                    const F2 sm = df::two_sum(ah[v], ph);
                     ah[v] = sm.h;
                     al[v] = df::add(al[v], df::add(sm.l, pe));
-                    // column side: g * u_row
-                    ph = df::mul(g.h, ur[v].x);
-                    pe = df::fma_(g.h, ur[v].x, -ph);
-                    pe = df::fma_(g.h, ur[v].y, pe);
-                    pe = df::fma_(g.l, ur[v].x, pe);
-                    sm = df::two_sum(ch[v], ph);
-                    ch[v] = sm.h;
-                    cl[v] = df::add(cl[v], df::add(sm.l, pe));
-                    ch[v] = __shfl_sync(0xffffffffu, ch[v], (lane + 1) & 31);
-                    cl[v] = __shfl_sync(0xffffffffu, cl[v], (lane + 1) & 31);
                 }
             }
-            // lane holds this warp's partial for column q*32 + lane
+        } else {
+            const int64_t col0 = int64_t(J) * kSymTile;
+#pragma unroll 1
+            for (int q = 0; q < kSymTile / 32; ++q) {
+                float ch[NV], cl[NV];   // travelling column accumulator
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const F2 r = df::fast_two_sum(ch[v], cl[v]);
-                cpart[(warp * 32 + lane) * NV + v] = make_float2(r.h, r.l);
-            }
-            __syncthreads();
-            for (int e = tid; e < 32 * NV; e += kSymTile) {
-                const int cl_ = e / NV, v = e - cl_ * NV;
-                double acc = 0.0;
-                for (int w = 0; w < kSymTile / 32; ++w) {
-                    const float2 p = cpart[(w * 32 + cl_) * NV + v];
-                    acc += double(p.x) + double(p.y);
+                for (int v = 0; v < NV; ++v) {
+                    ch[v] = 0.f;
+                    cl[v] = 0.f;
                 }
-                const int64_t c = col0 + q * 32 + cl_;
-                if (c < Nt && v < nv) part[(int64_t(I) * nv + v) * Nt + c] = acc;
-            }
-            __syncthreads();
+#pragma unroll 1
+                for (int st = 0; st < 32; ++st) {
+                    const int j = q * 32 + ((lane + st) & 31);
+                    float cpj[6];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const F2 r = df::fast_two_sum(ah[v], al[v]);
-                ah[v] = r.h;
-                al[v] = r.l;
+                    for (int k = 0; k < 6; ++k) cpj[k] = sc[k * kSymTile + j];
+                    const F2 g = kernel_df<KIND>(rp, cpj, cp.poly_m, stab, stab + 64);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        // row side: g * u_col
+                        const float2 u = su[j * NV + v];
+                        float ph = df::mul(g.h, u.x);
+                        float pe = df::fma_(g.h, u.x, -ph);
+                        pe = df::fma_(g.h, u.y, pe);
+                        pe = df::fma_(g.l, u.x, pe);
+                        F2 sm = df::two_sum(ah[v], ph);
+                        ah[v] = sm.h;
+                        al[v] = df::add(al[v], df::add(sm.l, pe));
+                        // column side: g * u_row
+                        ph = df::mul(g.h, ur[v].x);
+                        pe = df::fma_(g.h, ur[v].x, -ph);
+                        pe = df::fma_(g.h, ur[v].y, pe);
+                        pe = df::fma_(g.l, ur[v].x, pe);
+                        sm = df::two_sum(ch[v], ph);
+                        ch[v] = sm.h;
+                        cl[v] = df::add(cl[v], df::add(sm.l, pe));
+                        ch[v] = __shfl_sync(0xffffffffu, ch[v], (lane + 1) & 31);
+                        cl[v] = __shfl_sync(0xffffffffu, cl[v], (lane + 1) & 31);
+                    }
+                }
+                // lane holds this warp's partial for column q*32 + lane
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const F2 r = df::fast_two_sum(ch[v], cl[v]);
+                    cpart[(warp * 32 + lane) * NV + v] = make_float2(r.h, r.l);
+                }
+                __syncthreads();
+                for (int e = tid; e < 32 * NV; e += kSymTile) {
+                    const int cl_ = e / NV, v = e - cl_ * NV;
+                    double acc = 0.0;
+                    for (int w = 0; w < kSymTile / 32; ++w) {
+                        const float2 p = cpart[(w * 32 + cl_) * NV + v];
+                        acc += double(p.x) + double(p.y);
+                    }
+                    const int64_t c = col0 + q * 32 + cl_;
+                    if (c < Nt && v < nv) {
+                        double* dst = part + (int64_t(cslot) * nv + v) * Nt + c;
+                        *dst = BAND ? *dst + acc : acc;
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const F2 r = df::fast_two_sum(ah[v], al[v]);
+                    ah[v] = r.h;
+                    al[v] = r.l;
+                }
             }
         }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) rsum[v] += double(ah[v]) + double(al[v]);
     }
     if (rvalid) {
+        const int rslot = BAND ? int(blockIdx.y) : J0;
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-            if (v < nv) part[(int64_t(J) * nv + v) * Nt + row] = double(ah[v]) + double(al[v]);
+            if (v < nv) {
+                double* dst = part + (int64_t(rslot) * nv + v) * Nt + row;
+                *dst = BAND ? *dst + rsum[v] : rsum[v];
+            }
     }
 }
 
@@ -294,28 +329,44 @@ int width_df(int n) {
 
 constexpr int kSymMaxNV = 8;   // widest block that takes the symmetric path
 
-template <int NV>
-cudaError_t launch_sym(const CovParams& cp, const double* U, int64_t ldu, double* part, unsigned pairs,
-                       int nt_tiles, int nv, cudaStream_t s) {
+template <int KIND, int NV>
+cudaError_t sym_df_kind(const CovParams& cp, const double* U, int64_t ldu, double* part, const SymPlan& pl, int nv,
+                        cudaStream_t s) {
     const size_t smem = (size_t(6) * kSymTile + 2 * size_t(kSymTile) * NV + 2 * size_t(kSymTile) * NV) * sizeof(float);
-    switch (cp.kind) {
-        case KL_K_EXP: covmv_df_sym_kernel<KL_K_EXP, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
-        case KL_K_GAUSS: covmv_df_sym_kernel<KL_K_GAUSS, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
-        case KL_K_EXP_SEPARABLE: covmv_df_sym_kernel<KL_K_EXP_SEPARABLE, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
-        default: covmv_df_sym_kernel<KL_K_POLY_TEST, NV><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nt_tiles, nv); break;
+    if (!pl.band) {
+        SymBand bd{pl.T, pl.D, 0, 1, 0};
+        const unsigned pairs = unsigned(int64_t(pl.T) * (pl.T + 1) / 2);
+        covmv_df_sym_kernel<KIND, NV, false><<<pairs, kSymTile, smem, s>>>(cp, U, ldu, part, nv, bd);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(part, 0, size_t(pl.slots) * nv * cp.Nt * sizeof(double), s);
+    for (int t = 0; t < pl.launches && e == cudaSuccess; ++t) {
+        SymBand bd{pl.T, pl.D, t * kSymBandW, kSymBandW / kSymBandS, kSymBandS};
+        covmv_df_sym_kernel<KIND, NV, true><<<dim3(unsigned(pl.T), unsigned(kSymBandS)), kSymTile, smem, s>>>(
+            cp, U, ldu, part, nv, bd);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <int NV>
+cudaError_t launch_sym(const CovParams& cp, const double* U, int64_t ldu, double* part, const SymPlan& pl, int nv,
+                       cudaStream_t s) {
+    switch (cp.kind) {
+        case KL_K_EXP: return sym_df_kind<KL_K_EXP, NV>(cp, U, ldu, part, pl, nv, s);
+        case KL_K_GAUSS: return sym_df_kind<KL_K_GAUSS, NV>(cp, U, ldu, part, pl, nv, s);
+        case KL_K_EXP_SEPARABLE: return sym_df_kind<KL_K_EXP_SEPARABLE, NV>(cp, U, ldu, part, pl, nv, s);
+        default: return sym_df_kind<KL_K_POLY_TEST, NV>(cp, U, ldu, part, pl, nv, s);
+    }
 }
 
 }  // namespace
 
-// partial-sum scratch (doubles) the double-float stage 5 needs for nvec vectors
+// partial-sum scratch (doubles) of the non-symmetric double-float stage 5 (column splits, groups
+// of up to 32 vectors); the symmetric path needs sym_part_doubles
 size_t covmv_df_part_doubles(int64_t Nt, int nvec) {
-    const int64_t nt_tiles = (Nt + kSymTile - 1) / kSymTile;
-    const int64_t g = nvec < kSymMaxNV ? nvec : kSymMaxNV;
-    const size_t sym = size_t(nt_tiles) * size_t(g) * size_t(Nt);
-    const size_t flat = size_t(covmv_df_splits(Nt)) * 32 * size_t(Nt);
-    return sym > flat ? sym : flat;
+    (void)nvec;
+    return size_t(covmv_df_splits(Nt)) * 32 * size_t(Nt);
 }
 
 int covmv_df_splits(int64_t Nt) {
@@ -346,19 +397,19 @@ cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, i
         if (g <= kSymMaxNV && nt_tiles >= 2) {
             // narrow blocks: symmetric tiles halve the kernel evaluations
             const int w = width_df(g);
-            const unsigned pairs = unsigned(int64_t(nt_tiles) * (nt_tiles + 1) / 2);
+            const SymPlan pl = sym_plan(Nt, g);
             switch (w) {
-                case 8: e = launch_sym<8>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
-                case 4: e = launch_sym<4>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
-                case 2: e = launch_sym<2>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
-                default: e = launch_sym<1>(cp, Ug, ldu, part, pairs, nt_tiles, g, s); break;
+                case 8: e = launch_sym<8>(cp, Ug, ldu, part, pl, g, s); break;
+                case 4: e = launch_sym<4>(cp, Ug, ldu, part, pl, g, s); break;
+                case 2: e = launch_sym<2>(cp, Ug, ldu, part, pl, g, s); break;
+                default: e = launch_sym<1>(cp, Ug, ldu, part, pl, g, s); break;
             }
             if (e != cudaSuccess) return e;
-            count_launches(2);
+            count_launches(1 + pl.launches);
             int64_t tot = Nt * g;
             int blocks = int((tot + 255) / 256);
             if (blocks > num_sms() * 8) blocks = num_sms() * 8;
-            covmv_df_reduce<<<blocks, 256, 0, s>>>(part, nt_tiles, Nt, g, Z + int64_t(v0) * ldz, ldz, scale2, J);
+            covmv_df_reduce<<<blocks, 256, 0, s>>>(part, pl.slots, Nt, g, Z + int64_t(v0) * ldz, ldz, scale2, J);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             v0 += g;

@@ -155,6 +155,31 @@ struct Eig {
         return KL_OK;
     }
 
+    // CholQR2 of W with the same right factors applied to a companion block C (the operator
+    // products of W): dst = W R^{-1}, cdst = C R^{-1}.  dst may equal W and cdst may equal C.
+    kl_status cholqr_pair(double* Wb, double* Cb, int b, double* dst, double* cdst, bool* deficient) {
+        int flags[2] = {0, 0};
+        double* cur = Wb;
+        double* ccur = Cb;
+        for (int pass = 0; pass < 2; ++pass) {
+            cudaError_t e = launch_gram(cur, N, b, cur, N, b, N, G(), b, Part(), maxparts, s);
+            if (e != cudaSuccess) return cuda_fail(e, "gram");
+            e = launch_chol_inv(G(), b, b, Rinv(), pass == 0 ? R1() : Rtmp(), Flag() + pass, s);
+            if (e != cudaSuccess) return cuda_fail(e, "chol");
+            double* out = (pass == 0) ? Y() : dst;
+            double* cout = (pass == 0) ? Y2() : cdst;
+            e = launch_gemm_tall(1.0, cur, N, N, b, Rinv(), b, b, 0.0, out, N, s);
+            if (e == cudaSuccess) e = launch_gemm_tall(1.0, ccur, N, N, b, Rinv(), b, b, 0.0, cout, N, s);
+            if (e != cudaSuccess) return cuda_fail(e, "scale");
+            cur = out;
+            ccur = cout;
+        }
+        KL_CUDA(cudaMemcpyAsync(flags, Flag(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        KL_CUDA(cudaStreamSynchronize(s));
+        *deficient = (flags[0] != 0 || flags[1] != 0);
+        return KL_OK;
+    }
+
     // fresh random directions orthogonal to V[:, 0:j] written into dst (N x b)
     kl_status random_orthonormal(double* dst, int b, int j) {
         for (int attempt = 0; attempt < 3; ++attempt) {
@@ -313,7 +338,248 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
     }
 }
 
+// Block LOBPCG (Knyazev's locally optimal block preconditioned conjugate gradient, without a
+// preconditioner) for the nx largest eigenpairs, in the orthonormal-basis form: every step
+// applies the operator to the residual block R = A X - X Theta only, and Rayleigh-Ritz runs on
+// span[X, P, R] (P: the previous step's search directions), kept orthonormal in float64 (CGS2 and
+// CholQR2) together with their operator products, so no product is recomputed.
+// Basis layout: X in V[:, 0:nx], P in V[:, nx:2nx] (once it exists), R after them; the products
+// alike in AV.  On entry V[:, 0:nx] holds an orthonormal start block; with `have_ax` AV[:, 0:nx]
+// already holds its products and Theta its Ritz values (a previous phase).  On exit V[:, 0:nx]
+// holds the Ritz vectors (descending), AV their products, theta/est the values and the residual
+// norms of the k wanted pairs.
+kl_status run_lobpcg(Eig& E, int prec, int nx, int k, double tol, int maxit, bool have_ax, int* iters,
+                     std::vector<double>& theta, std::vector<double>& est, bool* converged) {
+    const int64_t N = E.N;
+    double* V = E.V();
+    double* AV = E.AV();
+    cudaError_t e;
+    *converged = false;
+    theta.assign(3 * nx, 0.0);
+    est.assign(nx, 0.0);
+    if (!have_ax) {
+        // products of the start block and Rayleigh-Ritz on it
+        KL_TRY(E.apply(prec, V, AV, nx));
+        e = launch_gram(V, N, nx, AV, N, nx, N, E.T(), E.mmax, E.Part(), E.maxparts, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        KL_TRY(E.sym_eig(nx));
+        e = launch_gemm_tall(1.0, V, N, N, nx, E.S(), E.mmax, nx, 0.0, E.Y(), N, E.s);
+        if (e == cudaSuccess) e = launch_gemm_tall(1.0, AV, N, N, nx, E.S(), E.mmax, nx, 0.0, E.Y2(), N, E.s);
+        if (e == cudaSuccess) e = launch_copy_block(E.Y(), N, V, N, N, nx, E.s);
+        if (e == cudaSuccess) e = launch_copy_block(E.Y2(), N, AV, N, N, nx, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "ritz block");
+    }
+    int np = 0;   // columns of P
+    for (int it = 0;; ++it) {
+        // ---- convergence of the k wanted pairs ----
+        e = launch_ritz_resid(AV, V, N, N, nx, E.Theta(), E.Part(), E.maxparts, E.Est(), E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
+        KL_CUDA(cudaMemcpyAsync(theta.data(), E.Theta(), nx * sizeof(double), cudaMemcpyDeviceToHost, E.s));
+        KL_CUDA(cudaMemcpyAsync(est.data(), E.Est(), nx * sizeof(double), cudaMemcpyDeviceToHost, E.s));
+        KL_CUDA(cudaStreamSynchronize(E.s));
+        bool ok = true;
+        for (int i = 0; i < k; ++i) {
+            if (!std::isfinite(theta[i]) || !std::isfinite(est[i]))
+                return fail(KL_ERR_NUMERIC, "non-finite Ritz values (NaN or Inf in the start block or the operator)");
+            ok = ok && est[i] <= tol * fabs(theta[i]);
+        }
+        *iters = it;
+        if (ok || it >= maxit) {
+            *converged = ok;
+            return KL_OK;
+        }
+        // ---- residual block, orthonormal against [X, P], and its products ----
+        const int r0 = nx + np;
+        e = launch_ritz_residual_block(AV, V, N, N, nx, E.Theta(), E.W(), N, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "residual block");
+        KL_TRY(E.orthogonalize(E.W(), nx, r0));
+        bool def = false;
+        KL_TRY(E.cholqr(E.W(), nx, V + size_t(r0) * N, &def));
+        if (def) KL_TRY(E.random_orthonormal(V + size_t(r0) * N, nx, r0));
+        KL_TRY(E.apply(prec, V + size_t(r0) * N, AV + size_t(r0) * N, nx));
+        // ---- Rayleigh-Ritz on Z = [X, P, R] ----
+        const int mz = r0 + nx;
+        e = launch_gram(V, N, mz, AV, N, mz, N, E.T(), E.mmax, E.Part(), E.maxparts, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        KL_TRY(E.sym_eig(mz));
+        // new X = Z S[:, 0:nx]; new P = [P, R] S[nx:mz, 0:nx] (the X components dropped); the
+        // products alike.  P goes to the spare columns [mz, mz + nx) first.
+        double* Pn = V + size_t(mz) * N;
+        double* APn = AV + size_t(mz) * N;
+        const double* Sx = E.S() + nx;   // rows nx.. of S (column-major, ld mmax)
+        e = launch_gemm_tall(1.0, V + size_t(nx) * N, N, N, mz - nx, Sx, E.mmax, nx, 0.0, Pn, N, E.s);
+        if (e == cudaSuccess)
+            e = launch_gemm_tall(1.0, AV + size_t(nx) * N, N, N, mz - nx, Sx, E.mmax, nx, 0.0, APn, N, E.s);
+        if (e == cudaSuccess) e = launch_gemm_tall(1.0, V, N, N, mz, E.S(), E.mmax, nx, 0.0, E.Y(), N, E.s);
+        if (e == cudaSuccess) e = launch_gemm_tall(1.0, AV, N, N, mz, E.S(), E.mmax, nx, 0.0, E.Y2(), N, E.s);
+        if (e == cudaSuccess) e = launch_copy_block(E.Y(), N, V, N, N, nx, E.s);
+        if (e == cudaSuccess) e = launch_copy_block(E.Y2(), N, AV, N, N, nx, E.s);
+        if (e == cudaSuccess) e = launch_copy_block(Pn, N, V + size_t(nx) * N, N, N, nx, E.s);
+        if (e == cudaSuccess) e = launch_copy_block(APn, N, AV + size_t(nx) * N, N, N, nx, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "lobpcg update");
+        // ---- X orthonormal again (the rotations' rounding would otherwise accumulate over the
+        // steps), then P orthonormal against X; their products follow every transformation ----
+        bool xdef = false;
+        KL_TRY(E.cholqr_pair(V, AV, nx, V, AV, &xdef));
+        if (xdef) return fail(KL_ERR_NUMERIC, "LOBPCG: the Ritz block lost rank");
+        double* P = V + size_t(nx) * N;
+        double* AP = AV + size_t(nx) * N;
+        KL_TRY(E.orthogonalize(P, nx, nx));                       // P -= X H (twice), H accumulated
+        e = launch_gemm_tall(-1.0, AV, N, N, nx, E.H(), E.mmax, nx, 1.0, AP, N, E.s);
+        if (e != cudaSuccess) return cuda_fail(e, "lobpcg products");
+        bool pdef = false;
+        KL_TRY(E.cholqr_pair(P, AP, nx, P, AP, &pdef));
+        np = pdef ? 0 : nx;
+    }
+}
+
 }  // namespace
+
+// outputs of a solve: eigenvalues, residuals (re-measured with the products carried with the
+// basis, or a fresh float64 application), eigenvectors, statistics and stage-5 event timing
+static kl_status finish_eigs(kl_handle h, Eig& E, const kl_eig_opts& o, int k, double tol, const std::vector<double>& theta,
+                      const std::vector<double>& est, int restarts, double ms32, double* evals_host, double* evecs_dev,
+                      int64_t ldv, kl_eig_info* info, cudaStream_t s,
+                      std::chrono::steady_clock::time_point t0) {
+    const int64_t N = h->N;
+    cudaError_t e;
+    // a bounded wait that gave up inside a tensor-core kernel invalidates the solve
+    if (o.precision == KL_P_TC64 || o.precision == KL_P_TC32) KL_TRY(check_device_status(h, s));
+
+    // ---- outputs ----
+    for (int i = 0; i < k; ++i) evals_host[i] = theta[i];
+    std::vector<double> resid(k, 0.0);
+    for (int i = 0; i < k; ++i) resid[i] = est[i] / std::max(fabs(theta[i]), 1e-300);
+    if (o.verify) {
+        // explicit float64 residuals ||A y - theta y|| / |theta|
+        // verify 1: A~'y from the operator products kept with the basis (AV S);
+        // verify 2: a fresh application with the float64 kernel
+        const double* AY = E.AV();
+        if (o.verify == 2) {
+            KL_TRY(E.apply(KL_P_FP64, E.V(), E.Y(), k));
+            AY = E.Y();
+        }
+        KL_CUDA(cudaMemcpyAsync(E.Theta(), theta.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+        e = launch_ritz_resid(AY, E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
+        if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
+        KL_CUDA(cudaMemcpyAsync(resid.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (evecs_dev) {
+        e = launch_copy_block(E.V(), N, evecs_dev, ldv, N, k, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy eigenvectors");
+    }
+    KL_CUDA(cudaStreamSynchronize(s));
+    int nconv = 0;
+    for (int i = 0; i < k; ++i) nconv += (resid[i] <= tol) ? 1 : 0;
+    if (info) {
+        info->applies = E.applies;
+        info->applies_fp64 = E.applies64;
+        info->applies_df64 = E.appliesdf;
+        info->applies_tc64 = E.appliestc64;
+        info->block_applies = E.block_applies;
+        info->restarts = restarts;
+        info->converged = nconv;
+        for (int i = 0; i < 64; ++i) info->resid[i] = i < k ? resid[i] : 0.0;
+        info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        info->ms_fp32_phase = ms32;
+        info->stage5_calls_fp64 = info->stage5_calls_fp32 = info->stage5_calls_df64 = 0;
+        info->ms_stage5_fp64 = info->ms_stage5_fp32 = info->ms_stage5_df64 = 0.0;
+        info->pairs_fp64 = info->pairs_fp32 = info->pairs_df64 = 0.0;
+        info->stage5_calls_tc64 = 0;
+        info->ms_stage5_tc64 = info->pairs_tc64 = 0.0;
+        const double pairs = double(h->Nt) * double(h->Nt);
+        for (const auto& r : h->prof_rec) {
+            float ms = 0.f;
+            KL_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[r.ev], h->prof_ev[r.ev + 1]));
+            if (r.kind == KL_P_FP64) {
+                info->stage5_calls_fp64 += 1;
+                info->ms_stage5_fp64 += ms;
+                info->pairs_fp64 += pairs;
+            } else if (r.kind == KL_P_DF64) {
+                info->stage5_calls_df64 += 1;
+                info->ms_stage5_df64 += ms;
+                info->pairs_df64 += pairs;
+            } else if (r.kind == KL_P_TC64) {
+                info->stage5_calls_tc64 += 1;
+                info->ms_stage5_tc64 += ms;
+                info->pairs_tc64 += pairs;
+            } else {
+                info->stage5_calls_fp32 += 1;
+                info->ms_stage5_fp32 += ms;
+                info->pairs_fp32 += pairs;
+            }
+        }
+    }
+    if (nconv < k) return fail(KL_ERR_NOT_CONVERGED, "not every wanted eigenpair reached the tolerance");
+    return KL_OK;
+}
+
+// Block LOBPCG solve (opts.method 2: every application in opts.precision; method 3: a first
+// phase with the float32-class operator to tol_low, then the float64-class operator from the
+// float32 Ritz block, whose products are recomputed and whose search directions restart).
+static kl_status lobpcg_impl(kl_handle h, int k, double tol, const kl_eig_opts& o, double* evals_host, double* evecs_dev,
+                      int64_t ldv, kl_eig_info* info, cudaStream_t s, std::chrono::steady_clock::time_point t0) {
+    const int64_t N = h->N;
+    if (o.precision != KL_P_FP64 && o.precision != KL_P_DF64 && o.precision != KL_P_TC64)
+        return fail(KL_ERR_INVALID_ARG, "LOBPCG: opts.precision must be KL_P_FP64, KL_P_DF64 or KL_P_TC64");
+    const int nx = o.block >= k ? o.block : std::max(k, int(std::min<int64_t>(32, N / 3)));
+    if (nx > 48) return fail(KL_ERR_INVALID_ARG, "LOBPCG: block above 48");
+    if (int64_t(3) * nx > N) return fail(KL_ERR_INVALID_ARG, "LOBPCG: 3 x block exceeds the problem dimension");
+    const int maxit = o.maxiter > 0 ? o.maxiter : 1000;
+    h->prof_on = (info != nullptr);
+    h->prof_rec.clear();
+    struct ProfOff {
+        kl_handle h;
+        ~ProfOff() { h->prof_on = false; }
+    } prof_off{h};
+    Eig E;
+    E.h = h;
+    E.s = s;
+    E.N = N;
+    E.seed = o.seed;
+    KL_TRY(E.alloc(3 * nx, nx));
+    cudaError_t e;
+    if (o.start_dev) {
+        e = launch_copy_block(o.start_dev, N, E.W(), N, N, nx, s);
+        if (e == cudaSuccess) e = launch_gram(E.W(), N, nx, E.W(), N, nx, N, E.G(), nx, E.Part(), E.maxparts, s);
+        if (e != cudaSuccess) return cuda_fail(e, "start block");
+        std::vector<double> g(size_t(nx) * nx);
+        KL_CUDA(cudaMemcpyAsync(g.data(), E.G(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        KL_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nx; ++i)
+            if (!std::isfinite(g[size_t(i) * nx + i])) return fail(KL_ERR_NUMERIC, "the start block contains NaN or Inf");
+    } else {
+        e = launch_random_block(E.W(), N, N, nx, o.seed, 0, s);
+        E.rng_offset = uint64_t(N) * nx;
+        if (e != cudaSuccess) return cuda_fail(e, "start block");
+    }
+    bool def = false;
+    KL_TRY(E.cholqr(E.W(), nx, E.V(), &def));
+    if (def) KL_TRY(E.random_orthonormal(E.V(), nx, 0));
+    std::vector<double> theta, est;
+    int iters = 0, iters2 = 0;
+    bool conv = false;
+    double ms32 = 0.0;
+    if (o.method == 2) {
+        KL_TRY(run_lobpcg(E, o.precision, nx, k, tol, maxit, false, &iters, theta, est, &conv));
+    } else {
+        const double tl = o.tol_low > 0.0 ? o.tol_low : (o.precision == KL_P_TC64 ? 1e-6 : 1e-5);
+        const int lowp = (o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32;
+        KL_TRY(run_lobpcg(E, lowp, nx, k, std::max(tl, tol), maxit, false, &iters, theta, est, &conv));
+        if (lowp == KL_P_TC32) KL_TRY(check_device_status(h, s));
+        KL_CUDA(cudaStreamSynchronize(s));
+        ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        // the float32 Ritz block, re-orthonormalised in float64, restarts the iteration with the
+        // float64-class operator (its products are recomputed there)
+        bool defp = false;
+        KL_TRY(E.cholqr(E.V(), nx, E.W(), &defp));
+        e = launch_copy_block(E.W(), N, E.V(), N, N, nx, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy");
+        KL_TRY(run_lobpcg(E, o.precision, nx, k, tol, maxit, false, &iters2, theta, est, &conv));
+    }
+    if (o.precision == KL_P_TC64) KL_TRY(check_device_status(h, s));
+    return finish_eigs(h, E, o, k, tol, theta, est, iters + iters2, ms32, evals_host, evecs_dev, ldv, info, s, t0);
+}
 
 kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, double* evals_host, double* evecs_dev,
                     int64_t ldv, kl_eig_info* info, cudaStream_t s) {
@@ -333,7 +599,8 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     o.low_precision = KL_P_FP32;
     o.nstart = 0;
     if (opts_in) o = *opts_in;
-    if (o.method != 0 && o.method != 1) return fail(KL_ERR_INVALID_ARG, "method must be 0 or 1");
+    if (o.method < 0 || o.method > 3) return fail(KL_ERR_INVALID_ARG, "method must be 0, 1, 2 or 3");
+    if (o.method >= 2) return lobpcg_impl(h, k, tol, o, evals_host, evecs_dev, ldv, info, s, t0);
     // float32-class arithmetic throughout is allowed for the plain method (results accurate to
     // the float32 operator: residual tolerances of about 1e-5 and above, e.g. training data)
     const bool f32_plain = (o.method == 0 && (o.precision == KL_P_FP32 || o.precision == KL_P_TC32));
@@ -461,75 +728,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
     }
 
-    // a bounded wait that gave up inside a tensor-core kernel invalidates the solve
-    if (o.precision == KL_P_TC64 || o.precision == KL_P_TC32) KL_TRY(check_device_status(h, s));
-
-    // ---- outputs ----
-    for (int i = 0; i < k; ++i) evals_host[i] = theta[i];
-    std::vector<double> resid(k, 0.0);
-    for (int i = 0; i < k; ++i) resid[i] = est[i] / std::max(fabs(theta[i]), 1e-300);
-    if (o.verify) {
-        // explicit float64 residuals ||A y - theta y|| / |theta|
-        // verify 1: A~'y from the operator products kept with the basis (AV S);
-        // verify 2: a fresh application with the float64 kernel
-        const double* AY = E.AV();
-        if (o.verify == 2) {
-            KL_TRY(E.apply(KL_P_FP64, E.V(), E.Y(), k));
-            AY = E.Y();
-        }
-        KL_CUDA(cudaMemcpyAsync(E.Theta(), theta.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
-        e = launch_ritz_resid(AY, E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
-        if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
-        KL_CUDA(cudaMemcpyAsync(resid.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    if (evecs_dev) {
-        e = launch_copy_block(E.V(), N, evecs_dev, ldv, N, k, s);
-        if (e != cudaSuccess) return cuda_fail(e, "copy eigenvectors");
-    }
-    KL_CUDA(cudaStreamSynchronize(s));
-    int nconv = 0;
-    for (int i = 0; i < k; ++i) nconv += (resid[i] <= tol) ? 1 : 0;
-    if (info) {
-        info->applies = E.applies;
-        info->applies_fp64 = E.applies64;
-        info->applies_df64 = E.appliesdf;
-        info->applies_tc64 = E.appliestc64;
-        info->block_applies = E.block_applies;
-        info->restarts = restarts;
-        info->converged = nconv;
-        for (int i = 0; i < 64; ++i) info->resid[i] = i < k ? resid[i] : 0.0;
-        info->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        info->ms_fp32_phase = ms32;
-        info->stage5_calls_fp64 = info->stage5_calls_fp32 = info->stage5_calls_df64 = 0;
-        info->ms_stage5_fp64 = info->ms_stage5_fp32 = info->ms_stage5_df64 = 0.0;
-        info->pairs_fp64 = info->pairs_fp32 = info->pairs_df64 = 0.0;
-        info->stage5_calls_tc64 = 0;
-        info->ms_stage5_tc64 = info->pairs_tc64 = 0.0;
-        const double pairs = double(h->Nt) * double(h->Nt);
-        for (const auto& r : h->prof_rec) {
-            float ms = 0.f;
-            KL_CUDA(cudaEventElapsedTime(&ms, h->prof_ev[r.ev], h->prof_ev[r.ev + 1]));
-            if (r.kind == KL_P_FP64) {
-                info->stage5_calls_fp64 += 1;
-                info->ms_stage5_fp64 += ms;
-                info->pairs_fp64 += pairs;
-            } else if (r.kind == KL_P_DF64) {
-                info->stage5_calls_df64 += 1;
-                info->ms_stage5_df64 += ms;
-                info->pairs_df64 += pairs;
-            } else if (r.kind == KL_P_TC64) {
-                info->stage5_calls_tc64 += 1;
-                info->ms_stage5_tc64 += ms;
-                info->pairs_tc64 += pairs;
-            } else {
-                info->stage5_calls_fp32 += 1;
-                info->ms_stage5_fp32 += ms;
-                info->pairs_fp32 += pairs;
-            }
-        }
-    }
-    if (nconv < k) return fail(KL_ERR_NOT_CONVERGED, "not every wanted eigenpair reached the tolerance");
-    return KL_OK;
+    return finish_eigs(h, E, o, k, tol, theta, est, restarts, ms32, evals_host, evecs_dev, ldv, info, s, t0);
 }
 
 }  // namespace kl

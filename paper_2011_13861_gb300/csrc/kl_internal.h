@@ -124,6 +124,45 @@ cudaError_t launch_covmv_tc64(const CovParams& cp, const double* U, int64_t ldu,
                               double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
 size_t covmv_tc64_part_doubles(int64_t Nt);
 size_t covmv_tc64_image_bytes(int64_t Nt);
+// Symmetric stage 5 (each kernel value serves the pairs (k, l) and (l, k)): points are cut into
+// T tiles of 256 and every unordered tile pair is evaluated once.  Two schedules:
+//   * triangular: one launch, one CTA per pair (I <= J); row sums of pair (I, J) go to partial
+//     slot J and column sums to slot I, so T slots of nv x Ntilde doubles are needed;
+//   * band (bounded workspace): the pairs {I, (I + d) mod T}, d = 0 .. floor(T/2), taken in
+//     launches of W consecutive bands d; CTA (I, s) of a launch takes the W/S bands
+//     d0 + s W/S .. and keeps the row sums of tile I in registers across them (row slot s),
+//     while each band's column sums go to column slot S + (d - d0).  Within a launch every
+//     slot position has one writer; the launches run in order on the stream and add into the
+//     slots, which start at zero, so the sum is deterministic with S + W slots whatever Ntilde.
+// The band schedule is used when the triangular one would need more than the slot limit
+// (set_sym_slot_limit, default 512 MiB).
+constexpr int kSymTileSize = 256;
+constexpr int kSymBandW = 16, kSymBandS = 4;
+struct SymPlan {
+    bool band = false;
+    int T = 0;          // tiles
+    int D = 0;          // bands 0 .. D-1 (D = T/2 + 1)
+    int launches = 1;
+    int slots = 0;      // partial slots of nv x Ntilde doubles
+};
+SymPlan sym_plan(int64_t Nt, int nv);
+size_t sym_part_doubles(int64_t Nt, int nv);
+void set_sym_slot_limit(int64_t bytes);
+struct SymBand {        // one launch of the band schedule
+    int T, D, d0, nd, S;
+};
+#ifdef __CUDACC__
+// band d (and tile J) of CTA (I, s), step k of a band launch; false when that step has no pair
+__device__ __forceinline__ bool sym_band_pair(const SymBand& b, int I, int s, int k, int* J, int* d) {
+    const int dd = b.d0 + s * b.nd + k;
+    if (dd >= b.D) return false;
+    if ((b.T & 1) == 0 && 2 * dd == b.T && I >= b.T / 2) return false;   // {I, I + T/2} once
+    *d = dd;
+    *J = (I + dd) % b.T;
+    return true;
+}
+#endif
+
 cudaError_t launch_covmv32_sym(const CovParams& cp, const float* U, int64_t ldu, int nvec, double* Z,
                                int64_t ldz, double scale2, const double* J, double* part, int splits,
                                cudaStream_t s);
@@ -134,7 +173,7 @@ cudaError_t launch_covmv_df(const CovParams& cp, const double* U, int64_t ldu, i
                             int64_t ldz, double scale2, const double* J, double* part, int splits,
                             cudaStream_t s);
 int covmv_df_splits(int64_t Nt);
-size_t covmv_df_part_doubles(int64_t Nt, int nvec);
+size_t covmv_df_part_doubles(int64_t Nt, int nvec);   // flat (non-symmetric) double-float partials
 
 // dense block linear algebra (linalg.cu)
 cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
@@ -160,6 +199,9 @@ cudaError_t launch_ritz_resid(const double* AY, const double* Y, int64_t ld, int
 cudaError_t launch_set_restart_T(double* T, int ldt, int m, const double* theta, int p,
                                  const double* R, int ldr, const double* S, int lds, int srow0,
                                  int b, cudaStream_t s);
+// W[:, c] = AX[:, c] - theta[c] X[:, c] for c < nc (theta on the device)
+cudaError_t launch_ritz_residual_block(const double* AX, const double* X, int64_t ld, int64_t N, int nc,
+                                      const double* theta, double* W, int64_t ldw, cudaStream_t s);
 cudaError_t launch_copy_block(const double* src, int64_t lds, double* dst, int64_t ldd,
                               int64_t rows, int cols, cudaStream_t s);
 cudaError_t launch_to_float(const double* src, int64_t lds, float* dst, int64_t ldd, int64_t rows,

@@ -527,6 +527,17 @@ __global__ void add_inplace_kernel(double* __restrict__ H, const double* __restr
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) H[e] += H2[e];
 }
 
+// W[:, c] = AX[:, c] - theta[c] X[:, c]  (block of Ritz residuals)
+__global__ void ritz_residual_block_kernel(const double* __restrict__ AX, const double* __restrict__ X, int64_t ld,
+                                           int64_t N, int nc, const double* __restrict__ theta,
+                                           double* __restrict__ W, int64_t ldw) {
+    const int64_t total = N * nc;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t c = e / N, i = e - c * N;
+        W[c * ldw + i] = fma(-theta[c], X[c * ld + i], AX[c * ld + i]);
+    }
+}
+
 int grid_for(int64_t work, int threads, int cap) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -717,6 +728,14 @@ cudaError_t launch_fill_T_block(double* T, int ldt, int r0, int c0, const double
 
 cudaError_t launch_add_inplace(double* H, const double* H2, int n, cudaStream_t s) {
     add_inplace_kernel<<<grid_for(n, 256, 64), 256, 0, s>>>(H, H2, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ritz_residual_block(const double* AX, const double* X, int64_t ld, int64_t N, int nc,
+                                      const double* theta, double* W, int64_t ldw, cudaStream_t s) {
+    if (N == 0 || nc == 0) return cudaSuccess;
+    ritz_residual_block_kernel<<<grid_for(N * nc, 256, num_sms() * 8), 256, 0, s>>>(AX, X, ld, N, nc, theta, W, ldw);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -3,10 +3,10 @@
 // rates are the denominators of the roofline fractions the stage-5 kernels report (the kernels
 // are compute-bound: a few MB of points and vectors against Ntilde^2 kernel evaluations).
 //
-// Each kernel runs a persistent grid of full-occupancy CTAs; every thread advances 16
-// independent dependency chains, unrolled so that the loop's own counter and
-// branch are a small fraction of the issued instructions.  The chains stay bounded and finite
-// (a contraction for FMA, x -> 2^-x and x -> 1/sqrt(x) for the MUFU functions) and their sum is
+// Each kernel runs a persistent grid of full-occupancy CTAs; every thread advances independent
+// dependency chains, unrolled so that the loop's own counter and branch are a small fraction of
+// the issued instructions.  The chains stay bounded and finite (a tiny increment or a
+// contraction for FMA, x -> 2^-x and x -> 1/sqrt(x) for the MUFU functions) and their sum is
 // stored only under a condition the compiler cannot decide, so no operation is removed.
 #include "kl_internal.h"
 
@@ -39,20 +39,26 @@ __device__ __forceinline__ void stamp(double* sink, int at) {
     }
 }
 
+// four independent chains a thread, each with its own multiplicands (more chains measured
+// slower on GB300: 1.60 DFMA per SM and cycle with 16 chains, 1.90 with 4, against a pipe peak of 2)
 __global__ void __launch_bounds__(kThreads) dfma_rate_kernel(int iters, double a, double b, double* sink) {
-    double x[16];
+    double x[4], p[4], q[4];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) x[i] = 0.5 + 1e-3 * i + 1e-9 * threadIdx.x;
+    for (int i = 0; i < 4; ++i) {
+        x[i] = 0.5 + 1e-3 * i + 1e-9 * threadIdx.x;
+        p[i] = a * (1.0 + 1e-3 * i);
+        q[i] = b * (1.0 + 1e-4 * i);
+    }
     stamp(sink, 0);
-#pragma unroll 8
+#pragma unroll 16
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) x[i] = fma(x[i], a, b);
+        for (int i = 0; i < 4; ++i) x[i] = fma(p[i], q[i], x[i]);
     }
     stamp(sink, 1);
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) s += x[i];
+    for (int i = 0; i < 4; ++i) s += x[i];
     if (s == -1.0) sink[0] = s;
 }
 
@@ -108,8 +114,8 @@ extern "C" kl_status kl_pipe_rates(double* rates_host, int n, void* stream) {
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     // operations per launch: chains x iterations x threads
-    const int iters[4] = {1024, 32768, 8192, 4096};
-    const double ops[4] = {16.0 * iters[0] * threads, 16.0 * iters[1] * threads, 16.0 * iters[2] * threads,
+    const int iters[4] = {4096, 32768, 8192, 4096};
+    const double ops[4] = {4.0 * iters[0] * threads, 16.0 * iters[1] * threads, 16.0 * iters[2] * threads,
                            16.0 * iters[3] * threads};
     int launches = 0;
     for (int op = 0; op < 4 && e == cudaSuccess; ++op) {
@@ -118,7 +124,7 @@ extern "C" kl_status kl_pipe_rates(double* rates_host, int n, void* stream) {
             e = cudaEventRecord(e0, s);
             if (e != cudaSuccess) break;
             switch (op) {
-                case 0: dfma_rate_kernel<<<grid, kThreads, 0, s>>>(iters[0], 0.999999, 1e-7, snk); break;
+                case 0: dfma_rate_kernel<<<grid, kThreads, 0, s>>>(iters[0], 1e-9, 1e-9, snk); break;
                 case 1: ffma_rate_kernel<<<grid, kThreads, 0, s>>>(iters[1], 0.9999f, 1e-5f, snk); break;
                 case 2: mufu_rate_kernel<0><<<grid, kThreads, 0, s>>>(iters[2], 0.5f, snk); break;
                 default: mufu_rate_kernel<1><<<grid, kThreads, 0, s>>>(iters[3], 0.7f, snk); break;

@@ -70,21 +70,26 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "df64", "tc32", "tc64"])
     ap.add_argument("--nvec", type=int, default=1)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--solve", default=None, choices=[None, "plain", "plain_df", "mixed"],
+    ap.add_argument("--solve", default=None, choices=[None, "plain", "plain_df", "mixed", "lobpcg", "mixed_lobpcg"],
                     help="run one warm-up and one timed eigensolve instead of stage 5 alone")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--tol-low", type=float, default=0.0)
     ap.add_argument("--ncv", type=int, default=0)
+    ap.add_argument("--maxiter", type=int, default=0, help="restart / step bound of --solve (0 = library default)")
     ap.add_argument("--polish-block", type=int, default=0)
     ap.add_argument("--polish-ncv", type=int, default=0)
     ap.add_argument("--low", default="fp32", choices=["fp32", "tc32"])
     ap.add_argument("--mlp-train", action="store_true", help="time training steps of the warm-start network")
     ap.add_argument("--contract", action="store_true", help="time the forward and backward contractions")
     ap.add_argument("--peaks", action="store_true", help="measured pipe rates (kl_pipe_rates)")
+    ap.add_argument("--sym-slot-limit", type=int, default=None,
+                    help="bytes of the one-launch symmetric schedule's slots (kl_set_sym_slot_limit)")
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--accurate", default="df64", choices=["fp64", "df64", "tc64"],
                     help="accurate-phase arithmetic of --solve plain_df / mixed")
     a = ap.parse_args()
+    if a.sym_slot_limit is not None:
+        kl.set_sym_slot_limit(a.sym_slot_limit)
     if a.mlp_train:
         return mlp_train(a)
     if a.contract:
@@ -95,8 +100,8 @@ def main():
     w = inputs.WORKLOADS[a.workload]
     G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
     if a.solve:
-        method = 1 if a.solve == "mixed" else 0
-        block = a.block or (16 if method == 1 else 4)
+        method = {"plain": 0, "plain_df": 0, "mixed": 1, "lobpcg": 2, "mixed_lobpcg": 3}[a.solve]
+        block = a.block or {0: 4, 1: 16, 2: 32, 3: 32}[method]
         prec = kl.KL_P_FP64 if a.solve == "plain" else \
             {"fp64": kl.KL_P_FP64, "df64": kl.KL_P_DF64, "tc64": kl.KL_P_TC64}[a.accurate]
         start = torch.from_numpy(inputs.random_block(G.N, block, seed=1).T.copy()).cuda()
@@ -105,7 +110,8 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             ev, _, info = G.eigs(w["k"], 1e-8, method=method, block=block, start=start, precision=prec,
-                                 tol_low=a.tol_low, ncv=a.ncv, polish_block=a.polish_block,
+                                 tol_low=a.tol_low, ncv=a.ncv, maxiter=a.maxiter, raise_on_nonconv=False,
+                                 polish_block=a.polish_block,
                                  polish_ncv=a.polish_ncv,
                                  low_precision=kl.KL_P_TC32 if a.low == "tc32" else kl.KL_P_FP32)
             e1.record()

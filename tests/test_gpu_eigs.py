@@ -123,3 +123,26 @@ def test_reduced_cube_all_tensor_core(kl):
     info = check(kl, "cube-p2-16^3-exp-L0.5", 20, method=1, block=16, eig_tol=1e-10, precision=4,
                  low_precision=3)
     assert info["applies_tc64"] > 0
+
+
+# ---- block LOBPCG (methods 2 and 3) ----
+
+def test_square_lobpcg(kl):
+    """Block LOBPCG on 16 vectors (10 wanted) against the dense generalized-form oracle."""
+    check(kl, "square-p2-20x20-expsep", 10, method=2, block=16, eig_tol=1e-10)
+
+
+@pytest.mark.parametrize("precision", [0, 4], ids=["fp64", "tc64"])
+def test_reduced_cube_lobpcg(kl, precision):
+    """LOBPCG on a 32-vector block over the 20 wanted pairs of the 5,832-point exponential cube,
+    every application float64 or tensor-core float64-class: eigenvalues, cluster angles and
+    float64-operator residuals against the oracle."""
+    info = check(kl, "cube-p2-16^3-exp-L0.5", 20, method=2, block=32, eig_tol=1e-10, precision=precision)
+    assert info["applies"] % 32 == 0
+
+
+def test_reduced_cube_gaussian_mixed_lobpcg(kl):
+    """Mixed LOBPCG (method 3): float32 applications to 1e-6, then the tensor-core float64-class
+    operator from the float32 Ritz block."""
+    info = check(kl, "cube-p3-16^3-gauss-L0.3", 20, method=3, block=32, eig_tol=1e-10, precision=4)
+    assert 0 < info["applies_tc64"] < info["applies"]

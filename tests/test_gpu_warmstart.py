@@ -70,6 +70,18 @@ def test_forward_matches_oracle(kl, shape):
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "w%d-d%d-b%d" % (s[1], s[2], s[5]))
 def test_loss_and_gradient_match_oracle(kl, shape):
+    """Loss and gradients of the tensor-core network against the oracle, which models every
+    bfloat16 rounding of the kernels.  The two still differ because the kernels form their float32
+    sums in another order than the float64 oracle: where such a sum lies within 2^-24 of a
+    bfloat16 rounding boundary, the rounded factor comes out one bfloat16 unit (2^-8 of itself)
+    apart.  The backward pass rounds the layer input h and the propagated gradient d of every
+    layer, and a flip in d at one layer reaches every earlier layer, so a weight-gradient entry of
+    the first of four layers can carry up to about four such flips per summand: 4 x 2^-8 = 1.6e-2
+    of the sum of its summands' magnitudes, which for these random inputs stays within about the
+    largest gradient entry.  Hence the bar 2e-2 x max|ref| on the largest error.  Flips are rare
+    (most sums are far from a boundary), so the median error sits at the float32 level: the second
+    bar, 1e-3 x max|ref|, is loose for it on purpose and catches a systematic error such as a
+    missing rounding or a transposed product."""
     import torch
     n_in, width, depth, k, n, batch = shape
     rng = np.random.default_rng(12)
