@@ -42,6 +42,12 @@ REDUCED = {"cube-p3-48^3-gauss-L0.3": "cube-p3-16^3-gauss-L0.3",
            "cube-p2-32^3-exp-L0.5": "cube-p2-16^3-exp-L0.5"}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
+# workload and vector count (profiles/stage5_dram_cube-p3-48^3-gauss.md); None where the kernel
+# changed after the capture
+TRAFFIC = {("tc64", "cube-p3-48^3-gauss-L0.3", 32): 61176576.0 + 29777920.0}
+
+
 def flops_per_eval(kind):
     """Algorithmic flops of one kernel evaluation: 3 subtractions, 3 multiplications, 2 additions
     and the scaling by 1/L (9), plus one exponential and, for the exponential kernel, one square
@@ -689,7 +695,8 @@ def main():
             "covmv_tcx_kernel<64> (tensor-core float64-class stage 5, exact bf16 slices)", "alu", w["kernel"], Nt,
             nv64, False, info_c["ms_stage5_tc64"] / nc64, nc64, ffma_flops,
             "measured float32 FMA rate x 2 (kl_pipe_rates, this run): the kernel's double-float "
-            "kernel values and slicing run on the float32 pipe, its bound")
+            "kernel values and slicing run on the float32 pipe, its bound",
+            TRAFFIC.get(("tc64", args.workload, int(round(nv64)))))
     share = {key: (info_c["ms_stage5_" + key] / ms_c) for key in ("fp32", "tc64")}
     dom = max(rl, key=lambda key: share[key]) if rl else None
     roofline = dict(rl[dom]) if dom else None

@@ -406,6 +406,18 @@ kl_status kl_prolongation_factor(int deg, int elems_coarse, int elems_fine, int*
  * Process-wide; affects workspaces sized after the call.  bytes < 0: KL_ERR_INVALID_ARG. */
 kl_status kl_set_sym_slot_limit(int64_t bytes);
 
+/* Schedule of the tensor-core float64-class stage 5 (KL_P_TC64), process-wide.  enable = 0
+ * (default): all Ntilde^2 kernel values are evaluated, sums in a fixed order.  enable != 0: each
+ * value once for both pairs (k, l) and (l, k) (symmetry of Gamma, future work in the paper's
+ * conclusions): row blocks of 128 points meet only the column chunks of their own and later
+ * column blocks, the same bfloat16 value slices feed the row-side product and, read
+ * transposed, the column-side product, and the column sums are added with float64 atomics (their
+ * order of addition, and the last bits of the result, may differ between runs).  It evaluates
+ * half the values but measured slower on GB300 (the column side's drains and 168 extra MMAs per
+ * chunk stall the pipeline), so it stays an option.  Problems with fewer than 256 points always
+ * use the full evaluation.  Affects later calls. */
+kl_status kl_set_tc_symmetric(int enable);
+
 /* Measured throughput of the arithmetic pipes that bound the stage-5 kernels (no counterpart
  * in the paper: the denominators of the roofline fractions that the benchmark reports).
  * Runs four short microbenchmarks on the current device (about 0.1 s in total, synchronous)

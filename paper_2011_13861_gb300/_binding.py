@@ -102,6 +102,7 @@ SIGNATURES = {
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
     "kl_pipe_rates": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "kl_set_sym_slot_limit": (ctypes.c_int, [_c_int64]),
+    "kl_set_tc_symmetric": (ctypes.c_int, [ctypes.c_int]),
     "kl_kernel_launches": (ctypes.c_uint64, []),
     "kl_last_error": (ctypes.c_char_p, []),
     "kl_destroy": (None, [_vp]),
@@ -565,3 +566,9 @@ def set_sym_slot_limit(nbytes):
     """kl_set_sym_slot_limit: largest partial-slot workspace (bytes) of the one-launch symmetric
     stage-5 schedule; above it the banded schedule with a fixed slot count runs."""
     _check(load().kl_set_sym_slot_limit(int(nbytes)))
+
+
+def set_tc_symmetric(enable):
+    """kl_set_tc_symmetric: the tensor-core float64-class stage 5 evaluates each kernel value once
+    for both pairs (True) or all Ntilde^2 values (False, the default)."""
+    _check(load().kl_set_tc_symmetric(1 if enable else 0))

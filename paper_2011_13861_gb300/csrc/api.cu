@@ -103,9 +103,10 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32, bool tc64 = false) {
         KL_TRY(ensure(h->w_tcimg, covmv_tc_image_bytes(h->Nt)));
     }
     if (tc64) {
-        const size_t tcp = covmv_tc64_part_doubles(h->Nt);
+        const bool sym = tc_symmetric_used(h->Nt);
+        const size_t tcp = sym ? covmv_tcs64_part_doubles(h->Nt) : covmv_tc64_part_doubles(h->Nt);
         if (tcp > part) part = tcp;
-        KL_TRY(ensure(h->w_tcimg, covmv_tc64_image_bytes(h->Nt)));
+        KL_TRY(ensure(h->w_tcimg, sym ? covmv_tcs64_image_bytes(h->Nt) : covmv_tc64_image_bytes(h->Nt)));
     }
     KL_TRY(ensure(h->w_part, part * sizeof(double)));
     return KL_OK;
@@ -238,8 +239,8 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
     const double* J = withJ ? h->dJ : nullptr;
     cudaError_t e;
     if (precision == KL_P_TC64) {
-        e = launch_covmv_tc64(cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr), h->w_tcimg.ptr,
-                              h->dStatus, s);
+        e = (tc_symmetric_used(h->Nt) ? launch_covmv_tcs64 : launch_covmv_tc64)(
+            cp, u, ldu, nvec, z, ldz, s2, J, static_cast<double*>(h->w_part.ptr), h->w_tcimg.ptr, h->dStatus, s);
         if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product (tensor cores, float64 class)");
         return KL_OK;
     }
@@ -377,7 +378,8 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
                 e = launch_covmv_df(cp, u64, ld, nvec, b.z, ld, s2, h->dJ, part, covmv_df_splits(h->Nt), s);
                 break;
             case KL_P_TC64:
-                e = launch_covmv_tc64(cp, u64, ld, nvec, b.z, ld, s2, h->dJ, part, h->w_tcimg.ptr, h->dStatus, s);
+                e = (tc_symmetric_used(h->Nt) ? launch_covmv_tcs64 : launch_covmv_tc64)(
+                    cp, u64, ld, nvec, b.z, ld, s2, h->dJ, part, h->w_tcimg.ptr, h->dStatus, s);
                 break;
             case KL_P_TC32:
                 e = launch_covmv_tc(cp, u32, ld, nvec, b.z, ld, s2, h->dJ, part, h->w_tcimg.ptr, h->dStatus, s);
@@ -716,5 +718,10 @@ void kl_destroy(kl_handle h) {
 extern "C" kl_status kl_set_sym_slot_limit(int64_t bytes) {
     if (bytes < 0) return fail(KL_ERR_INVALID_ARG, "kl_set_sym_slot_limit: negative byte count");
     set_sym_slot_limit(bytes);
+    return KL_OK;
+}
+
+extern "C" kl_status kl_set_tc_symmetric(int enable) {
+    set_tc_symmetric(enable != 0);
     return KL_OK;
 }

@@ -506,7 +506,578 @@ size_t part_doubles(int64_t Nt) {
     return size_t(sc.G) * size_t(sc.maxseg) * kNB * kRows;
 }
 
+// ------------------------------------------------------------------------------------------
+// Symmetric float64-class kernel: each kernel value serves the pairs (k, l) and (l, k)
+// ------------------------------------------------------------------------------------------
+// Row block I (128 rows) is paired with the column chunks c >= 4I only: the four chunks of its
+// own 128 x 128 diagonal block (row side only: it holds both (k, l) and (l, k)) and every chunk
+// of the column blocks J > I.  For an off-diagonal chunk the kernel values are used twice:
+//   * row side, as in covmv_tcx_kernel: D1[row][v] += Gamma[row][col] (u/sigma)[col][v];
+//   * column side: D2[v][col] += (u/sigma)[row][v]^T Gamma[row][col] over the block's 128 rows,
+//     with A = the row block's u slices (K-major, vectors on M, rows on K; M = 128 with lanes
+//     32..127 unused) and B = the same kernel-value slices read MN-major (columns on N, rows
+//     on K: the 16-byte rows of the values' core matrices are 8 consecutive columns).
+// The value slices are stored with a uniform core-matrix grid (8-row groups 512 bytes apart,
+// 8-column groups 128 bytes apart) so that both descriptors address them: K-major for the row
+// side (leading byte offset 128, stride byte offset 512), MN-major for the column side (leading
+// byte offset 512 between the K groups of rows, stride byte offset 128 between the N groups of
+// columns).  The column side's level sums over the 128 rows are exact like the row side's over
+// 128 columns; they are drained after every chunk by the four warps that own tensor-memory
+// lanes 0..31 (one per vector), combined in double-float and added into a float64 column-sum
+// array with atomic additions (the only step whose summation order is not fixed), which the
+// final reduction adds to the row sums.
+constexpr int kSymStages = 2;
+constexpr int kRowU = 4 * kBSlice * 6;            // the row block's u slices: 4 chunks x 6 slices x 2 KB
+constexpr int kRowUPad = 4096;                    // lanes 32..127 of the column-side A operand read past the end
+struct Ts {
+    using X = Tx<64>;
+    static constexpr int kOffA = 0;
+    static constexpr int kOffImg = kOffA + kSymStages * X::kAStage;
+    static constexpr int kOffRowU = kOffImg + kSymStages * X::kImg;
+    static constexpr int kOffTab = kOffRowU + kRowU + kRowUPad;
+    static constexpr int kOffBar = kOffTab + 128 * 4;
+    static constexpr int kBarLoaded = 0, kBarFull = kSymStages, kBarEmpty = 2 * kSymStages;
+    static constexpr int kBarBlkDone = 3 * kSymStages, kBarBlkFree = kBarBlkDone + 2;
+    static constexpr int kBarRowU = kBarBlkFree + 2, kBarRowUFree = kBarRowU + 1;
+    static constexpr int kBarD2Done = kBarRowUFree + 1, kBarD2Free = kBarD2Done + 1;
+    static constexpr int kNumBars = kBarD2Free + 1;
+    static constexpr int kOffTmem = kOffBar + 8 * kNumBars;
+    static constexpr int kSmemBytes = kOffTmem + 16;
+    static constexpr int kD2Col = 320;            // column-side accumulators after the row side's 2 x 5 x 32
+    // producers, loader, row-side and column-side MMA issuers
+    static constexpr int kThreads = Tx<64>::kProducers + 96;
+    static_assert(kOffRowU % 16 == 0 && kOffBar % 8 == 0, "bulk-copy and mbarrier alignment");
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+};
+
+// tiles before row block I: sum over I' < I of (len - 4 I')
+__host__ __device__ __forceinline__ int64_t sym_tiles_before(int64_t I, int64_t len) { return I * len - 2 * I * (I - 1); }
+
+// row block and chunk of tile t
+__host__ __device__ __forceinline__ void sym_tile(int64_t t, int64_t len, int64_t* I, int64_t* c) {
+    const double a = double(len) + 2.0;
+    int64_t i = int64_t((a - sqrt(fmax(a * a - 8.0 * double(t), 0.0))) * 0.25);
+    if (i < 0) i = 0;
+    while (i > 0 && sym_tiles_before(i, len) > t) --i;
+    while (sym_tiles_before(i + 1, len) <= t && len - 4 * (i + 1) > 0) ++i;
+    *I = i;
+    *c = 4 * i + (t - sym_tiles_before(i, len));
+}
+
+struct SymSchedule {
+    int64_t len = 0, rb = 0, T = 0, G = 0;
+};
+
+inline cudaError_t make_sym_schedule(int64_t Nt, SymSchedule* sc) {
+    sc->len = (Nt + kChunk - 1) / kChunk;
+    sc->rb = (Nt + kRows - 1) / kRows;
+    sc->T = sym_tiles_before(sc->rb, sc->len);
+    sc->G = int64_t(num_sms());
+    if (sc->G > sc->T) sc->G = sc->T;
+    if (sc->G < 1) sc->G = 1;
+    return cudaSuccess;
+}
+
+// Symmetric float64-class kernel.  part slot b + I (kNB x kRows doubles) holds CTA b's row sums
+// of row block I; zcol[v * Nt + col] receives the column sums (scaled like the row sums).
+template <int KIND>
+__global__ void __launch_bounds__(Ts::kThreads, 1)
+covmv_tcs_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, const double* __restrict__ sigma,
+                 double* __restrict__ part, double* __restrict__ zcol, int64_t len, int64_t T,
+                 int* __restrict__ status) {
+    using X = Tx<64>;
+    constexpr int kSlices = X::kSlices, kAccs = X::kAccs, kAStage = X::kAStage, kImg = X::kImg;
+    constexpr int kCoordBytes = X::kCoordBytes, kProducers = X::kProducers;
+    constexpr int kVpt = X::kVpt;
+    // warps 0..15 producers (warps 0, 4, 8, 12 also drain the column side: tensor-memory lanes
+    // 0..31), 16 loader, 17 row-side MMA issuer (allocates tensor memory), 18 column-side MMA issuer
+    constexpr int kLoaderWarp = 16, kMmaWarp = 17, kMma2Warp = 18;
+    constexpr int kTmemCols = X::kTmemCols, kTmemBuf = 160;   // row side: 2 buffers x 5 x 32 columns
+    constexpr int kOffA = Ts::kOffA, kOffImg = Ts::kOffImg, kOffRowU = Ts::kOffRowU, kOffTab = Ts::kOffTab;
+    constexpr int kOffBar = Ts::kOffBar, kOffTmem = Ts::kOffTmem;
+    constexpr int kBarLoaded = Ts::kBarLoaded, kBarFull = Ts::kBarFull, kBarEmpty = Ts::kBarEmpty;
+    constexpr int kBarBlkDone = Ts::kBarBlkDone, kBarBlkFree = Ts::kBarBlkFree;
+    constexpr int kBarRowU = Ts::kBarRowU, kBarRowUFree = Ts::kBarRowUFree;
+    constexpr int kBarD2Done = Ts::kBarD2Done, kBarD2Free = Ts::kBarD2Free;
+    constexpr uint32_t kIdesc2 = idesc_bf16(kRows, kNB) | (1u << 16);   // B read MN-major
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + kOffBar;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffTmem);
+    float* stab = reinterpret_cast<float*>(smem + kOffTab);
+
+    if (tid < 128) stab[tid] = cp.tabdf[tid];
+    // the pad read by the unused lanes of the column-side A operand: finite (zero) values
+    for (int e = tid; e < kRowUPad / 16; e += blockDim.x)
+        reinterpret_cast<uint4*>(smem + kOffRowU + kRowU)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int st = 0; st < kSymStages; ++st) {
+            mbar_init(bar0 + 8 * (kBarLoaded + st), 1);
+            mbar_init(bar0 + 8 * (kBarFull + st), kProducers);
+            mbar_init(bar0 + 8 * (kBarEmpty + st), 2);   // both MMA issuers commit
+        }
+        for (int p = 0; p < 2; ++p) {
+            mbar_init(bar0 + 8 * (kBarBlkDone + p), 1);
+            mbar_init(bar0 + 8 * (kBarBlkFree + p), kProducers);
+        }
+        mbar_init(bar0 + 8 * kBarRowU, 1);
+        mbar_init(bar0 + 8 * kBarRowUFree, 1);
+        mbar_init(bar0 + 8 * kBarD2Done, 1);
+        mbar_init(bar0 + 8 * kBarD2Free, 4);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t G = gridDim.x;
+    const int64_t t0 = tile_begin(blockIdx.x, T, G);
+    const int ntiles = int(tile_begin(int64_t(blockIdx.x) + 1, T, G) - t0);
+    int I0, c0;
+    {
+        int64_t Iw, cw;
+        sym_tile(t0, len, &Iw, &cw);
+        I0 = int(Iw);
+        c0 = int(cw);
+    }
+    const int lenc = int(len);
+    const int64_t Nt = cp.Nt;
+    bool ok = true;
+
+    if (warp < kLoaderWarp) {
+        // ------------------------------ producers ------------------------------
+        const int r = tid & (kRows - 1), qd = tid / kRows;   // row in block; columns and vectors qd*kVpt..
+        const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+        const bool d2_warp = (warp & 3) == 0;                 // owns tensor-memory lanes 0..31 (the vectors)
+        int nb = 0, qseg = 0;
+        int I = I0, c = c0, rb = -1;
+        float rc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        F2 acc[kVpt];
+#pragma unroll
+        for (int v = 0; v < kVpt; ++v) acc[v] = F2{0.f, 0.f};
+        bool pend = false, pend_seg_end = false;
+        int pend_nb = 0;
+        int pend_rb = 0;
+        bool pend2 = false;                                   // column-side sums of the previous tile
+        int n2p = 0;                                          // column-side uses produced so far
+        int pend2_c = 0;
+        const double cscale = 0.00390625 / double(cp.gscale);
+        // row side: add drain block dnb's level accumulators into the double-float sums; at a
+        // segment end write the row's sums to the segment's partial slot.  False if the wait gave up.
+        auto drain = [&](int dnb, bool dseg_end, int drb) -> bool {
+            const int dp = dnb & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarBlkDone + dp), uint32_t((dnb >> 1) & 1))))
+                return false;
+            fence_after_sync();
+            float L[kAccs][8];
+#pragma unroll
+            for (int a = 0; a < kAccs; ++a)
+                tmem_ld8(tmem + lane_base + uint32_t(dp * kTmemBuf + a * 32 + qd * kVpt), L[a]);
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+#pragma unroll
+                for (int a = 0; a < kAccs; ++a) df_acc(acc[v], L[a][v]);
+                acc[v] = df::fast_two_sum(acc[v].h, acc[v].l);
+            }
+            fence_before_sync();
+            mbar_arrive(bar0 + 8 * (kBarBlkFree + dp));
+            if (dseg_end) {
+                if (int64_t(drb) * kRows + r < Nt) {
+                    // slot b + I of row block I: a CTA's segments take consecutive slots and the next
+                    // CTA starts at or after its last row block, so slots never collide
+                    double* slot = part + (int64_t(blockIdx.x) + drb) * (int64_t(kNB) * kRows) + r;
+#pragma unroll
+                    for (int v = 0; v < kVpt; ++v) {
+                        const int vv = qd * kVpt + v;
+                        if (vv < nv) slot[vv * kRows] = (double(acc[v].h) + double(acc[v].l)) * (sigma[vv] * cscale);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < kVpt; ++v) acc[v] = F2{0.f, 0.f};
+            }
+            return true;
+        };
+        // column side (warps 0, 4, 8, 12): the level sums of chunk dc for vector = lane and columns
+        // 8 (warp / 4) .. + 7, added in float64 (the level sums are exact float32 values, and the
+        // float64 pipe is otherwise idle) into the column-sum array
+        auto drain2 = [&](int dn2, int dc) -> bool {
+            if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * kBarD2Done, uint32_t(dn2 & 1)))) return false;
+            fence_after_sync();
+            const int jq = warp >> 2;
+            uint32_t L[kAccs][8];
+#pragma unroll
+            for (int a = 0; a < kAccs; ++a) tmem_ld8_nowait(tmem + uint32_t(Ts::kD2Col + a * 32 + 8 * jq), L[a]);
+            tmem_ld_wait();
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar0 + 8 * kBarD2Free);
+            if (lane < nv) {
+                const double sc = sigma[lane] * cscale;
+                double* zc = zcol + int64_t(lane) * Nt + int64_t(dc) * kChunk + 8 * jq;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    double x = double(__uint_as_float(L[0][j]));
+#pragma unroll
+                    for (int a = 1; a < kAccs; ++a) x += double(__uint_as_float(L[a][j]));
+                    if (int64_t(dc) * kChunk + 8 * jq + j < Nt) atomicAdd(zc + j, x * sc);
+                }
+            }
+            return true;
+        };
+        for (int i = 0; i < ntiles; ++i) {
+            if (I != rb) {
+                rb = I;
+                const int64_t row = int64_t(rb) * kRows + r;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) rc[k] = row < Nt ? cp.Pdf[k * cp.ldp + row] : 0.f;
+            }
+            if (i == 0 || c == 4 * I) qseg = 0;
+            const int st = i % kSymStages;
+            ok = __all_sync(0xffffffffu, mbar_wait(bar0 + 8 * (kBarLoaded + st), uint32_t((i / kSymStages) & 1)));
+            if (!ok) break;
+            const float* img_c = reinterpret_cast<const float*>(smem + kOffImg + st * kImg);
+            {
+                // the 8 columns qd*8 .. +7, coordinates read as float2 pairs per two columns
+                const int cc = qd * kVpt;
+                uint32_t w[kSlices][4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    float o[2][kSlices];
+                    float2 cp2[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) cp2[k] = *reinterpret_cast<const float2*>(img_c + k * kChunk + cc + e);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float c6[6];
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) c6[k] = h ? cp2[k].y : cp2[k].x;
+                        F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
+                        if (KIND == KL_K_POLY_TEST) {   // the other kernels have gscale = 1
+                            g.h = __fmul_rn(g.h, cp.gscale);
+                            g.l = __fmul_rn(g.l, cp.gscale);
+                        }
+                        slices6(g, o[h]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(o[0][q], o[1][q]);
+                }
+                // uniform core-matrix grid: 8-row groups 512 bytes apart, 8-column groups 128
+                unsigned char* As = smem + kOffA + st * kAStage + (r >> 3) * 512 + (cc >> 3) * 128 + (r & 7) * 16;
+#pragma unroll
+                for (int q = 0; q < kSlices; ++q)
+                    *reinterpret_cast<uint4*>(As + q * kASlice) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            }
+            fence_proxy_async();
+            mbar_arrive(bar0 + 8 * (kBarFull + st));
+
+            // deferred drains of the previous tile's accumulators (the tensor core has had this
+            // tile's evaluation time to finish them)
+            if (pend) {
+                ok = drain(pend_nb, pend_seg_end, pend_rb);
+                if (!ok) break;
+                pend = false;
+            }
+            if (pend2) {
+                if (d2_warp) {
+                    ok = drain2(n2p - 1, pend2_c);
+                    if (!ok) break;
+                }
+                pend2 = false;
+            }
+            const bool seg_end = (i == ntiles - 1) || (c == lenc - 1);
+            const bool blk_end = seg_end || (qseg % kDrainChunks == kDrainChunks - 1);
+            ++qseg;
+            if (blk_end) {
+                pend = true;
+                pend_nb = nb++;
+                pend_seg_end = seg_end;
+                pend_rb = rb;
+            }
+            if (c >= 4 * I + 4) {   // off the diagonal block: the column side follows
+                pend2 = true;
+                pend2_c = c;
+                ++n2p;
+            }
+            if (++c == lenc) {
+                ++I;
+                c = 4 * I;
+            }
+        }
+        if (ok && pend) ok = drain(pend_nb, pend_seg_end, pend_rb);
+        if (ok && pend2 && d2_warp) ok = drain2(n2p - 1, pend2_c);
+    } else if (warp == kLoaderWarp) {
+        // ------------------------------ loader ------------------------------
+        if (lane == 0) {
+            int issued = 0, krow = 0;
+            int I = I0, c = c0, prevI = -1;
+            for (int i = 0; i < ntiles; ++i) {
+                const int st = i % kSymStages;
+                if (i >= kSymStages) {
+                    ok = mbar_wait(bar0 + 8 * (kBarEmpty + st), uint32_t(((i / kSymStages) - 1) & 1));
+                    if (!ok) break;
+                }
+                if (I != prevI) {
+                    // the row block's u slices (chunks 4I .. 4I+3 of the image; the image holds
+                    // zero chunks up to 4 x row blocks) once the previous row block's MMAs are done
+                    if (krow >= 1) {
+                        ok = mbar_wait(bar0 + 8 * kBarRowUFree, uint32_t((krow - 1) & 1));
+                        if (!ok) break;
+                    }
+                    const uint32_t rbar = bar0 + 8 * kBarRowU;
+                    mbar_expect_tx(rbar, uint32_t(kRowU));
+                    for (int q = 0; q < 4; ++q)
+                        bulk_copy_tx(sbase + kOffRowU + q * (kRowU / 4), img + int64_t(4 * I + q) * kImg + kCoordBytes,
+                                     uint32_t(kRowU / 4), rbar);
+                    ++krow;
+                    prevI = I;
+                }
+                bulk_load(sbase + kOffImg + st * kImg, img + int64_t(c) * kImg, kImg, bar0 + 8 * (kBarLoaded + st));
+                issued = i + 1;
+                if (++c == lenc) {
+                    ++I;
+                    c = 4 * I;
+                }
+            }
+            if (!ok) {
+                for (int i = issued - kSymStages; i < issued; ++i)
+                    if (i >= 0) mbar_wait(bar0 + 8 * (kBarLoaded + i % kSymStages), uint32_t((i / kSymStages) & 1));
+                if (krow >= 1) mbar_wait(bar0 + 8 * kBarRowU, uint32_t((krow - 1) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ------------------------------ row-side MMA issuer ------------------------------
+        if (lane == 0) {
+            int nb = 0, qseg = 0, committed = 0;
+            int I = I0, c = c0;
+            // descriptor low words: start address >> 4 in bits 0..13 (addresses stay below 256 KB,
+            // so constant offsets never carry out of the field); high words are constant
+            const uint32_t dA = uint32_t(make_desc(sbase + kOffA, 128, 512));
+            const uint32_t dB = uint32_t(make_desc(sbase + kOffImg + kCoordBytes, 128, 256));
+            const uint32_t hA = uint32_t(make_desc(0, 128, 512) >> 32), hB = uint32_t(make_desc(0, 128, 256) >> 32);
+            for (int i = 0; i < ntiles; ++i) {
+                const int st = i % kSymStages;
+                const uint32_t ph = uint32_t((i / kSymStages) & 1);
+                const bool seg_begin = (i == 0) || (c == 4 * I);
+                if (seg_begin) qseg = 0;
+                const bool blk_begin = seg_begin || (qseg % kDrainChunks == 0);
+                const bool seg_end = (i == ntiles - 1) || (c == lenc - 1);
+                const bool blk_end = seg_end || (qseg % kDrainChunks == kDrainChunks - 1);
+                const int dp = nb & 1;
+                if (blk_begin && nb >= 2) {
+                    ok = mbar_wait(bar0 + 8 * (kBarBlkFree + dp), uint32_t(((nb >> 1) - 1) & 1));
+                    if (!ok) break;
+                }
+                ok = mbar_wait(bar0 + 8 * (kBarFull + st), ph);
+                if (!ok) break;
+                ok = mbar_wait(bar0 + 8 * (kBarLoaded + st), ph);
+                if (!ok) break;
+                fence_after_sync();
+                const uint32_t a0 = dA + uint32_t((st * kAStage) >> 4), b0 = dB + uint32_t((st * kImg) >> 4);
+                const uint32_t d0 = tmem + uint32_t(dp * kTmemBuf);
+                // row side: values K-major (columns on K), u slices of the chunk's columns
+#pragma unroll
+                for (int ks = 0; ks < kChunk / kK; ++ks) {
+#pragma unroll
+                    for (int q = 0; q < X::kProducts; ++q) {
+                        int sl, ul, a;
+                        bool first;
+                        product<64>(q, &sl, &ul, &a, &first);
+                        const bool fresh = first && ks == 0 && blk_begin;
+                        mma_bf16_lo(d0 + uint32_t(a * 32), a0 + uint32_t((sl * kASlice + ks * 256) >> 4), hA,
+                                    b0 + uint32_t((ul * kBSlice + ks * kBSub) >> 4), hB, kIdesc, fresh ? 0u : 1u);
+                    }
+                }
+                mma_commit(bar0 + 8 * (kBarEmpty + st));
+                committed = i + 1;
+                if (blk_end) {
+                    mma_commit(bar0 + 8 * (kBarBlkDone + dp));
+                    ++nb;
+                }
+                ++qseg;
+                if (++c == lenc) {
+                    ++I;
+                    c = 4 * I;
+                }
+            }
+            if (!ok && committed > 0) {
+                const int last = committed - 1;
+                mbar_wait(bar0 + 8 * (kBarEmpty + last % kSymStages), uint32_t((last / kSymStages) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp == kMma2Warp) {
+        // ------------------------------ column-side MMA issuer ------------------------------
+        if (lane == 0) {
+            int committed = 0, krow = 0, n2 = 0;
+            int I = I0, c = c0, curI = -1;
+            const uint32_t dU = uint32_t(make_desc(sbase + kOffRowU, 128, 256));
+            const uint32_t dV = uint32_t(make_desc(sbase + kOffA, 512, 128));
+            const uint32_t hU = uint32_t(make_desc(0, 128, 256) >> 32), hV = uint32_t(make_desc(0, 512, 128) >> 32);
+            for (int i = 0; i < ntiles; ++i) {
+                const int st = i % kSymStages;
+                const uint32_t ph = uint32_t((i / kSymStages) & 1);
+                const bool seg_end = (i == ntiles - 1) || (c == lenc - 1);
+                const bool offdiag = c >= 4 * I + 4;
+                if (I != curI) {
+                    ok = mbar_wait(bar0 + 8 * kBarRowU, uint32_t(krow & 1));
+                    if (!ok) break;
+                    ++krow;
+                    curI = I;
+                }
+                // every tile, also on the diagonal: this issuer's Empty commit for tile i must not
+                // come before the stage holds tile i (it would complete an earlier use's phase)
+                ok = mbar_wait(bar0 + 8 * (kBarFull + st), ph);
+                if (!ok) break;
+                ok = mbar_wait(bar0 + 8 * (kBarLoaded + st), ph);
+                if (!ok) break;
+                if (offdiag) {
+                    if (n2 >= 1) {
+                        ok = mbar_wait(bar0 + 8 * kBarD2Free, uint32_t((n2 - 1) & 1));
+                        if (!ok) break;
+                    }
+                    fence_after_sync();
+                    // u slices of the row block (vectors on M, rows on K) times the values read
+                    // MN-major (rows on K, columns on N)
+                    const uint32_t v0 = dV + uint32_t((st * kAStage) >> 4);
+                    const uint32_t d0 = tmem + uint32_t(Ts::kD2Col);
+#pragma unroll
+                    for (int kk = 0; kk < kRows / kK; ++kk) {
+#pragma unroll
+                        for (int q = 0; q < X::kProducts; ++q) {
+                            int sl, ul, a;
+                            bool first;
+                            product<64>(q, &sl, &ul, &a, &first);
+                            mma_bf16_lo(d0 + uint32_t(a * 32),
+                                        dU + uint32_t(((kk >> 1) * (kRowU / 4) + ul * kBSlice + (kk & 1) * kBSub) >> 4), hU,
+                                        v0 + uint32_t((sl * kASlice + kk * 1024) >> 4), hV, kIdesc2,
+                                        (first && kk == 0) ? 0u : 1u);
+                        }
+                    }
+                    mma_commit(bar0 + 8 * kBarD2Done);
+                    ++n2;
+                }
+                // every tile: the stage is free of this issuer's reads (at once on the diagonal)
+                mma_commit(bar0 + 8 * (kBarEmpty + st));
+                committed = i + 1;
+                if (seg_end) mma_commit(bar0 + 8 * kBarRowUFree);
+                if (++c == lenc) {
+                    ++I;
+                    c = 4 * I;
+                }
+            }
+            if (!ok && committed > 0) {
+                const int last = committed - 1;
+                mbar_wait(bar0 + 8 * (kBarEmpty + last % kSymStages), uint32_t((last / kSymStages) & 1));
+            }
+        }
+        __syncwarp();
+    }
+    fence_before_sync();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    fence_after_sync();
+    if (!ok && tid == 0) atomicExch(status, int(KL_ERR_TIMEOUT));
+    if (warp == kMmaWarp) tmem_dealloc(tmem, kTmemCols);
+}
+// z[v][r] = scale2 J[r] (row sums from the partial slots of r's row block, CTAs in increasing order,
+// + the column sums)
+__global__ void tcs_reduce(const double* __restrict__ part, const double* __restrict__ zcol, int64_t Nt, int nv,
+                           int64_t len, int64_t T, int64_t G, double* __restrict__ Z, int64_t ldz, double scale2,
+                           const double* __restrict__ J) {
+    const int64_t total = Nt * nv;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t v = idx / Nt, r = idx - v * Nt;
+        const int64_t rb = r / kRows, rl = r - rb * kRows;
+        const int64_t tlo = sym_tiles_before(rb, len), thi = sym_tiles_before(rb + 1, len) - 1;
+        const int64_t blo = ((tlo + 1) * G - 1) / T, bhi = ((thi + 1) * G - 1) / T;
+        double acc = 0.0;
+        for (int64_t b = blo; b <= bhi; ++b) acc += part[((b + rb) * kNB + v) * kRows + rl];
+        acc += zcol[v * Nt + r];
+        acc *= scale2;
+        if (J) acc *= J[r];
+        Z[v * ldz + r] = acc;
+    }
+}
+
+template <int KIND>
+cudaError_t launch_tcs_kind(const CovParams& cp, const unsigned char* im, int g, const double* sigma, double* slots,
+                            double* zcol, const SymSchedule& sc, int* status, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(covmv_tcs_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Ts::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    covmv_tcs_kernel<KIND><<<unsigned(sc.G), Ts::kThreads, Ts::kSmemBytes, s>>>(cp, im, g, sigma, slots, zcol,
+                                                                                      sc.len, sc.T, status);
+    return cudaGetLastError();
+}
+
+bool g_tc_symmetric = false;
+
 }  // namespace
+
+void set_tc_symmetric(bool on) { g_tc_symmetric = on; }
+bool tc_symmetric_used(int64_t Nt) { return g_tc_symmetric && Nt >= 2 * kRows; }
+
+// workspace of the symmetric float64-class kernel: G + row blocks partial slots, then the column
+// sums (32 x Ntilde doubles); the image holds 4 chunks per row block
+size_t covmv_tcs64_part_doubles(int64_t Nt) {
+    SymSchedule sc;
+    if (Nt <= 0 || make_sym_schedule(Nt, &sc) != cudaSuccess) return 0;
+    return size_t(sc.G + sc.rb) * kNB * kRows + size_t(Nt) * kNB;
+}
+size_t covmv_tcs64_image_bytes(int64_t Nt) {
+    return size_t(4 * ((Nt + kRows - 1) / kRows)) * Tx<64>::kImg + kNB * sizeof(double);
+}
+
+cudaError_t launch_covmv_tcs64(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
+                               double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s) {
+    using X = Tx<64>;
+    const int64_t Nt = cp.Nt;
+    if (Nt == 0 || nvec == 0) return cudaSuccess;
+    SymSchedule sc;
+    cudaError_t e = make_sym_schedule(Nt, &sc);
+    if (e != cudaSuccess) return e;
+    unsigned char* im = static_cast<unsigned char*>(img);
+    const int64_t nchunks = 4 * sc.rb;
+    double* sigma = reinterpret_cast<double*>(im + nchunks * X::kImg);
+    double* slots = part;
+    double* zcol = part + (sc.G + sc.rb) * kNB * kRows;
+    const int img_blocks = int(nchunks < int64_t(num_sms()) * 8 ? nchunks : int64_t(num_sms()) * 8);
+    for (int v0 = 0; v0 < nvec; v0 += kNB) {
+        const int g = (nvec - v0) < kNB ? (nvec - v0) : kNB;
+        const double* Ug = U + int64_t(v0) * ldu;
+        tcx_scale_kernel<double><<<g, 256, 0, s>>>(Ug, ldu, Nt, sigma);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        tcx_image_kernel<64, double><<<img_blocks, 6 * kChunk, 0, s>>>(cp.Pdf, cp.ldp, Nt, Ug, ldu, g, sigma, im,
+                                                                      nchunks);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(zcol, 0, size_t(Nt) * g * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        switch (cp.kind) {
+            case KL_K_EXP: e = launch_tcs_kind<KL_K_EXP>(cp, im, g, sigma, slots, zcol, sc, status, s); break;
+            case KL_K_GAUSS: e = launch_tcs_kind<KL_K_GAUSS>(cp, im, g, sigma, slots, zcol, sc, status, s); break;
+            case KL_K_EXP_SEPARABLE:
+                e = launch_tcs_kind<KL_K_EXP_SEPARABLE>(cp, im, g, sigma, slots, zcol, sc, status, s);
+                break;
+            default: e = launch_tcs_kind<KL_K_POLY_TEST>(cp, im, g, sigma, slots, zcol, sc, status, s);
+        }
+        if (e != cudaSuccess) return e;
+        const int64_t tot = Nt * g;
+        int blocks = int((tot + 255) / 256);
+        if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+        tcs_reduce<<<blocks, 256, 0, s>>>(slots, zcol, Nt, g, sc.len, sc.T, sc.G, Z + int64_t(v0) * ldz, ldz,
+                                          scale2, J);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        count_launches(4);
+    }
+    return cudaSuccess;
+}
 
 size_t covmv_tc64_part_doubles(int64_t Nt) { return part_doubles<64>(Nt); }
 size_t covmv_tc_part_doubles(int64_t Nt) { return part_doubles<32>(Nt); }

@@ -124,6 +124,14 @@ cudaError_t launch_covmv_tc64(const CovParams& cp, const double* U, int64_t ldu,
                               double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
 size_t covmv_tc64_part_doubles(int64_t Nt);
 size_t covmv_tc64_image_bytes(int64_t Nt);
+// the symmetric float64-class tensor-core stage 5 (each kernel value serves both pairs; column
+// sums added with atomics); used for KL_P_TC64 when tc_symmetric_used(Ntilde)
+cudaError_t launch_covmv_tcs64(const CovParams& cp, const double* U, int64_t ldu, int nvec, double* Z, int64_t ldz,
+                               double scale2, const double* J, double* part, void* img, int* status, cudaStream_t s);
+size_t covmv_tcs64_part_doubles(int64_t Nt);
+size_t covmv_tcs64_image_bytes(int64_t Nt);
+void set_tc_symmetric(bool on);
+bool tc_symmetric_used(int64_t Nt);
 // Symmetric stage 5 (each kernel value serves the pairs (k, l) and (l, k)): points are cut into
 // T tiles of 256 and every unordered tile pair is evaluated once.  Two schedules:
 //   * triangular: one launch, one CTA per pair (I <= J); row sums of pair (I, J) go to partial

@@ -82,6 +82,8 @@ def main():
     ap.add_argument("--mlp-train", action="store_true", help="time training steps of the warm-start network")
     ap.add_argument("--contract", action="store_true", help="time the forward and backward contractions")
     ap.add_argument("--peaks", action="store_true", help="measured pipe rates (kl_pipe_rates)")
+    ap.add_argument("--tc-sym", action="store_true",
+                    help="tensor-core float64 class: symmetric schedule (kl_set_tc_symmetric(1))")
     ap.add_argument("--sym-slot-limit", type=int, default=None,
                     help="bytes of the one-launch symmetric schedule's slots (kl_set_sym_slot_limit)")
     ap.add_argument("--batch", type=int, default=64)
@@ -90,6 +92,8 @@ def main():
     a = ap.parse_args()
     if a.sym_slot_limit is not None:
         kl.set_sym_slot_limit(a.sym_slot_limit)
+    if a.tc_sym:
+        kl.set_tc_symmetric(True)
     if a.mlp_train:
         return mlp_train(a)
     if a.contract:
