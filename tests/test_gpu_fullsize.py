@@ -158,3 +158,28 @@ def test_gaussian_cube_at_133k_points_kronecker_spectrum(kl):
     # the same problem with the double-float polish agrees
     ev2, _, _ = G.eigs(20, 1e-8, method=1, block=16, start=start, precision=kl.KL_P_DF64, want_vectors=False)
     assert np.abs(ev2 - vals[:20]).max() / vals[0] < 1e-10
+
+
+@pytest.fixture(scope="module")
+def cube_gauss_133k(kl):
+    w = inputs.WORKLOADS["cube-p3-48^3-gauss-L0.3"]
+    P = ibq.Problem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    return P, G
+
+
+@pytest.mark.parametrize("prec,nvec,tol", [(0, 4, 1e-12), (2, 8, 1e-12), (4, 32, 1e-12), (1, 16, 2e-6), (1, 5, 2e-6)],
+                         ids=["fp64-4-banded", "df64-8-banded", "tc64-32", "fp32-16-splits", "fp32-5-banded"])
+def test_stage5_sampled_rows_at_133k_points(kl, cube_gauss_133k, prec, nvec, tol):
+    """At 132,651 points the symmetric float64, double-float and float32 kernels run the banded
+    schedule (fixed 20 partial slots: 17 launches of 16 bands), the 16-vector float32 kernel its
+    wave-aware column splits with shared-memory float64 sums, and the tensor-core float64 class
+    its full evaluation; sampled rows, including the first and the last, against the oracle."""
+    import torch
+    P, G = cube_gauss_133k
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, nvec, seed=31 + nvec)
+    z = G.covmv(torch.from_numpy(u.T.copy()).cuda(), precision=prec).cpu().numpy().T
+    rows = np.concatenate([np.random.default_rng(8).choice(P.Nt, size=40, replace=False), [0, P.Nt - 1]])
+    ref = P.stage5(X, u, row_index=rows)
+    assert rel(z[rows], ref) < tol

@@ -199,3 +199,25 @@ def test_to_bspline(kl):
     v = G.to_bspline(torch.from_numpy(vp.T.copy()).cuda()).cpu().numpy().T
     Z = P.kron("Z")
     assert np.abs(v.T @ Z @ v - vp.T @ vp).max() < 1e-12 * np.abs(vp.T @ vp).max()
+
+
+@pytest.mark.parametrize("dim,p,ne", [(1, 1, 1), (2, 1, [1, 2]), (3, 1, 1), (1, 2, 253)],
+                         ids=["2pts", "6pts", "8pts", "255pts"])
+def test_tiny_problems_every_precision(kl, dim, p, ne):
+    """Degenerate sizes: 2 to 8 points (one partial tile in every kernel, a single row block on
+    the tensor cores) and 255 points (one point short of two symmetric tiles), 3 vectors, every
+    stage-5 arithmetic against the oracle."""
+    import torch
+    P = ibq.Problem(dim, p, ne, kernel="exp", L=0.7, sigma=0.9)
+    G = kl.KLProblem(dim, p, ne, kernel="exp", L=0.7, sigma=0.9)
+    X, _ = P.points_and_J()
+    u = inputs.random_block(P.Nt, 3, seed=77)
+    ref = P.stage5(X, u)
+    ud = torch.from_numpy(u.T.copy()).cuda()
+    for prec, tol in ((kl.KL_P_FP64, FP64_TOL), (kl.KL_P_DF64, FP64_TOL), (kl.KL_P_TC64, FP64_TOL),
+                      (kl.KL_P_FP32, FP32_TOL), (kl.KL_P_TC32, FP32_TOL)):
+        z = G.covmv(ud, precision=prec).cpu().numpy().T
+        assert rel(z, ref) < tol, (prec, rel(z, ref))
+    v = inputs.random_block(P.N, 2, seed=78)
+    y = G.apply(torch.from_numpy(v.T.copy()).cuda()).cpu().numpy().T
+    assert rel(y, P.dense_operator() @ v) < FP64_TOL
