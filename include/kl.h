@@ -205,8 +205,9 @@ kl_status kl_get_points(kl_handle h, double* X_host, double* J_host);
  *   method 0 (plain):  thick-restart block Lanczos, every operator application in
  *                      float64 (the paper's implicitly restarted Lanczos, Sec. 4.4.2).
  *   method 1 (mixed):  the same iteration with KL_P_FP32 operator applications until the
- *                      residual estimates reach `tol_low`, then block Lanczos with the
- *                      float64 operator from the float32 Ritz vectors (float64 polish).
+ *                      residual estimates reach `tol_low`, then block Lanczos from the
+ *                      float32 Ritz vectors whose first block takes the float64 operator
+ *                      (float64 polish; see polish_accurate).
  *   method 2 (LOBPCG): block LOBPCG (Knyazev's locally optimal block conjugate gradient,
  *                      no preconditioner) on a block of max(k, block) vectors (default
  *                      max(k, 32), at most 48): each step applies the operator to the residual
@@ -246,6 +247,12 @@ typedef struct {
                              * first-phase operator is applied to them once, and the iteration
                              * starts from their `block` leading Ritz vectors (Rayleigh-Ritz
                              * compression of a wider warm-start subspace). */
+    int polish_accurate;    /* method 1: 0 (default) = only the polish's first application (on the
+                             * float32 Ritz block) in `precision`, its correction blocks in
+                             * `low_precision`: their coefficients in the refined Ritz vectors are
+                             * of the size of the float32 residual, so the float32 operator's error
+                             * reaches the residuals only as a product of the two (~1e-13 of
+                             * ||A~'||); 1 = every polish application in `precision` */
 } kl_eig_opts;
 
 typedef struct {
@@ -420,11 +427,13 @@ kl_status kl_set_tc_symmetric(int enable);
 
 /* Measured throughput of the arithmetic pipes that bound the stage-5 kernels (no counterpart
  * in the paper: the denominators of the roofline fractions that the benchmark reports).
- * Runs four short microbenchmarks on the current device (about 0.1 s in total, synchronous)
+ * Runs four (five) short microbenchmarks on the current device (about 0.1 s in total, synchronous)
  * and writes, as operations per second for the whole GPU: rates_host[0] float64 FMA,
  * [1] float32 FMA, [2] MUFU ex2 (float32), [3] MUFU rsqrt (float32); with n >= 8 also the SM
  * clock in MHz that each of the four timed launches ran at ([4..7], from the SM cycle counter
- * and the global timer of one thread).  n >= 4, else KL_ERR_INVALID_ARG. */
+ * and the global timer of one thread); with n >= 10 also the packed float32 pair FMA
+ * (fma.rn.f32x2, counted as two FMAs) in [8] and its clock in [9].  n >= 4, else
+ * KL_ERR_INVALID_ARG. */
 kl_status kl_pipe_rates(double* rates_host, int n, void* stream);
 
 /* Failure-detection self-test (no counterpart in the paper): one GPU thread waits on an

@@ -37,7 +37,7 @@ class KLEigOpts(ctypes.Structure):
                 ("maxiter", ctypes.c_int), ("seed", ctypes.c_uint64), ("start_dev", _vp),
                 ("tol_low", ctypes.c_double), ("verify", ctypes.c_int), ("precision", ctypes.c_int),
                 ("polish_block", ctypes.c_int), ("polish_ncv", ctypes.c_int), ("low_precision", ctypes.c_int),
-                ("nstart", ctypes.c_int)]
+                ("nstart", ctypes.c_int), ("polish_accurate", ctypes.c_int)]
 
 
 class KLEigInfo(ctypes.Structure):
@@ -335,7 +335,7 @@ class KLProblem:
 
     def eigs(self, k, tol=1e-8, method=0, block=1, ncv=0, maxiter=0, seed=1, start=None, tol_low=0.0,
              verify=True, want_vectors=True, stream=None, raise_on_nonconv=True, precision=KL_P_FP64,
-             polish_block=0, polish_ncv=0, low_precision=KL_P_FP32):
+             polish_block=0, polish_ncv=0, low_precision=KL_P_FP32, polish_accurate=False):
         """The k largest eigenpairs (descending).  Returns (evals numpy, evecs (k, N) tensor or None, info dict)."""
         import numpy as np
         import torch
@@ -350,7 +350,7 @@ class KLProblem:
         opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1),
                          _ptr(start) if start is not None else None, float(tol_low), 1 if verify else 0,
                          int(precision), int(polish_block), int(polish_ncv), int(low_precision),
-                         nstart if nstart > int(block) else 0)
+                         nstart if nstart > int(block) else 0, 1 if polish_accurate else 0)
         ev = np.zeros(k)
         vecs = None
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -381,7 +381,8 @@ def apply_batched(problems, vs, precision=KL_P_DF64, stream=None):
 
 
 def eigs_batched(problems, k, tol=1e-8, method=0, block=4, ncv=0, maxiter=0, seed=1, tol_low=0.0, verify=True,
-                 want_vectors=True, precision=KL_P_DF64, polish_block=0, polish_ncv=0, low_precision=KL_P_FP32):
+                 want_vectors=True, precision=KL_P_DF64, polish_block=0, polish_ncv=0, low_precision=KL_P_FP32,
+                 polish_accurate=False):
     """kl_eigs_batched: the k largest eigenpairs of every problem, solved together.  Returns
     (evals (count, k) numpy, list of (k, N_i) tensors or None, list of info dicts, statuses, batch info)."""
     import numpy as np
@@ -389,7 +390,7 @@ def eigs_batched(problems, k, tol=1e-8, method=0, block=4, ncv=0, maxiter=0, see
     n = len(problems)
     opts = KLEigOpts(int(method), int(block), int(ncv), int(maxiter), int(seed) & (2 ** 64 - 1), None,
                      float(tol_low), 1 if verify else 0, int(precision), int(polish_block), int(polish_ncv),
-                     int(low_precision))
+                     int(low_precision), 0, 1 if polish_accurate else 0)
     ev = np.zeros((n, k))
     dev = torch.device("cuda", torch.cuda.current_device())
     vecs = [torch.empty((k, p.N), dtype=torch.float64, device=dev) for p in problems] if want_vectors else None
@@ -555,11 +556,13 @@ def wait_selftest(seconds=0.05, stream=None):
 
 def pipe_rates(stream=None):
     """kl_pipe_rates: measured operations per second of the float64 FMA, float32 FMA, MUFU ex2
-    and MUFU rsqrt pipes of the current GPU, and the SM clock each launch ran at (dict)."""
-    out = (ctypes.c_double * 8)()
-    _check(load().kl_pipe_rates(ctypes.cast(out, ctypes.c_void_p), 8, _stream(stream)))
+    and MUFU rsqrt pipes of the current GPU, the packed float32 pair FMA (FMAs per second), and
+    the SM clock each launch ran at (dict)."""
+    out = (ctypes.c_double * 10)()
+    _check(load().kl_pipe_rates(ctypes.cast(out, ctypes.c_void_p), 10, _stream(stream)))
     return {"dfma_per_s": out[0], "ffma_per_s": out[1], "ex2_per_s": out[2], "rsqrt_per_s": out[3],
-            "sm_mhz": {"dfma": out[4], "ffma": out[5], "ex2": out[6], "rsqrt": out[7]}}
+            "ffma2_per_s": out[8],
+            "sm_mhz": {"dfma": out[4], "ffma": out[5], "ex2": out[6], "rsqrt": out[7], "ffma2": out[9]}}
 
 
 def set_sym_slot_limit(nbytes):

@@ -14,8 +14,9 @@
 //               end with an explicit float64 application when requested.
 //
 // Method 1 ("mixed") runs the iteration with the float32 stage-5 kernel until the estimates
-// reach tol_low, then continues from the float32 Ritz vectors with the float64 operator in
-// one wide block (b = number of kept vectors), which converges in a few block steps.
+// reach tol_low, then continues from the float32 Ritz vectors in one wide block (b = number
+// of kept vectors), which converges in a few block steps: the first block takes the float64
+// (-class) operator, the correction blocks after it the float32 one (see run_phase).
 // Everything stays on the device; per restart the host reads back the Ritz values and
 // residual estimates of the wanted pairs (a few hundred bytes).
 #include <math.h>
@@ -219,12 +220,25 @@ struct Phase {
     bool early_rr;     // Rayleigh-Ritz after every block step (used for the float64 polish)
     int maxrestart;
     int exit_vecs;     // Ritz vectors left in V[:, 0:exit_vecs] on exit (>= k)
+    int prec_next;     // arithmetic of every application after the phase's first (see run_phase)
 };
 
 // Runs one thick-restart block Lanczos phase.  On entry V[:, 0:j0] holds an orthonormal basis
 // whose last b columns form the active block and T[0:j0, 0:j0] = V^T A V is valid for all
 // but the active block's column (the next expansion recomputes it).  On exit V[:, 0:k] holds
 // the k wanted Ritz vectors, Theta their values and est[] the residual estimates.
+//
+// Correction blocks in lower precision (P.prec_next != P.prec, the polish of the mixed method):
+// only the phase's first application (the float32 phase's Ritz block X) takes P.prec; every
+// later block Q_i takes P.prec_next.  The Ritz vectors of span[X, Q_1, ..] are
+// y = X s_0 + sum_i Q_i s_i with |s_i| of the order of X's residual, so an operator error eps
+// in A Q_i moves their residuals, and the products carried with them, by about
+// eps ||A|| |s_i|: 1e-7 x 1e-6 of ||A|| for a float32 operator after a float32 phase that
+// stopped at 1e-6, far below a 1e-8 tolerance.  What must stay in the accurate precision is
+// the coupling of the accurate columns (X, or the Ritz vectors kept at a restart, whose
+// products are carried) to the correction blocks: it is of the size of the residual, so it
+// comes from the accurate products (the Cholesky factor R of X's residual block, or the
+// restart coupling) and a correction block's own V^T A Q never overwrites those rows of T.
 kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::vector<double>& theta,
                     std::vector<double>& est, bool* converged) {
     const int b = P.b, m = P.m;
@@ -232,17 +246,25 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
     *converged = false;
     theta.assign(m, 0.0);
     est.assign(m, 0.0);
+    bool first = true;
+    int acc = 0;   // leading basis columns whose products are accurate (correction blocks only)
     for (int it = 0;; ++it) {
         // ---- expansion until the basis is full ----
         bool full = false;
         while (!full) {
             double* Q = E.V() + size_t(j - b) * E.N;
-            KL_TRY(E.apply(P.prec, Q, E.W(), b));
+            const bool corr = !first && P.prec_next != P.prec;
+            KL_TRY(E.apply(corr ? P.prec_next : P.prec, Q, E.W(), b));
+            first = false;
             // keep the raw products: A V[:, j-b:j]
             cudaError_t ec = launch_copy_block(E.W(), E.N, E.AV() + size_t(j - b) * E.N, E.N, E.N, b, E.s);
             if (ec != cudaSuccess) return cuda_fail(ec, "copy products");
             KL_TRY(E.orthogonalize(E.W(), b, j));
-            cudaError_t e = launch_fill_T_block(E.T(), E.mmax, 0, j - b, E.H(), E.mmax, j, b, true, E.s);
+            // T[r0:j, j-b:j] = H[r0:j] (and its mirror); a correction block leaves the rows of
+            // the accurate columns as the accurate products set them
+            const int r0 = corr ? acc : 0;
+            if (!corr) acc = j;
+            cudaError_t e = launch_fill_T_block(E.T(), E.mmax, r0, j - b, E.H() + r0, E.mmax, j - r0, b, true, E.s);
             if (e != cudaSuccess) return cuda_fail(e, "fill T");
             if (j + b > m) {
                 full = true;
@@ -335,6 +357,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         e = launch_set_restart_T(E.T(), E.mmax, E.mmax, E.Theta(), keep, E.R(), b, E.S(), E.mmax, j - b, b, E.s);
         if (e != cudaSuccess) return cuda_fail(e, "restart T");
         j = keep + b;
+        acc = keep;   // the kept Ritz vectors carry their products; the coupling is set above
     }
 }
 
@@ -628,7 +651,9 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     // 32 with the vectors beyond k as guards; the other precisions default to k
     const int pol_def = (o.precision == KL_P_TC64) ? std::max(k, int(std::min<int64_t>(32, N / 3))) : k;
     const int pol_b = std::min(std::max(o.polish_block > 0 ? o.polish_block : pol_def, k), 48);
-    int pol_m = o.polish_ncv > 0 ? o.polish_ncv / pol_b * pol_b : 3 * pol_b;
+    // polish basis: three blocks when every block takes the accurate arithmetic; four when only
+    // the first does (a further correction block costs a float32 application)
+    int pol_m = o.polish_ncv > 0 ? o.polish_ncv / pol_b * pol_b : (o.polish_accurate ? 3 : 4) * pol_b;
     pol_m = std::min(std::max(pol_m, 2 * pol_b), 160 / pol_b * pol_b);
 
     // stage-5 event timing for the whole call (read back at the end)
@@ -697,23 +722,24 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
     bool conv = false;
     double ms32 = 0.0;
     if (o.method == 0) {
-        Phase P{o.precision, b, m, keep, tol, false, maxrestart, k};
+        Phase P{o.precision, b, m, keep, tol, false, maxrestart, k, o.precision};
         KL_TRY(run_phase(E, P, k, b, &restarts, theta, est, &conv));
     } else {
         // the float32 operator's error is relative to |lambda_1|, the residual test to |theta_i|:
-        // before a tensor-core polish (whose launches cost as much as ~8 float32 block
-        // applications) the float32 phase goes one decade further
+        // before a tensor-core polish (one launch costs as much as ~6 float32 block applications)
+        // the float32 phase goes one decade further, which also keeps the correction blocks few
         const double tl = o.tol_low > 0.0 ? o.tol_low : (o.precision == KL_P_TC64 ? 1e-6 : 1e-5);
         const int pb = std::min(pol_b, m);
         const int lowp = (o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32;
-        Phase P1{lowp, b, m, keep, std::max(tl, tol), false, maxrestart, pb};
+        Phase P1{lowp, b, m, keep, std::max(tl, tol), false, maxrestart, pb, lowp};
         KL_TRY(run_phase(E, P1, k, b, &restarts, theta, est, &conv));
         if (lowp == KL_P_TC32) KL_TRY(check_device_status(h, s));
         KL_CUDA(cudaStreamSynchronize(s));
         ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
         // they form the first, wide block of a float64 block Lanczos run.
-        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, k};
+        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, k,
+                  o.polish_accurate ? o.precision : lowp};
         // re-orthonormalise the float32-phase Ritz block in float64 (CholQR2) before it becomes
         // the first block of the float64-accurate phase
         {

@@ -146,3 +146,42 @@ def test_reduced_cube_gaussian_mixed_lobpcg(kl):
     operator from the float32 Ritz block."""
     info = check(kl, "cube-p3-16^3-gauss-L0.3", 20, method=3, block=32, eig_tol=1e-10, precision=4)
     assert 0 < info["applies_tc64"] < info["applies"]
+
+
+# ---- the polish's correction blocks (kl_eig_opts.polish_accurate) ----
+
+@pytest.mark.parametrize("name,precision,low", [("cube-p3-16^3-gauss-L0.3", 4, 1), ("cube-p2-16^3-exp-L0.5", 0, 1),
+                                                ("cube-p2-16^3-exp-L0.5", 2, 3)],
+                         ids=["tc64-after-fp32", "fp64-after-fp32", "df64-after-tc32"])
+def test_polish_correction_blocks(kl, name, precision, low):
+    """Default polish: only its first block (the float32 Ritz block) takes the accurate arithmetic,
+    the correction blocks take the first phase's.  Against the polish with every application
+    accurate: one accurate block application instead of several, residuals re-measured with a
+    fresh float64 application that agree with those carried with the basis (they may differ by
+    the low-precision operator's error times the correction coefficients: ~1e-7 x 1e-6 of
+    ||A~'|| over |theta|, far below 1e-11), and eigenpairs that meet the oracle alike."""
+    import torch
+    k, tol = 20, 1e-8
+    P, lam, Vp = oracle_pairs(name, k)
+    w = inputs.WORKLOADS[name]
+    G = kl.KLProblem(w["dim"], w["p"], w["ne"], kernel=w["kernel"], sigma=w["sigma"], L=w["L"])
+    start = torch.from_numpy(inputs.random_block(G.N, 16, seed=1).T.copy()).cuda()
+    acc_key = {0: "applies_fp64", 2: "applies_df64", 4: "applies_tc64"}[precision]
+    pb = max(k, min(32, G.N // 3)) if precision == 4 else k
+    runs = {}
+    for accurate in (False, True):
+        ev, vec, info = G.eigs(k, tol, method=1, block=16, start=start, precision=precision, low_precision=low,
+                               polish_accurate=accurate)
+        y = G.apply(vec)
+        lt = torch.from_numpy(ev).cuda().reshape(-1, 1)
+        fresh = ((y - lt * vec).norm(dim=1) / lt.abs().reshape(-1)).cpu().numpy()
+        assert fresh.max() <= tol, (accurate, fresh)
+        assert np.abs(fresh - np.asarray(info["resid"])).max() < 1e-11, (accurate, fresh, info["resid"])
+        assert np.abs(ev - lam[:k]).max() / lam[0] < 1e-10
+        V = vec.cpu().numpy().T
+        for g in clusters(lam, k):
+            assert max_sin_angle(V[:, g], Vp[:, g]) < 1e-6
+        runs[accurate] = (ev, info)
+    assert runs[False][1][acc_key] == pb
+    assert runs[True][1][acc_key] > pb
+    assert np.abs(runs[False][0] - runs[True][0]).max() / lam[0] < 1e-12
