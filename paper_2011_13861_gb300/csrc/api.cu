@@ -90,7 +90,7 @@ kl_status ensure_apply_ws(kl_handle h, int nvec, bool fp32, bool tc64 = false) {
     const int s64 = covmv_splits(h->Nt, nvec, false), s32 = covmv_splits(h->Nt, nvec, true);
     const int sdf = covmv_df_splits(h->Nt);
     size_t groups = size_t(s64) * 16;
-    if (size_t(s32) * 32 > groups) groups = size_t(s32) * 32;
+    if (size_t(s32) * 16 > groups) groups = size_t(s32) * 16;   // float32 groups: at most 16 vectors
     if (size_t(sdf) * 32 > groups) groups = size_t(sdf) * 32;
     size_t part = size_t(h->Nt) * groups;
     const size_t dfp = covmv_df_part_doubles(h->Nt, nvec);

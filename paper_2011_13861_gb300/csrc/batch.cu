@@ -186,9 +186,14 @@ __device__ void f32_item(const BatchReq& q, int64_t rb, int64_t sp, double* __re
     const int64_t c_begin = sp * q.cps;
     int64_t c_end = c_begin + q.cps;
     if (c_end > Nt) c_end = Nt;
-    float acc[NV];
+    // even widths: the sums of vectors (v, v + 1) in one 64-bit register pair, one packed FMA
+    constexpr bool PACK = (NV % 2 == 0);
+    float acc[PACK ? 1 : NV];
+    unsigned long long acc2[PACK ? NV / 2 : 1];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+    for (int v = 0; v < (PACK ? 1 : NV); ++v) acc[v] = 0.f;
+#pragma unroll
+    for (int w = 0; w < (PACK ? NV / 2 : 1); ++w) acc2[w] = 0ull;
     for (int64_t c0 = c_begin; c0 < c_end; c0 += kBTile) {
         __syncthreads();
         const int64_t c = c0 + threadIdx.x;
@@ -202,14 +207,27 @@ __device__ void f32_item(const BatchReq& q, int64_t rb, int64_t sp, double* __re
         for (int j = 0; j < jmax; ++j) {
             const float4 p = sp3[j];
             const float g = kernel32<KIND>(x0 - p.x, y0 - p.y, z0 - p.z, x0, y0, z0, p.x, p.y, p.z, cp.poly_m);
+            if constexpr (PACK) {
+                const unsigned long long g2 = f2_dup(g);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] = fmaf(g, su[j][v], acc[v]);
+                for (int w = 0; w < NV / 2; ++w)
+                    acc2[w] = f2_fma(g2, *reinterpret_cast<const unsigned long long*>(&su[j][2 * w]), acc2[w]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] = fmaf(g, su[j][v], acc[v]);
+            }
         }
     }
     if (valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
-            if (v < q.nv) part[q.part_off + (sp * q.nv + v) * Nt + row] = double(acc[v]);
+        for (int v = 0; v < NV; ++v) {
+            float a;
+            if constexpr (PACK)
+                a = (v & 1) ? f2_hi(acc2[v >> 1]) : f2_lo(acc2[v >> 1]);
+            else
+                a = acc[v];
+            if (v < q.nv) part[q.part_off + (sp * q.nv + v) * Nt + row] = double(a);
+        }
     }
 }
 
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(kBRows)
 batch_f32_kernel(const BatchHdr* __restrict__ hdr, const BatchReq* __restrict__ reqs, int* __restrict__ counter,
                  double* __restrict__ part) {
     __shared__ float4 sp3[kBTile];
-    __shared__ float su[kBTile][NV];
+    __shared__ __align__(16) float su[kBTile][NV];
     __shared__ long long s_item;
     const int nreq = hdr->nreq;
     const int64_t total = hdr->total_items;

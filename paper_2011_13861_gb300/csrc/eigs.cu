@@ -288,12 +288,13 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                 bool ok = (nc == k);
                 for (int i = 0; i < nc && ok; ++i) ok = rs[i] <= P.tol * fabs(th[i]);
                 if (ok) {
-                    // Ritz vectors into V[:, 0:k]
-                    e = launch_gemm_tall(1.0, E.V(), E.N, E.N, j, E.S(), E.mmax, k, 0.0, E.Y(), E.N, E.s);
+                    // Ritz vectors into V[:, 0:ke]
+                    const int ke = std::min(std::max(k, P.exit_vecs), j);
+                    e = launch_gemm_tall(1.0, E.V(), E.N, E.N, j, E.S(), E.mmax, ke, 0.0, E.Y(), E.N, E.s);
                     if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
-                    e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, k, E.s);
+                    e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, ke, E.s);
                     if (e != cudaSuccess) return cuda_fail(e, "copy");
-                    KL_TRY(E.rotate_products(j, k));
+                    KL_TRY(E.rotate_products(j, ke));
                     for (int i = 0; i < k; ++i) {
                         theta[i] = th[i];
                         est[i] = rs[i];
@@ -404,6 +405,7 @@ kl_status run_lobpcg(Eig& E, int prec, int nx, int k, double tol, int maxit, boo
         for (int i = 0; i < k; ++i) {
             if (!std::isfinite(theta[i]) || !std::isfinite(est[i]))
                 return fail(KL_ERR_NUMERIC, "non-finite Ritz values (NaN or Inf in the start block or the operator)");
+            est[i] *= fabs(theta[i]);   // launch_ritz_resid gives ||A~'x - theta x|| / |theta|
             ok = ok && est[i] <= tol * fabs(theta[i]);
         }
         *iters = it;
@@ -738,20 +740,43 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
         // they form the first, wide block of a float64 block Lanczos run.
-        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, k,
+        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, pb,
                   o.polish_accurate ? o.precision : lowp};
-        // re-orthonormalise the float32-phase Ritz block in float64 (CholQR2) before it becomes
-        // the first block of the float64-accurate phase
-        {
-            bool defp = false;
-            KL_TRY(E.cholqr(E.V(), pb, E.W(), &defp));
-            e = launch_copy_block(E.W(), N, E.V(), N, N, pb, s);
-            if (e != cudaSuccess) return cuda_fail(e, "copy");
+        // With float32 correction blocks the residuals carried with the Ritz vectors are off by
+        // about eps32 ||A~'|| |s|, s their coefficients on the correction blocks.  Where the
+        // float32 phase left a wanted vector far from the float64 one (a pair whose eigenvalue is
+        // small against lambda_1 and close to its neighbour's) that can exceed the tolerance:
+        // the residuals are then re-measured from the carried products, and a pass that fails
+        // starts again from its Ritz vectors with one more accurate application (the error it
+        // leaves shrinks by eps32 ||A~'|| / |theta_k| per pass); after kMaxPolishPasses the
+        // correction blocks take the accurate arithmetic as well.
+        constexpr int kMaxPolishPasses = 4;
+        for (int pass = 0;; ++pass) {
+            // re-orthonormalise the Ritz block in float64 (CholQR2) before it becomes the first
+            // block of the accurate phase
+            {
+                bool defp = false;
+                KL_TRY(E.cholqr(E.V(), pb, E.W(), &defp));
+                e = launch_copy_block(E.W(), N, E.V(), N, N, pb, s);
+                if (e != cudaSuccess) return cuda_fail(e, "copy");
+            }
+            // the active block is V[:, 0:pb]; T is rebuilt by the first expansion
+            e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
+            if (e != cudaSuccess) return cuda_fail(e, "memset");
+            KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
+            if (!conv || P2.prec_next == P2.prec) break;
+            // residuals ||A~'y - theta y|| of the k wanted Ritz vectors from their carried products
+            e = launch_ritz_resid(E.AV(), E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
+            if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
+            std::vector<double> rx(k);
+            KL_CUDA(cudaMemcpyAsync(rx.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
+            KL_CUDA(cudaStreamSynchronize(s));
+            bool ok = true;   // rx holds ||A~'y - theta y|| / |theta|
+            for (int i = 0; i < k; ++i) ok = ok && rx[i] <= tol;
+            if (ok) break;
+            ++restarts;
+            if (pass + 1 >= kMaxPolishPasses) P2.prec_next = P2.prec;
         }
-        // the active block is V[:, 0:pb]; T is rebuilt by the first expansion
-        e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
-        if (e != cudaSuccess) return cuda_fail(e, "memset");
-        KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
     }
 
     return finish_eigs(h, E, o, k, tol, theta, est, restarts, ms32, evals_host, evecs_dev, ldv, info, s, t0);

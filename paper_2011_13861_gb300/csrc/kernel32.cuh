@@ -32,5 +32,23 @@ __device__ __forceinline__ float kernel32(float dx, float dy, float dz, float x0
     }
 }
 
+// Packed float32 pairs (fma.rn.f32x2): one instruction performs two IEEE float32 FMAs, each
+// rounded exactly as fmaf, on the two halves of 64-bit registers (low half = first element).
+// The FMA pipe's throughput is the same as for scalar FFMA (measured: kl_pipe_rates), but one
+// issue slot serves two FMAs, which is what the issue-bound float32 stage-5 loop is short of.
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long f2_dup(float g) {
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(g));
+    return d;
+}
+
+__device__ __forceinline__ float f2_lo(unsigned long long x) { return __uint_as_float(unsigned(x)); }
+__device__ __forceinline__ float f2_hi(unsigned long long x) { return __uint_as_float(unsigned(x >> 32)); }
 
 }  // namespace kl
