@@ -442,6 +442,15 @@ kl_status kl_pipe_rates(double* rates_host, int n, void* stream);
  * status a stalled tensor-core pipeline returns; the context stays usable.  Synchronous. */
 kl_status kl_wait_selftest(double seconds, void* stream);
 
+/* Self-check of the packed-pair double-float arithmetic of the tensor-core float64-class
+ * producers (no counterpart in the paper): n random pairs of column points (and a row point
+ * each) are evaluated through the exponential, Gaussian and separable-exponential kernels, sliced
+ * and summed, once value by value (the scalar double-float code) and once two values per packed
+ * float32-pair instruction; *mismatches receives the number of float words that differ (0: the
+ * two are bit-identical).  Synchronous on `stream`.  n >= 0, mismatches non-NULL, else
+ * KL_ERR_INVALID_ARG. */
+kl_status kl_df2_selftest(int64_t n, uint64_t seed, int64_t* mismatches, void* stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded (all handles, all
  * threads); for tracing and launch accounting. */
 uint64_t kl_kernel_launches(void);

@@ -100,6 +100,7 @@ SIGNATURES = {
     "kl_prolongation_factor": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int), _vp]),
     "kl_wait_selftest": (ctypes.c_int, [ctypes.c_double, _vp]),
+    "kl_df2_selftest": (ctypes.c_int, [_c_int64, ctypes.c_uint64, _vp, _vp]),
     "kl_pipe_rates": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "kl_set_sym_slot_limit": (ctypes.c_int, [_c_int64]),
     "kl_set_tc_symmetric": (ctypes.c_int, [ctypes.c_int]),
@@ -545,6 +546,14 @@ def mapped_points(dim, p, ne, pt=None, net=None, lo=None, hi=None, nurbs=None, i
                                 ctypes.c_void_p(X.ctypes.data), ctypes.c_void_p(J.ctypes.data)))
     del keep
     return X, J
+
+
+def df2_selftest(n, seed=1, stream=None):
+    """kl_df2_selftest: float words in which the packed-pair double-float kernel values, slices
+    and sums differ from the scalar ones over n random column pairs (0 = bit-identical)."""
+    out = _c_int64(0)
+    _check(load().kl_df2_selftest(int(n), int(seed) & (2 ** 64 - 1), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def wait_selftest(seconds=0.05, stream=None):

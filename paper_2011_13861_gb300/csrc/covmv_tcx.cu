@@ -34,6 +34,7 @@
 //     accumulators in tensor memory, double-buffered per 128-column drain block.
 // Every wait is bounded (~2 s), after which the CTA records KL_ERR_TIMEOUT, drains its own
 // asynchronous operations and returns.
+#include "df2.cuh"
 #include "df64.cuh"
 #include "kernel32.cuh"
 #include "tc_slices.cuh"
@@ -230,9 +231,10 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
         int64_t rb = -1;
         float rc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float* rsrc = CLS == 64 ? cp.Pdf : cp.P32;
-        F2 acc[kVpt];
+        // the row's double-float sums, two vectors to a packed pair (vectors 2w and 2w + 1)
+        df2::P acc2[kVpt / 2];
 #pragma unroll
-        for (int v = 0; v < kVpt; ++v) acc[v] = F2{0.f, 0.f};
+        for (int w = 0; w < kVpt / 2; ++w) acc2[w] = df2::P{df2::dup(0.f), df2::dup(0.f)};
         bool pend = false, pend_seg_end = false;
         int pend_nb = 0, pend_seg = 0;
         int64_t pend_rb = 0;
@@ -250,10 +252,11 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
                 for (int a = 0; a < kAccs; ++a)
                     tmem_ld8(tmem + lane_base + uint32_t(dp * kTmemBuf + a * 32 + qd * kVpt + g8 * 8), L[a]);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) {
+                for (int w = 0; w < 4; ++w) {
+                    df2::P& A = acc2[g8 * 4 + w];
 #pragma unroll
-                    for (int a = 0; a < kAccs; ++a) df_acc(acc[g8 * 8 + v], L[a][v]);
-                    acc[g8 * 8 + v] = df::fast_two_sum(acc[g8 * 8 + v].h, acc[g8 * 8 + v].l);
+                    for (int a = 0; a < kAccs; ++a) df2::acc_add(A, df2::mk(L[a][2 * w], L[a][2 * w + 1]));
+                    A = df2::fast_two_sum(A.h, A.l);
                 }
             }
             fence_before_sync();
@@ -264,13 +267,14 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
 #pragma unroll
                     for (int v = 0; v < kVpt; ++v) {
                         const int vv = qd * kVpt + v;
-                        if (vv < nv)
-                            slot[vv * kRows] = (double(acc[v].h) + double(acc[v].l)) *
-                                               (sigma[vv] * 0.00390625 / double(gscale));
+                        const df2::P& A = acc2[v / 2];
+                        const float h = (v & 1) ? df2::hi(A.h) : df2::lo(A.h);
+                        const float l = (v & 1) ? df2::hi(A.l) : df2::lo(A.l);
+                        if (vv < nv) slot[vv * kRows] = (double(h) + double(l)) * (sigma[vv] * 0.00390625 / double(gscale));
                     }
                 }
 #pragma unroll
-                for (int v = 0; v < kVpt; ++v) acc[v] = F2{0.f, 0.f};
+                for (int w = 0; w < kVpt / 2; ++w) acc2[w] = df2::P{df2::dup(0.f), df2::dup(0.f)};
             }
             return true;
         };
@@ -305,34 +309,50 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
                 uint32_t w[kSlices][4];
 #pragma unroll
                 for (int e = 0; e < 8; e += 2) {
-                    float o[2][kSlices];
-                    float2 cp2[CLS == 64 ? 6 : 1];
-                    if constexpr (CLS == 64) {
+                    if constexpr (CLS == 64 && KIND != KL_K_POLY_TEST) {
+                        // the two columns e, e + 1 in the two lanes of packed pairs (bit-identical
+                        // to evaluating them one after the other)
+                        df2::V r6[6], c6[6];
 #pragma unroll
-                        for (int k = 0; k < 6; ++k)
-                            cp2[k] = *reinterpret_cast<const float2*>(img_c + k * kChunk + c0 + e);
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if constexpr (CLS == 64) {
-                            float c6[6];
-#pragma unroll
-                            for (int k = 0; k < 6; ++k) c6[k] = h ? cp2[k].y : cp2[k].x;
-                            F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
-                            if (KIND == KL_K_POLY_TEST) {   // the other kernels have gscale = 1
-                                g.h = __fmul_rn(g.h, gscale);
-                                g.l = __fmul_rn(g.l, gscale);
-                            }
-                            slices6(g, o[h]);
-                        } else {
-                            const float x1 = cv[0][e + h], y1 = cv[1][e + h], z1 = cv[2][e + h];
-                            const float g = kernel32<KIND>(rc[0] - x1, rc[1] - y1, rc[2] - z1, rc[0], rc[1], rc[2],
-                                                           x1, y1, z1, cp.poly_m);
-                            slices3(KIND == KL_K_POLY_TEST ? __fmul_rn(g, gscale) : g, o[h]);
+                        for (int k = 0; k < 6; ++k) {
+                            r6[k] = df2::dup(rc[k]);
+                            c6[k] = df2::V{*reinterpret_cast<const unsigned long long*>(img_c + k * kChunk + c0 + e)};
                         }
-                    }
+                        const df2::P g = df2::kernel_df<KIND>(r6, c6, stab, stab + 64);
+                        df2::V o2[6];
+                        df2::slices6(g, o2);
 #pragma unroll
-                    for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(o[0][q], o[1][q]);
+                        for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(df2::lo(o2[q]), df2::hi(o2[q]));
+                    } else {
+                        float o[2][kSlices];
+                        float2 cp2[CLS == 64 ? 6 : 1];
+                        if constexpr (CLS == 64) {
+#pragma unroll
+                            for (int k = 0; k < 6; ++k)
+                                cp2[k] = *reinterpret_cast<const float2*>(img_c + k * kChunk + c0 + e);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if constexpr (CLS == 64) {
+                                float c6[6];
+#pragma unroll
+                                for (int k = 0; k < 6; ++k) c6[k] = h ? cp2[k].y : cp2[k].x;
+                                F2 g = df::kernel_df<KIND>(rc, c6, cp.poly_m, stab, stab + 64);
+                                if (KIND == KL_K_POLY_TEST) {   // the other kernels have gscale = 1
+                                    g.h = __fmul_rn(g.h, gscale);
+                                    g.l = __fmul_rn(g.l, gscale);
+                                }
+                                slices6(g, o[h]);
+                            } else {
+                                const float x1 = cv[0][e + h], y1 = cv[1][e + h], z1 = cv[2][e + h];
+                                const float g = kernel32<KIND>(rc[0] - x1, rc[1] - y1, rc[2] - z1, rc[0], rc[1],
+                                                               rc[2], x1, y1, z1, cp.poly_m);
+                                slices3(KIND == KL_K_POLY_TEST ? __fmul_rn(g, gscale) : g, o[h]);
+                            }
+                        }
+#pragma unroll
+                        for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(o[0][q], o[1][q]);
+                    }
                 }
                 unsigned char* As = smem + kOffA + st * kAStage + kmajor_offset(r, c0, kASub);
 #pragma unroll

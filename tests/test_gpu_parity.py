@@ -221,3 +221,13 @@ def test_tiny_problems_every_precision(kl, dim, p, ne):
     v = inputs.random_block(P.N, 2, seed=78)
     y = G.apply(torch.from_numpy(v.T.copy()).cuda()).cpu().numpy().T
     assert rel(y, P.dense_operator() @ v) < FP64_TOL
+
+
+def test_packed_double_float_pairs_are_bit_identical(kl):
+    """The tensor-core float64-class producers evaluate two kernel values per packed float32-pair
+    instruction; kl_df2_selftest runs the scalar and the packed double-float code on the same
+    random points (spans 1/4 to 64, so the exponential's clamp is reached) for the exponential,
+    Gaussian and separable-exponential kernels, their six slices and the slices' double-float
+    sum, and counts differing float words: none may differ."""
+    assert kl.df2_selftest(1 << 20, seed=7) == 0
+    assert kl.df2_selftest(0) == 0
