@@ -586,8 +586,8 @@ def measure_secondary(kl, inputs, flush, stream, plain_block, mixed_block, steps
     out = {"workload": SECONDARY_WORKLOAD, "N": G.N, "Ntilde": Nt, "k": k,
            "plain_fp64_s": ms_p / 1e3, "chosen_s": ms_c / 1e3, "speedup": ms_p / ms_c,
            "plain": "float64 thick-restart block Lanczos, block %d" % plain_block,
-           "chosen": "float32 stage-5 block Lanczos (block %d, symmetric tiles) + block-32 tensor-core "
-                     "float64-class polish" % mixed_block,
+           "chosen": "float32 stage-5 block Lanczos (block %d) + block-32 polish: one tensor-core "
+                     "float64-class stage 5, float32 correction blocks" % mixed_block,
            "plain_applies": ip["applies"], "chosen_applies": ic["applies"],
            "plain_evals_per_s": ip["applies"] * float(Nt) * Nt / (ms_p * 1e-3),
            "chosen_evals_per_s": ic["applies"] * float(Nt) * Nt / (ms_c * 1e-3),
@@ -595,7 +595,8 @@ def measure_secondary(kl, inputs, flush, stream, plain_block, mixed_block, steps
            "accuracy_plain": mode_accuracy(SECONDARY_WORKLOAD, ev_p, None, k),
            "accuracy_chosen": mode_accuracy(SECONDARY_WORKLOAD, ev_c, None, k),
            "plain_stage5_fp64_ms_per_call": ip["ms_stage5_fp64"] / calls,
-           "chosen_stage5_ms": {"fp32": ic["ms_stage5_fp32"], "tc64": ic["ms_stage5_tc64"]},
+           "chosen_stage5_ms": {"fp32": ic["ms_stage5_fp32"], "tc64": ic["ms_stage5_tc64"],
+                                "tc32": ic["ms_stage5_tc32"]},
            "timing": "CUDA events, mean of %d after 2 warm-ups each, L2 flushed" % steps}
     out["roofline_plain_fp64"] = roofline_entry(
         "covmv64_sym_kernel (float64 stage 5, symmetric tiles)", "alu", w["kernel"], Nt,
@@ -639,7 +640,8 @@ def main():
 
     def solve_chosen():
         # float32 stage 5 until the estimates reach 1e-6, then a polish block of max(k, 32) whose
-        # stage 5 runs on the tensor cores with exact slicing (float64-class)
+        # first application runs on the tensor cores with exact slicing (float64-class) and whose
+        # correction blocks take the float32 stage 5
         return G.eigs(k, TOL, method=1, block=args.block, start=start_c, precision=kl.KL_P_TC64)
 
     for _ in range(args.warmup):
@@ -685,9 +687,14 @@ def main():
     rl = {}
     nc32 = info_c["stage5_calls_fp32"]
     if nc32:
-        rl["fp32"] = roofline_entry("covmv32_kernel (float32 stage 5, %d vectors)" % args.block, "alu",
-                                    w["kernel"], Nt, args.block, args.block <= 8, info_c["ms_stage5_fp32"] / nc32,
-                                    nc32, ffma_flops, "measured float32 FMA rate x 2 (kl_pipe_rates, this run)")
+        # float32 calls: the float32 phase's blocks and the polish's correction blocks; the kernel
+        # runs groups of at most 16 vectors (a 32-vector call is two launches of the 16-wide kernel)
+        v32 = (info_c["applies"] - info_c["applies_fp64"] - info_c["applies_df64"] - info_c["applies_tc64"]
+               - info_c["applies_tc32"])
+        g32 = max(nc32, -(-v32 // 16))
+        rl["fp32"] = roofline_entry("covmv32_kernel (float32 stage 5, packed pair FMAs, %g-vector groups)" % (v32 / g32),
+                                    "alu", w["kernel"], Nt, v32 / g32, v32 / g32 <= 8, info_c["ms_stage5_fp32"] / g32,
+                                    g32, ffma_flops, "measured float32 FMA rate x 2 (kl_pipe_rates, this run)")
     nc64 = info_c["stage5_calls_tc64"]
     if nc64:
         nv64 = info_c["applies_tc64"] / nc64
@@ -697,7 +704,14 @@ def main():
             "measured float32 FMA rate x 2 (kl_pipe_rates, this run): the kernel's double-float "
             "kernel values and slicing run on the float32 pipe, its bound",
             TRAFFIC.get(("tc64", args.workload, int(round(nv64)))))
-    share = {key: (info_c["ms_stage5_" + key] / ms_c) for key in ("fp32", "tc64")}
+    nt32 = info_c["stage5_calls_tc32"]
+    if nt32:
+        nvt = info_c["applies_tc32"] / nt32
+        rl["tc32"] = roofline_entry(
+            "covmv_tcx_kernel<32> (tensor-core float32 class, the polish's correction blocks)", "alu", w["kernel"],
+            Nt, nvt, False, info_c["ms_stage5_tc32"] / nt32, nt32, ffma_flops,
+            "measured float32 FMA rate x 2 (kl_pipe_rates, this run): kernel values and slicing on the float32 pipe")
+    share = {key: (info_c["ms_stage5_" + key] / ms_c) for key in ("fp32", "tc64", "tc32")}
     dom = max(rl, key=lambda key: share[key]) if rl else None
     roofline = dict(rl[dom]) if dom else None
     if roofline is not None:
@@ -721,7 +735,7 @@ def main():
 
     secondary = batched = warm = None
     if world == 1 and not args.no_secondary:
-        secondary = measure_secondary(kl, inputs, flush, stream, 4, 4, 3, dfma_flops)
+        secondary = measure_secondary(kl, inputs, flush, stream, 4, 16, 3, dfma_flops)
     if world == 1 and not args.no_batched:
         batched = measure_batched(kl, inputs)
     if world == 1 and not args.no_warm_start:
@@ -740,7 +754,8 @@ def main():
         "config": {"workload": args.workload, "dim": w["dim"], "degree": w["p"], "elements": w["ne"],
                    "kernel": w["kernel"], "L": w["L"], "sigma": w["sigma"], "N": N, "Ntilde": Nt, "k": k,
                    "tol": TOL, "chosen_form": "block Lanczos, float32 stage 5 (block %d) to 1e-6, then a "
-                                              "block-32 polish with the tensor-core float64-class stage 5"
+                                              "block-32 polish: one tensor-core float64-class stage 5 on "
+                                              "the float32 Ritz block, float32 correction blocks"
                                               % args.block,
                    "L2": "flushed between steps (256 MB write)"},
         "chosen": {"seconds": ms_c / 1e3, "step_ms": t_c, "applies": info_c["applies"],
@@ -749,7 +764,8 @@ def main():
                    "resid_fp64_operator": [float(x) for x in fp64_resid],
                    "evals_per_s": info_c["applies"] * float(Nt) * Nt / (ms_c * 1e-3),
                    "ms_fp32_phase": info_c["ms_fp32_phase"],
-                   "stage5_ms": {"fp32": info_c["ms_stage5_fp32"], "tc64": info_c["ms_stage5_tc64"]},
+                   "stage5_ms": {"fp32": info_c["ms_stage5_fp32"], "tc64": info_c["ms_stage5_tc64"],
+                                 "tc32": info_c["ms_stage5_tc32"]},
                    "accuracy": acc_c},
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": (plain["seconds"] / (ms_c / 1e3)) if plain else None,

@@ -272,6 +272,9 @@ typedef struct {
     int stage5_calls_tc64;  /* stage-5 launch groups, time and kernel evaluations in KL_P_TC64 */
     double ms_stage5_tc64, pairs_tc64;
     int applies_tc64;       /* operator applications counted per vector in KL_P_TC64 */
+    int stage5_calls_tc32;  /* the same for KL_P_TC32 (the other float32-class counts above are KL_P_FP32's) */
+    double ms_stage5_tc32, pairs_tc32;
+    int applies_tc32;
 } kl_eig_info;
 
 /* ---- Many independent problems at once (no counterpart in the paper) ----------------
@@ -442,12 +445,12 @@ kl_status kl_pipe_rates(double* rates_host, int n, void* stream);
  * status a stalled tensor-core pipeline returns; the context stays usable.  Synchronous. */
 kl_status kl_wait_selftest(double seconds, void* stream);
 
-/* Self-check of the packed-pair double-float arithmetic of the tensor-core float64-class
- * producers (no counterpart in the paper): n random pairs of column points (and a row point
- * each) are evaluated through the exponential, Gaussian and separable-exponential kernels, sliced
- * and summed, once value by value (the scalar double-float code) and once two values per packed
- * float32-pair instruction; *mismatches receives the number of float words that differ (0: the
- * two are bit-identical).  Synchronous on `stream`.  n >= 0, mismatches non-NULL, else
+/* Self-check of the packed-pair arithmetic of the tensor-core stage-5 producers (no counterpart
+ * in the paper): n random pairs of column points (and a row point each) are evaluated through
+ * the exponential, Gaussian and separable-exponential kernels in double-float (float64 class:
+ * values, six slices, their sum) and in float32 (float32 class: values, three slices), once value
+ * by value (the scalar code) and once two values per packed float32-pair instruction;
+ * *mismatches receives the number of float words that differ (0: the two are bit-identical).  Synchronous on `stream`.  n >= 0, mismatches non-NULL, else
  * KL_ERR_INVALID_ARG. */
 kl_status kl_df2_selftest(int64_t n, uint64_t seed, int64_t* mismatches, void* stream);
 

@@ -51,7 +51,9 @@ class KLEigInfo(ctypes.Structure):
                 ("pairs_fp64", ctypes.c_double), ("pairs_fp32", ctypes.c_double), ("pairs_df64", ctypes.c_double),
                 ("applies_df64", ctypes.c_int),
                 ("stage5_calls_tc64", ctypes.c_int), ("ms_stage5_tc64", ctypes.c_double),
-                ("pairs_tc64", ctypes.c_double), ("applies_tc64", ctypes.c_int)]
+                ("pairs_tc64", ctypes.c_double), ("applies_tc64", ctypes.c_int),
+                ("stage5_calls_tc32", ctypes.c_int), ("ms_stage5_tc32", ctypes.c_double),
+                ("pairs_tc32", ctypes.c_double), ("applies_tc32", ctypes.c_int)]
 
 
 class KLBatchInfo(ctypes.Structure):
@@ -160,7 +162,9 @@ def _info_dict(info, k, st):
             "stage5_calls_df64": info.stage5_calls_df64, "ms_stage5_df64": info.ms_stage5_df64,
             "pairs_df64": info.pairs_df64, "applies_df64": info.applies_df64,
             "stage5_calls_tc64": info.stage5_calls_tc64, "ms_stage5_tc64": info.ms_stage5_tc64,
-            "pairs_tc64": info.pairs_tc64, "applies_tc64": info.applies_tc64}
+            "pairs_tc64": info.pairs_tc64, "applies_tc64": info.applies_tc64,
+            "stage5_calls_tc32": info.stage5_calls_tc32, "ms_stage5_tc32": info.ms_stage5_tc32,
+            "pairs_tc32": info.pairs_tc32, "applies_tc32": info.applies_tc32}
 
 
 def _check(status):

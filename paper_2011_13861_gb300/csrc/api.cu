@@ -365,7 +365,7 @@ kl_status apply_impl(kl_handle h, int precision, const double* v, int64_t ldv, d
     double* part = static_cast<double*>(h->w_part.ptr);
     int slot;
     const bool fp32 = (precision == KL_P_FP32 || precision == KL_P_TC32);
-    KL_TRY(prof_begin(h, fp32 ? KL_P_FP32 : precision, nvec, s, &slot));
+    KL_TRY(prof_begin(h, precision, nvec, s, &slot));
     if (h->batch && (precision == KL_P_FP32 || precision == KL_P_DF64)) {
         // many instances solved together: stage 5 joins the other instances' requests
         KL_TRY(batch_stage5(h, precision, b.u, ld, b.z, ld, nvec, true, s));

@@ -323,6 +323,15 @@ covmv_tcx_kernel(CovParams cp, const unsigned char* __restrict__ img, int nv, co
                         df2::slices6(g, o2);
 #pragma unroll
                         for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(df2::lo(o2[q]), df2::hi(o2[q]));
+                    } else if constexpr (CLS == 32 && KIND != KL_K_POLY_TEST) {
+                        // float32 class: the two columns e, e + 1 in packed pairs (bit-identical)
+                        const df2::V dx = df2::sub(df2::dup(rc[0]), df2::mk(cv[0][e], cv[0][e + 1]));
+                        const df2::V dy = df2::sub(df2::dup(rc[1]), df2::mk(cv[1][e], cv[1][e + 1]));
+                        const df2::V dz = df2::sub(df2::dup(rc[2]), df2::mk(cv[2][e], cv[2][e + 1]));
+                        df2::V o2[3];
+                        df2::slices3(df2::kernel32<KIND>(dx, dy, dz), o2);
+#pragma unroll
+                        for (int q = 0; q < kSlices; ++q) w[q][e / 2] = pack_bf16(df2::lo(o2[q]), df2::hi(o2[q]));
                     } else {
                         float o[2][kSlices];
                         float2 cp2[CLS == 64 ? 6 : 1];

@@ -199,6 +199,33 @@ __device__ __forceinline__ P kernel_df(const V* r, const V* c, const float* th, 
     return exp_neg(sqrt(s, mk(s0, s1)), th, tl);
 }
 
+// kernel32.cuh kernel values for two columns (float32 class, coordinates pre-scaled so that one
+// MUFU ex2 gives the exponential): the differences and squares packed, the MUFU steps per lane
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int KIND>
+__device__ __forceinline__ V kernel32(V dx, V dy, V dz) {
+    if (KIND == KL_K_EXP_SEPARABLE) {
+        const unsigned long long m = 0x7FFFFFFF7FFFFFFFull;   // |.| of both lanes
+        const V s = add(add(V{dx.x & m}, V{dy.x & m}), V{dz.x & m});
+        return mk(ex2_approx(-lo(s)), ex2_approx(-hi(s)));
+    }
+    const V s = fma_(dz, dz, fma_(dy, dy, mul(dx, dx)));
+    if (KIND == KL_K_GAUSS) return mk(ex2_approx(-lo(s)), ex2_approx(-hi(s)));
+    const float s0 = fmaxf(lo(s), 1e-30f), s1 = fmaxf(hi(s), 1e-30f);
+    return mk(ex2_approx(-s0 * rsqrt_approx(s0)), ex2_approx(-s1 * rsqrt_approx(s1)));
+}
+
 // tc_slices.cuh digit and slices6 on pairs
 __device__ __forceinline__ V digit(V& x, float shifter) {
     const V sh = dup(shifter);
@@ -216,6 +243,14 @@ __device__ __forceinline__ void slices6(P g, V* out) {
     out[3] = digit(x, 0.0029296875f);
     out[4] = digit(x, 1.1444091796875e-05f);
     out[5] = digit(x, 4.4703483581542969e-08f);
+}
+
+// tc_slices.cuh slices3 on pairs
+__device__ __forceinline__ void slices3(V g, V* out) {
+    V x = g;
+    out[0] = digit(x, 49152.f);
+    out[1] = digit(x, 192.f);
+    out[2] = digit(x, 0.75f);
 }
 
 // tc_slices.cuh df_acc for two sums at once: acc += x, then the final renormalisation

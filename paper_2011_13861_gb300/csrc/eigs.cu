@@ -62,7 +62,7 @@ struct Eig {
     int* Sweeps() { return static_cast<int*>(bSweeps.ptr); }
     int maxparts = 0;
     // statistics
-    int applies = 0, applies64 = 0, appliesdf = 0, appliestc64 = 0, block_applies = 0;
+    int applies = 0, applies64 = 0, appliesdf = 0, appliestc64 = 0, appliestc32 = 0, block_applies = 0;
     uint64_t rng_offset = 0;
     uint64_t seed = 1;
 
@@ -107,6 +107,7 @@ struct Eig {
         if (prec == KL_P_FP64) applies64 += b;
         if (prec == KL_P_DF64) appliesdf += b;
         if (prec == KL_P_TC64) appliestc64 += b;
+        if (prec == KL_P_TC32) appliestc32 += b;
         block_applies += 1;
         return KL_OK;
     }
@@ -221,6 +222,7 @@ struct Phase {
     int maxrestart;
     int exit_vecs;     // Ritz vectors left in V[:, 0:exit_vecs] on exit (>= k)
     int prec_next;     // arithmetic of every application after the phase's first (see run_phase)
+    bool carry = true; // keep A~'V with the basis (false: a later phase recomputes the products)
 };
 
 // Runs one thick-restart block Lanczos phase.  On entry V[:, 0:j0] holds an orthonormal basis
@@ -257,8 +259,10 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
             KL_TRY(E.apply(corr ? P.prec_next : P.prec, Q, E.W(), b));
             first = false;
             // keep the raw products: A V[:, j-b:j]
-            cudaError_t ec = launch_copy_block(E.W(), E.N, E.AV() + size_t(j - b) * E.N, E.N, E.N, b, E.s);
-            if (ec != cudaSuccess) return cuda_fail(ec, "copy products");
+            if (P.carry) {
+                cudaError_t ec = launch_copy_block(E.W(), E.N, E.AV() + size_t(j - b) * E.N, E.N, E.N, b, E.s);
+                if (ec != cudaSuccess) return cuda_fail(ec, "copy products");
+            }
             KL_TRY(E.orthogonalize(E.W(), b, j));
             // T[r0:j, j-b:j] = H[r0:j] (and its mirror); a correction block leaves the rows of
             // the accurate columns as the accurate products set them
@@ -294,7 +298,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                     if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
                     e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, ke, E.s);
                     if (e != cudaSuccess) return cuda_fail(e, "copy");
-                    KL_TRY(E.rotate_products(j, ke));
+                    if (P.carry) KL_TRY(E.rotate_products(j, ke));
                     for (int i = 0; i < k; ++i) {
                         theta[i] = th[i];
                         est[i] = rs[i];
@@ -339,7 +343,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
         e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, keep, E.s);
         if (e != cudaSuccess) return cuda_fail(e, "copy");
-        KL_TRY(E.rotate_products(j, keep));
+        if (P.carry) KL_TRY(E.rotate_products(j, keep));
         if (ok || last) {
             *converged = ok;
             return KL_OK;
@@ -501,6 +505,7 @@ static kl_status finish_eigs(kl_handle h, Eig& E, const kl_eig_opts& o, int k, d
         info->applies_fp64 = E.applies64;
         info->applies_df64 = E.appliesdf;
         info->applies_tc64 = E.appliestc64;
+        info->applies_tc32 = E.appliestc32;
         info->block_applies = E.block_applies;
         info->restarts = restarts;
         info->converged = nconv;
@@ -510,8 +515,8 @@ static kl_status finish_eigs(kl_handle h, Eig& E, const kl_eig_opts& o, int k, d
         info->stage5_calls_fp64 = info->stage5_calls_fp32 = info->stage5_calls_df64 = 0;
         info->ms_stage5_fp64 = info->ms_stage5_fp32 = info->ms_stage5_df64 = 0.0;
         info->pairs_fp64 = info->pairs_fp32 = info->pairs_df64 = 0.0;
-        info->stage5_calls_tc64 = 0;
-        info->ms_stage5_tc64 = info->pairs_tc64 = 0.0;
+        info->stage5_calls_tc64 = info->stage5_calls_tc32 = 0;
+        info->ms_stage5_tc64 = info->pairs_tc64 = info->ms_stage5_tc32 = info->pairs_tc32 = 0.0;
         const double pairs = double(h->Nt) * double(h->Nt);
         for (const auto& r : h->prof_rec) {
             float ms = 0.f;
@@ -528,6 +533,10 @@ static kl_status finish_eigs(kl_handle h, Eig& E, const kl_eig_opts& o, int k, d
                 info->stage5_calls_tc64 += 1;
                 info->ms_stage5_tc64 += ms;
                 info->pairs_tc64 += pairs;
+            } else if (r.kind == KL_P_TC32) {
+                info->stage5_calls_tc32 += 1;
+                info->ms_stage5_tc32 += ms;
+                info->pairs_tc32 += pairs;
             } else {
                 info->stage5_calls_fp32 += 1;
                 info->ms_stage5_fp32 += ms;
@@ -734,14 +743,18 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         const int pb = std::min(pol_b, m);
         const int lowp = (o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32;
         Phase P1{lowp, b, m, keep, std::max(tl, tol), false, maxrestart, pb, lowp};
+        P1.carry = false;   // the polish applies the operator to the Ritz block afresh
         KL_TRY(run_phase(E, P1, k, b, &restarts, theta, est, &conv));
         if (lowp == KL_P_TC32) KL_TRY(check_device_status(h, s));
         KL_CUDA(cudaStreamSynchronize(s));
         ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
         // they form the first, wide block of a float64 block Lanczos run.
-        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, pb,
-                  o.polish_accurate ? o.precision : lowp};
+        // the correction blocks take the float32 class; blocks wider than 16 vectors run on the
+        // tensor-core float32 kernel (one launch for up to 32 vectors, measured 23.1 ms against
+        // 2 x 13.6 ms for the CUDA-core kernel's two 16-wide groups at 132,651 points)
+        const int corr_p = (lowp == KL_P_FP32 && pb > 16) ? KL_P_TC32 : lowp;
+        Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, pb, o.polish_accurate ? o.precision : corr_p};
         // With float32 correction blocks the residuals carried with the Ritz vectors are off by
         // about eps32 ||A~'|| |s|, s their coefficients on the correction blocks.  Where the
         // float32 phase left a wanted vector far from the float64 one (a pair whose eigenvalue is

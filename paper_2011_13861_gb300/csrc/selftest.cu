@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "df2.cuh"
+#include "kernel32.cuh"
 #include "kl_internal.h"
 #include "tc_common.cuh"
 #include "tc_slices.cuh"
@@ -100,6 +101,36 @@ __global__ void df2_selftest_kernel(long long n, unsigned long long seed, const 
             a = df2::fast_two_sum(a.h, a.l);
             bad += (__float_as_uint(a0.h) != __float_as_uint(df2::lo(a.h))) + (__float_as_uint(a0.l) != __float_as_uint(df2::lo(a.l)));
             bad += (__float_as_uint(a1.h) != __float_as_uint(df2::hi(a.h))) + (__float_as_uint(a1.l) != __float_as_uint(df2::hi(a.l)));
+            // float32 class (the heads as float32 coordinates): kernel values and three slices
+            float f0, f1;
+            df2::V f;
+            const df2::V dx = df2::sub(df2::dup(r[0]), df2::mk(c0[0], c1[0]));
+            const df2::V dy = df2::sub(df2::dup(r[1]), df2::mk(c0[1], c1[1]));
+            const df2::V dz = df2::sub(df2::dup(r[2]), df2::mk(c0[2], c1[2]));
+            if (kind == 0) {
+                f0 = kernel32<KL_K_EXP>(r[0] - c0[0], r[1] - c0[1], r[2] - c0[2], r[0], r[1], r[2], c0[0], c0[1], c0[2], 0);
+                f1 = kernel32<KL_K_EXP>(r[0] - c1[0], r[1] - c1[1], r[2] - c1[2], r[0], r[1], r[2], c1[0], c1[1], c1[2], 0);
+                f = df2::kernel32<KL_K_EXP>(dx, dy, dz);
+            } else if (kind == 1) {
+                f0 = kernel32<KL_K_GAUSS>(r[0] - c0[0], r[1] - c0[1], r[2] - c0[2], r[0], r[1], r[2], c0[0], c0[1], c0[2], 0);
+                f1 = kernel32<KL_K_GAUSS>(r[0] - c1[0], r[1] - c1[1], r[2] - c1[2], r[0], r[1], r[2], c1[0], c1[1], c1[2], 0);
+                f = df2::kernel32<KL_K_GAUSS>(dx, dy, dz);
+            } else {
+                f0 = kernel32<KL_K_EXP_SEPARABLE>(r[0] - c0[0], r[1] - c0[1], r[2] - c0[2], r[0], r[1], r[2], c0[0], c0[1],
+                                                  c0[2], 0);
+                f1 = kernel32<KL_K_EXP_SEPARABLE>(r[0] - c1[0], r[1] - c1[1], r[2] - c1[2], r[0], r[1], r[2], c1[0], c1[1],
+                                                  c1[2], 0);
+                f = df2::kernel32<KL_K_EXP_SEPARABLE>(dx, dy, dz);
+            }
+            bad += (__float_as_uint(f0) != __float_as_uint(df2::lo(f))) + (__float_as_uint(f1) != __float_as_uint(df2::hi(f)));
+            float t0[3], t1[3];
+            df2::V t[3];
+            tcs::slices3(f0, t0);
+            tcs::slices3(f1, t1);
+            df2::slices3(f, t);
+            for (int q = 0; q < 3; ++q)
+                bad += (__float_as_uint(t0[q]) != __float_as_uint(df2::lo(t[q]))) +
+                       (__float_as_uint(t1[q]) != __float_as_uint(df2::hi(t[q])));
         }
     }
     if (bad) atomicAdd(mismatches, bad);
