@@ -45,7 +45,9 @@ REDUCED = {"cube-p3-48^3-gauss-L0.3": "cube-p3-16^3-gauss-L0.3",
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel on the same
 # workload and vector count (profiles/stage5_dram_cube-p3-48^3-gauss.md); None where the kernel
 # changed after the capture
-TRAFFIC = {("tc64", "cube-p3-48^3-gauss-L0.3", 32): 61176576.0 + 29777920.0}
+TRAFFIC = {("tc64", "cube-p3-48^3-gauss-L0.3", 32): 61230592.0 + 29322240.0,
+           ("tc32", "cube-p3-48^3-gauss-L0.3", 32): 29455616.0 + 3426816.0,
+           ("fp32", "cube-p3-48^3-gauss-L0.3", 16): 10383616.0 + 58083584.0}
 
 
 def flops_per_eval(kind):
@@ -694,7 +696,8 @@ def main():
         g32 = max(nc32, -(-v32 // 16))
         rl["fp32"] = roofline_entry("covmv32_kernel (float32 stage 5, packed pair FMAs, %g-vector groups)" % (v32 / g32),
                                     "alu", w["kernel"], Nt, v32 / g32, v32 / g32 <= 8, info_c["ms_stage5_fp32"] / g32,
-                                    g32, ffma_flops, "measured float32 FMA rate x 2 (kl_pipe_rates, this run)")
+                                    g32, ffma_flops, "measured float32 FMA rate x 2 (kl_pipe_rates, this run)",
+                                    TRAFFIC.get(("fp32", args.workload, int(round(v32 / g32)))))
     nc64 = info_c["stage5_calls_tc64"]
     if nc64:
         nv64 = info_c["applies_tc64"] / nc64
@@ -710,7 +713,8 @@ def main():
         rl["tc32"] = roofline_entry(
             "covmv_tcx_kernel<32> (tensor-core float32 class, the polish's correction blocks)", "alu", w["kernel"],
             Nt, nvt, False, info_c["ms_stage5_tc32"] / nt32, nt32, ffma_flops,
-            "measured float32 FMA rate x 2 (kl_pipe_rates, this run): kernel values and slicing on the float32 pipe")
+            "measured float32 FMA rate x 2 (kl_pipe_rates, this run): kernel values and slicing on the float32 pipe",
+            TRAFFIC.get(("tc32", args.workload, int(round(nvt)))))
     share = {key: (info_c["ms_stage5_" + key] / ms_c) for key in ("fp32", "tc64", "tc32")}
     dom = max(rl, key=lambda key: share[key]) if rl else None
     roofline = dict(rl[dom]) if dom else None
