@@ -223,6 +223,7 @@ struct Phase {
     int exit_vecs;     // Ritz vectors left in V[:, 0:exit_vecs] on exit (>= k)
     int prec_next;     // arithmetic of every application after the phase's first (see run_phase)
     bool carry = true; // keep A~'V with the basis (false: a later phase recomputes the products)
+    bool skip_first_rr = false;   // no early Rayleigh-Ritz check after the phase's first block
 };
 
 // Runs one thick-restart block Lanczos phase.  On entry V[:, 0:j0] holds an orthonormal basis
@@ -274,7 +275,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                 full = true;
                 break;
             }
-            if (P.early_rr) {
+            if (P.early_rr && !(P.skip_first_rr && it == 0 && j == j0)) {
                 // Rayleigh-Ritz on the current basis, residual block = W (not yet normalised)
                 KL_TRY(E.sym_eig(j));
                 e = launch_gram(E.W(), E.N, b, E.W(), E.N, b, E.N, E.G(), b, E.Part(), E.maxparts, E.s);
@@ -776,6 +777,9 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
             // the active block is V[:, 0:pb]; T is rebuilt by the first expansion
             e = cudaMemsetAsync(E.T(), 0, sizeof(double) * cap_m * cap_m, s);
             if (e != cudaSuccess) return cuda_fail(e, "memset");
+            // the float32 Ritz block alone carries residuals of about tol_low: no check before the
+            // first correction block unless tol_low is within a decade of tol
+            P2.skip_first_rr = (pass == 0 && tl >= 10.0 * tol);
             KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
             if (!conv || P2.prec_next == P2.prec) break;
             // residuals ||A~'y - theta y|| of the k wanted Ritz vectors from their carried products
