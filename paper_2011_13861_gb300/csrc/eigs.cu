@@ -112,6 +112,11 @@ struct Eig {
         return KL_OK;
     }
 
+    // One pass of classical Gram-Schmidt and of Cholesky-QR instead of two (a phase whose own
+    // operator is float32-accurate: the orthogonality a single pass leaves, about eps64 times
+    // the norm drop ||W|| / ||W - V H|| or times cond(W)^2, is far below what it resolves)
+    bool one_pass = false;
+
     // H (j x b, ld mmax) = V[:, 0:j]^T W ; W -= V H   (twice); returns accumulated H in H()
     kl_status orthogonalize(double* Wb, int b, int j) {
         if (j == 0) return KL_OK;
@@ -119,6 +124,7 @@ struct Eig {
         if (e != cudaSuccess) return cuda_fail(e, "gram");
         e = launch_gemm_tall(-1.0, V(), N, N, j, H(), mmax, b, 1.0, Wb, N, s);
         if (e != cudaSuccess) return cuda_fail(e, "update");
+        if (one_pass) return KL_OK;
         e = launch_gram(V(), N, j, Wb, N, b, N, H2(), mmax, Part(), maxparts, s);
         if (e != cudaSuccess) return cuda_fail(e, "gram");
         e = launch_gemm_tall(-1.0, V(), N, N, j, H2(), mmax, b, 1.0, Wb, N, s);
@@ -135,6 +141,17 @@ struct Eig {
     kl_status cholqr(double* Wb, int b, double* dst, bool* deficient) {
         int flags[2] = {0, 0};
         double* cur = Wb;
+        if (one_pass && dst != Wb) {
+            cudaError_t e = launch_gram(Wb, N, b, Wb, N, b, N, G(), b, Part(), maxparts, s);
+            if (e == cudaSuccess) e = launch_chol_inv(G(), b, b, Rinv(), R(), Flag(), s);
+            if (e != cudaSuccess) return cuda_fail(e, "chol");
+            e = launch_gemm_tall(1.0, Wb, N, N, b, Rinv(), b, b, 0.0, dst, N, s);
+            if (e != cudaSuccess) return cuda_fail(e, "scale");
+            KL_CUDA(cudaMemcpyAsync(flags, Flag(), sizeof(int), cudaMemcpyDeviceToHost, s));
+            KL_CUDA(cudaStreamSynchronize(s));
+            *deficient = (flags[0] != 0);
+            return KL_OK;
+        }
         for (int pass = 0; pass < 2; ++pass) {
             cudaError_t e = launch_gram(cur, N, b, cur, N, b, N, G(), b, Part(), maxparts, s);
             if (e != cudaSuccess) return cuda_fail(e, "gram");
@@ -224,6 +241,7 @@ struct Phase {
     int prec_next;     // arithmetic of every application after the phase's first (see run_phase)
     bool carry = true; // keep A~'V with the basis (false: a later phase recomputes the products)
     bool skip_first_rr = false;   // no early Rayleigh-Ritz check after the phase's first block
+    bool one_pass = false;        // single-pass Gram-Schmidt and Cholesky-QR (Eig::one_pass)
 };
 
 // Runs one thick-restart block Lanczos phase.  On entry V[:, 0:j0] holds an orthonormal basis
@@ -249,6 +267,11 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
     *converged = false;
     theta.assign(m, 0.0);
     est.assign(m, 0.0);
+    struct OnePass {
+        Eig& e;
+        ~OnePass() { e.one_pass = false; }
+    } one_pass_guard{E};
+    E.one_pass = P.one_pass;
     bool first = true;
     int acc = 0;   // leading basis columns whose products are accurate (correction blocks only)
     for (int it = 0;; ++it) {
@@ -745,6 +768,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         const int lowp = (o.low_precision == KL_P_TC32) ? KL_P_TC32 : KL_P_FP32;
         Phase P1{lowp, b, m, keep, std::max(tl, tol), false, maxrestart, pb, lowp};
         P1.carry = false;   // the polish applies the operator to the Ritz block afresh
+        P1.one_pass = true;
         KL_TRY(run_phase(E, P1, k, b, &restarts, theta, est, &conv));
         if (lowp == KL_P_TC32) KL_TRY(check_device_status(h, s));
         KL_CUDA(cudaStreamSynchronize(s));
