@@ -196,9 +196,10 @@ cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64
                                 uint64_t offset, cudaStream_t s);
 // Symmetric eigen-decomposition of the m x m (m <= 160) matrix T (column-major, ld ldt) by
 // float64 parallel cyclic Jacobi in one CTA: sorted eigenvalues (descending) and eigenvectors S.
-// work: m^2 doubles.
+// work: m^2 doubles.  The double-float kernel (m <= 112) rotates a pair while its off-diagonal
+// entry exceeds off_tol sqrt(|T_aa T_bb|) (1e-14: to double-float accuracy).
 cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, double* S, int lds,
-                              double* work, int* sweeps_out, cudaStream_t s);
+                              double* work, int* sweeps_out, cudaStream_t s, float off_tol = 1e-14f);
 cudaError_t launch_residual_norms(const double* G, int ldg, const double* S, int lds, int srow0,
                                   int b, int ncols, double* out, cudaStream_t s);
 cudaError_t launch_ritz_resid(const double* AY, const double* Y, int64_t ld, int64_t N, int k,

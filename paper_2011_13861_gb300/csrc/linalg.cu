@@ -304,7 +304,7 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
 // with c = 1/sqrt(1 + t^2) and s = t c formed in double-float so that c^2 + s^2 = 1 to ~2^-48:
 // every rotation is orthogonal to double-float accuracy, and an off-diagonal entry that a
 // rotation leaves at ~2^-24 of its size is removed by the next sweep.  Sweeps stop when no
-// off-diagonal entry exceeds 1e-14 sqrt(|T_aa T_bb|).
+// off-diagonal entry exceeds off_tol sqrt(|T_aa T_bb|) (1e-14 by default).
 constexpr int kEigDfThreads = 512;
 constexpr int kEigDfMax = 112;
 
@@ -326,7 +326,7 @@ __device__ __forceinline__ void df_rotate(df::F2 c, df::F2 sn, float& xh, float&
 
 __global__ void __launch_bounds__(kEigDfThreads)
 sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restrict__ evals,
-                  double* __restrict__ Sout, int lds, int* sweeps_out) {
+                  double* __restrict__ Sout, int lds, int* sweeps_out, float off_tol) {
     extern __shared__ float sdf[];
     const int ld = m | 1;                       // odd stride: column accesses spread over banks
     float* Th = sdf;                            // T, row-major [m][ld]
@@ -359,7 +359,7 @@ sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __rest
                 if (b < m) {
                     const float apq = Th[a * ld + b];
                     const float app = Th[a * ld + a], aqq = Th[b * ld + b];
-                    if (apq != 0.f && fabsf(apq) > 1e-14f * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+                    if (apq != 0.f && fabsf(apq) > off_tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
                         const df::F2 d = df::sub(df::F2{Th[b * ld + b], Tl[b * ld + b]},
                                                  df::F2{Th[a * ld + a], Tl[a * ld + a]});
                         const float theta = d.h / (2.f * apq);
@@ -655,14 +655,14 @@ cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64
 }
 
 cudaError_t launch_sym_eig_ws(const double* T, int ldt, int m, double* evals, double* S, int lds,
-                              double* work, int* sweeps_out, cudaStream_t s) {
+                              double* work, int* sweeps_out, cudaStream_t s, float off_tol) {
     if (m > kEigMax || m < 1) return cudaErrorInvalidValue;
     if (m <= kEigDfMax) {
         const size_t smem = size_t(4) * m * (m | 1) * sizeof(float);
         cudaError_t e = cudaFuncSetAttribute(sym_eig_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(size_t(4) * kEigDfMax * (kEigDfMax | 1) * sizeof(float)));
         if (e != cudaSuccess) return e;
-        sym_eig_df_kernel<<<1, kEigDfThreads, smem, s>>>(T, ldt, m, evals, S, lds, sweeps_out);
+        sym_eig_df_kernel<<<1, kEigDfThreads, smem, s>>>(T, ldt, m, evals, S, lds, sweeps_out, off_tol);
         count_launches(1);
         return cudaGetLastError();
     }
