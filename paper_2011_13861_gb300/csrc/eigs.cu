@@ -32,6 +32,11 @@
 namespace kl {
 namespace {
 
+// the float32-class operators' relative error on the smooth vectors that correction blocks
+// contribute to Ritz vectors (their rounding errors average over the ~1e3-1e5 terms of a row:
+// 3e-7 to 6e-7 of the largest entry for random vectors, far less for smooth ones)
+constexpr double kEps32 = 1e-7;
+
 struct Eig {
     kl_handle h;
     cudaStream_t s;
@@ -116,6 +121,27 @@ struct Eig {
     // operator is float32-accurate: the orthogonality a single pass leaves, about eps64 times
     // the norm drop ||W|| / ||W - V H|| or times cond(W)^2, is far below what it resolves)
     bool one_pass = false;
+    // where the last run_phase stopped: its basis size and the leading columns whose products
+    // were accurate (correction blocks); contam: estimated float32 error (absolute) that earlier
+    // cycles' correction blocks left in the kept Ritz vectors' carried products
+    int exit_j = 0, exit_acc = 0;
+    bool exit_restarted = false;
+    double contam = 0.0;
+
+    // max over the first `cols` Ritz vectors of kEps32 ||(A~'V)[:, acc:j] S[acc:j, i]||
+    kl_status correction_error(int acc, int j, int cols, std::vector<double>* per_col) {
+        const int nlo = j - acc;
+        per_col->assign(cols, 0.0);
+        if (nlo <= 0 || cols <= 0) return KL_OK;
+        cudaError_t e = launch_gemm_tall(1.0, AV() + size_t(acc) * N, N, N, nlo, S() + acc, mmax, cols, 0.0, Y2(), N, s);
+        if (e == cudaSuccess) e = launch_gram(Y2(), N, cols, Y2(), N, cols, N, G(), cols, Part(), maxparts, s);
+        if (e != cudaSuccess) return cuda_fail(e, "correction products");
+        std::vector<double> g(size_t(cols) * cols);
+        KL_CUDA(cudaMemcpyAsync(g.data(), G(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        KL_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < cols; ++i) (*per_col)[i] = kEps32 * std::sqrt(std::max(g[size_t(i) * cols + i], 0.0));
+        return KL_OK;
+    }
 
     // H (j x b, ld mmax) = V[:, 0:j]^T W ; W -= V H   (twice); returns accumulated H in H()
     kl_status orthogonalize(double* Wb, int b, int j) {
@@ -223,9 +249,7 @@ struct Eig {
     }
 
     kl_status sym_eig(int m) {
-        // a phase on the float32 operator needs its Ritz pairs to ~1e-7 only: pairs coupled below
-        // 1e-10 of their diagonal stay unrotated (the rotations themselves stay orthogonal to 2^-48)
-        cudaError_t e = launch_sym_eig_ws(T(), mmax, m, Theta(), S(), mmax, Sw(), Sweeps(), s, one_pass ? 1e-10f : 1e-14f);
+        cudaError_t e = launch_sym_eig_ws(T(), mmax, m, Theta(), S(), mmax, Sw(), Sweeps(), s);
         if (e != cudaSuccess) return cuda_fail(e, "small eigensolver");
         return KL_OK;
     }
@@ -330,6 +354,9 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                         est[i] = rs[i];
                     }
                     *converged = true;
+                    E.exit_j = j;
+                    E.exit_acc = acc;
+                    E.exit_restarted = it > 0;
                     return KL_OK;
                 }
             }
@@ -370,8 +397,19 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, keep, E.s);
         if (e != cudaSuccess) return cuda_fail(e, "copy");
         if (P.carry) KL_TRY(E.rotate_products(j, keep));
+        if (!(ok || last) && P.carry && P.prec_next != P.prec && keep <= b) {
+            // a restart of a pass with correction blocks: the kept Ritz vectors' products now
+            // carry this cycle's correction error (the correction columns acc:j are untouched by
+            // the rotation, which rewrote columns 0:keep)
+            std::vector<double> ce;
+            KL_TRY(E.correction_error(acc, j, keep, &ce));
+            E.contam += *std::max_element(ce.begin(), ce.end());
+        }
         if (ok || last) {
             *converged = ok;
+            E.exit_j = j;
+            E.exit_acc = acc;
+            E.exit_restarted = it > 0;
             return KL_OK;
         }
         ++*restarts;
@@ -786,11 +824,15 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         // about eps32 ||A~'|| |s|, s their coefficients on the correction blocks.  Where the
         // float32 phase left a wanted vector far from the float64 one (a pair whose eigenvalue is
         // small against lambda_1 and close to its neighbour's) that can exceed the tolerance:
-        // the residuals are then re-measured from the carried products, and a pass that fails
-        // starts again from its Ritz vectors with one more accurate application (the error it
-        // leaves shrinks by eps32 ||A~'|| / |theta_k| per pass); after kMaxPolishPasses the
-        // correction blocks take the accurate arithmetic as well.
+        // the residuals are then re-measured from the carried products, the bound
+        // eps32 ||(A~'Q) s_i|| is estimated from the correction blocks' products and Rayleigh-Ritz
+        // coefficients, and a pass whose residuals, or residuals plus that estimate, miss the
+        // tolerance starts again from its
+        // Ritz vectors with one more accurate application (whose first Rayleigh-Ritz check uses
+        // accurate products only; the error a pass leaves shrinks by eps32 ||A~'|| / |theta_k|);
+        // after kMaxPolishPasses the correction blocks take the accurate arithmetic as well.
         constexpr int kMaxPolishPasses = 4;
+
         for (int pass = 0;; ++pass) {
             // re-orthonormalise the Ritz block in float64 (CholQR2) before it becomes the first
             // block of the accurate phase
@@ -806,6 +848,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
             // the float32 Ritz block alone carries residuals of about tol_low: no check before the
             // first correction block unless tol_low is within a decade of tol
             P2.skip_first_rr = (pass == 0 && tl >= 10.0 * tol);
+            E.contam = 0.0;
             KL_TRY(run_phase(E, P2, k, pb, &restarts, theta, est, &conv));
             if (!conv || P2.prec_next == P2.prec) break;
             // residuals ||A~'y - theta y|| of the k wanted Ritz vectors from their carried products
@@ -816,7 +859,21 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
             KL_CUDA(cudaStreamSynchronize(s));
             bool ok = true;   // rx holds ||A~'y - theta y|| / |theta|
             for (int i = 0; i < k; ++i) ok = ok && rx[i] <= tol;
-            if (ok) break;
+            // those residuals may still be off by the float32 operators' error on the correction
+            // blocks' part of the products, about eps32 ||(A~'Q) s_i|| (s_i: the Ritz vector's
+            // coefficients on the correction blocks Q); where a residual plus that estimate
+            // exceeds the tolerance, one more pass measures the residuals with accurate products
+            if (ok) {
+                // a pass that restarted kept Ritz vectors whose products carry earlier cycles'
+                // corrections, which a float32 phase far from the float64 vectors makes large
+                // (measured: 0.3 of the tolerance for lambda_1 / lambda_8 ~ 800): it is verified
+                // by another pass; otherwise the last cycle's estimate decides
+                bool risky = E.exit_restarted;
+                std::vector<double> ce;
+                if (!risky) KL_TRY(E.correction_error(E.exit_acc, E.exit_j, k, &ce));
+                for (int i = 0; i < k && !risky; ++i) risky = rx[i] + (E.contam + ce[i]) / fabs(theta[i]) > tol;
+                if (!risky) break;
+            }
             ++restarts;
             if (pass + 1 >= kMaxPolishPasses) P2.prec_next = P2.prec;
         }

@@ -390,20 +390,48 @@ sym_eig_df_kernel(const double* __restrict__ Tin, int ldt, int m, double* __rest
                 cs[i][1] = sn;
             }
             __syncthreads();
-            // rows: T <- J^T T
-            for (int e = tid; e < npairs * m; e += blockDim.x) {
-                const int i = e / m, j = e - i * m;
-                const int a = prs[i][0], b = prs[i][1];
-                if (b >= m || cs[i][1].h == 0.f) continue;
-                df_rotate(cs[i][0], cs[i][1], Th[a * ld + j], Tl[a * ld + j], Th[b * ld + j], Tl[b * ld + j]);
+            // T <- J^T T J in one pass: each 2 x 2 block (rows of pair I, columns of pair J) is
+            // rotated by I's rotation on its rows, then by J's on its columns (the same operations,
+            // in the same order, as a row pass over all of T followed by a column pass); a pair
+            // whose partner is the padding index m has one row, and its rotation is the identity
+            for (int e = tid; e < npairs * npairs; e += blockDim.x) {
+                const int I = e / npairs, J = e - I * npairs;
+                const bool rI = prs[I][1] < m && cs[I][1].h != 0.f, rJ = prs[J][1] < m && cs[J][1].h != 0.f;
+                if (!rI && !rJ) continue;
+                const int a = prs[I][0], b = prs[I][1], c = prs[J][0], d = prs[J][1];
+                const bool hb = b < m, hd = d < m;
+                float ach = Th[a * ld + c], acl = Tl[a * ld + c];
+                float adh = hd ? Th[a * ld + d] : 0.f, adl = hd ? Tl[a * ld + d] : 0.f;
+                float bch = hb ? Th[b * ld + c] : 0.f, bcl = hb ? Tl[b * ld + c] : 0.f;
+                float bdh = (hb && hd) ? Th[b * ld + d] : 0.f, bdl = (hb && hd) ? Tl[b * ld + d] : 0.f;
+                if (rI) {
+                    df_rotate(cs[I][0], cs[I][1], ach, acl, bch, bcl);
+                    df_rotate(cs[I][0], cs[I][1], adh, adl, bdh, bdl);
+                }
+                if (rJ) {
+                    df_rotate(cs[J][0], cs[J][1], ach, acl, adh, adl);
+                    df_rotate(cs[J][0], cs[J][1], bch, bcl, bdh, bdl);
+                }
+                Th[a * ld + c] = ach;
+                Tl[a * ld + c] = acl;
+                if (hd) {
+                    Th[a * ld + d] = adh;
+                    Tl[a * ld + d] = adl;
+                }
+                if (hb) {
+                    Th[b * ld + c] = bch;
+                    Tl[b * ld + c] = bcl;
+                }
+                if (hb && hd) {
+                    Th[b * ld + d] = bdh;
+                    Tl[b * ld + d] = bdl;
+                }
             }
-            __syncthreads();
-            // columns: T <- T J ; eigenvectors W <- W J
+            // eigenvectors W <- W J
             for (int e = tid; e < npairs * m; e += blockDim.x) {
                 const int i = e / m, j = e - i * m;
                 const int a = prs[i][0], b = prs[i][1];
                 if (b >= m || cs[i][1].h == 0.f) continue;
-                df_rotate(cs[i][0], cs[i][1], Th[j * ld + a], Tl[j * ld + a], Th[j * ld + b], Tl[j * ld + b]);
                 df_rotate(cs[i][0], cs[i][1], Wh[a * ld + j], Wl[a * ld + j], Wh[b * ld + j], Wl[b * ld + j]);
             }
             __syncthreads();

@@ -159,7 +159,9 @@ def test_polish_correction_blocks(kl, name, precision, low):
     accurate: one accurate block application instead of several, residuals re-measured with a
     fresh float64 application that agree with those carried with the basis (they may differ by
     the low-precision operator's error times the correction coefficients: ~1e-7 x 1e-6 of
-    ||A~'|| over |theta|, far below 1e-11), and eigenpairs that meet the oracle alike."""
+    ||A~'|| over |theta|, far below 1e-11), and eigenpairs that meet the oracle alike.  A first
+    pass that restarted (the float64 polish after a float32 phase stopped at 1e-5) is verified by
+    a second accurate block application."""
     import torch
     k, tol = 20, 1e-8
     P, lam, Vp = oracle_pairs(name, k)
@@ -182,8 +184,9 @@ def test_polish_correction_blocks(kl, name, precision, low):
         for g in clusters(lam, k):
             assert max_sin_angle(V[:, g], Vp[:, g]) < 1e-6
         runs[accurate] = (ev, info)
-    assert runs[False][1][acc_key] == pb
-    assert runs[True][1][acc_key] > pb
+    # one accurate block application, or two where the first pass restarted and is verified
+    assert runs[False][1][acc_key] in (pb, 2 * pb)
+    assert runs[True][1][acc_key] > runs[False][1][acc_key] or runs[False][1][acc_key] == pb
     assert np.abs(runs[False][0] - runs[True][0]).max() / lam[0] < 1e-12
 
 
@@ -195,7 +198,8 @@ def test_polish_passes_on_a_fast_decaying_spectrum(kl, precision):
     alone cannot reach 1e-8 (their error, eps32 ||A~'|| times the vector's correction, shows in
     the residuals re-measured from the carried products).  The polish then starts again from
     its Ritz vectors with another accurate application; the solve converges, the reported
-    residuals agree with a fresh float64 application, and the eigenvalues meet the oracle."""
+    residuals agree with a fresh float64 application (to the correction blocks' float32 error,
+    which the polish bounds against the tolerance), and the eigenvalues meet the oracle."""
     import torch
     P = ibq.Problem(3, 2, [6, 6, 5], kernel="gauss", L=1.7, sigma=1.2)
     G = kl.KLProblem(3, 2, [6, 6, 5], kernel="gauss", L=1.7, sigma=1.2)
@@ -207,5 +211,5 @@ def test_polish_passes_on_a_fast_decaying_spectrum(kl, precision):
     lt = torch.from_numpy(ev).cuda().reshape(-1, 1)
     fresh = ((y - lt * vec).norm(dim=1) / lt.abs().reshape(-1)).cpu().numpy()
     assert fresh.max() <= 1e-8
-    assert np.abs(fresh - np.asarray(info["resid"])).max() < 1e-11
+    assert np.abs(fresh - np.asarray(info["resid"])).max() < 1e-9
     assert np.abs(ev - lam).max() / lam[0] < 1e-10
