@@ -305,7 +305,7 @@ sym_eig_kernel(const double* __restrict__ Tin, int ldt, int m, double* __restric
 // every rotation is orthogonal to double-float accuracy, and an off-diagonal entry that a
 // rotation leaves at ~2^-24 of its size is removed by the next sweep.  Sweeps stop when no
 // off-diagonal entry exceeds off_tol sqrt(|T_aa T_bb|) (1e-14 by default).
-constexpr int kEigDfThreads = 512;
+constexpr int kEigDfThreads = 1024;
 constexpr int kEigDfMax = 112;
 
 __device__ __forceinline__ df::F2 df_from_double(double x) {
