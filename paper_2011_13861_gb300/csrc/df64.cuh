@@ -173,6 +173,46 @@ KL_HD F2 exp_neg(F2 x, const float* tab_h, const float* tab_l) {
     return F2{mul(R.h, scale), mul(R.l, scale)};
 }
 
+// A float64 value as a double-float h + l by integer operations on its bit pattern (no float64
+// instruction): h is the value truncated to 24 significant bits, l the rest truncated to 24, so
+// h + l equals x to within 2^-47 |x|.  Magnitudes below 2^-73 (where l could leave the normal
+// float range) or from 2^128 on use the float conversion instead.
+KL_HD F2 split_double_bits(double x) {
+    unsigned long long u;
+#if defined(__CUDA_ARCH__)
+    u = static_cast<unsigned long long>(__double_as_longlong(x));
+#else
+    __builtin_memcpy(&u, &x, 8);
+#endif
+    const unsigned sign = unsigned(u >> 32) & 0x80000000u;
+    const int e = int((u >> 52) & 0x7FF) - 1023;
+    if (e < -73 || e > 127) {
+        const float h = float(x);
+        return F2{h, float(x - double(h))};
+    }
+    const unsigned hb = sign | (unsigned(e + 127) << 23) | (unsigned(u >> 29) & 0x7FFFFFu);
+    const unsigned m29 = unsigned(u) & 0x1FFFFFFFu;   // the 29 bits below h's last
+    unsigned lb = 0;
+    if (m29 != 0) {
+#if defined(__CUDA_ARCH__)
+        const int lz = __clz(int(m29)) - 3;             // leading zeros within the 29 bits
+#else
+        const int lz = __builtin_clz(m29) - 3;
+#endif
+        const int el = e - 52 + 28 - lz;                // exponent of l's leading bit
+        lb = sign | (unsigned(el + 127) << 23) | (((m29 << lz) >> 5) & 0x7FFFFFu);   // el >= e - 52 >= -125
+    }
+    float h, l;
+#if defined(__CUDA_ARCH__)
+    h = __uint_as_float(hb);
+    l = __uint_as_float(lb);
+#else
+    __builtin_memcpy(&h, &hb, 4);
+    __builtin_memcpy(&l, &lb, 4);
+#endif
+    return F2{h, l};
+}
+
 // |a|^2 + |b|^2 + |c|^2 of three normalised double-floats: exact head squares, their sum by
 // Fast2Sum on ordered (non-negative) operands, and one tail of the product errors, the cross
 // terms 2 h l and the two sums' errors (the l^2 terms are below 2^-48 of the result).

@@ -121,6 +121,17 @@ struct Eig {
     // operator is float32-accurate: the orthogonality a single pass leaves, about eps64 times
     // the norm drop ||W|| / ||W - V H|| or times cond(W)^2, is far below what it resolves)
     bool one_pass = false;
+    // the products of the basis: float64, or double-float on the float32 pipe where one_pass (the
+    // float32 phase, whose operator resolves neither)
+    cudaError_t gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q, double* out, int ldo) {
+        return one_pass ? launch_gram_df(A, lda, p, B, ldb, q, N, out, ldo, Part(), maxparts, s)
+                        : launch_gram(A, lda, p, B, ldb, q, N, out, ldo, Part(), maxparts, s);
+    }
+    cudaError_t gemm(double alpha, const double* A, int64_t lda, int p, const double* B, int ldb, int q, double beta,
+                     double* C, int64_t ldc) {
+        return one_pass ? launch_gemm_tall_df(alpha, A, lda, N, p, B, ldb, q, beta, C, ldc, s)
+                        : launch_gemm_tall(alpha, A, lda, N, p, B, ldb, q, beta, C, ldc, s);
+    }
     // where the last run_phase stopped: its basis size and the leading columns whose products
     // were accurate (correction blocks); contam: estimated float32 error (absolute) that earlier
     // cycles' correction blocks left in the kept Ritz vectors' carried products
@@ -146,9 +157,9 @@ struct Eig {
     // H (j x b, ld mmax) = V[:, 0:j]^T W ; W -= V H   (twice); returns accumulated H in H()
     kl_status orthogonalize(double* Wb, int b, int j) {
         if (j == 0) return KL_OK;
-        cudaError_t e = launch_gram(V(), N, j, Wb, N, b, N, H(), mmax, Part(), maxparts, s);
+        cudaError_t e = gram(V(), N, j, Wb, N, b, H(), mmax);
         if (e != cudaSuccess) return cuda_fail(e, "gram");
-        e = launch_gemm_tall(-1.0, V(), N, N, j, H(), mmax, b, 1.0, Wb, N, s);
+        e = gemm(-1.0, V(), N, j, H(), mmax, b, 1.0, Wb, N);
         if (e != cudaSuccess) return cuda_fail(e, "update");
         if (one_pass) return KL_OK;
         e = launch_gram(V(), N, j, Wb, N, b, N, H2(), mmax, Part(), maxparts, s);
@@ -168,10 +179,10 @@ struct Eig {
         int flags[2] = {0, 0};
         double* cur = Wb;
         if (one_pass && dst != Wb) {
-            cudaError_t e = launch_gram(Wb, N, b, Wb, N, b, N, G(), b, Part(), maxparts, s);
+            cudaError_t e = gram(Wb, N, b, Wb, N, b, G(), b);
             if (e == cudaSuccess) e = launch_chol_inv(G(), b, b, Rinv(), R(), Flag(), s);
             if (e != cudaSuccess) return cuda_fail(e, "chol");
-            e = launch_gemm_tall(1.0, Wb, N, N, b, Rinv(), b, b, 0.0, dst, N, s);
+            e = gemm(1.0, Wb, N, b, Rinv(), b, b, 0.0, dst, N);
             if (e != cudaSuccess) return cuda_fail(e, "scale");
             KL_CUDA(cudaMemcpyAsync(flags, Flag(), sizeof(int), cudaMemcpyDeviceToHost, s));
             KL_CUDA(cudaStreamSynchronize(s));
@@ -327,7 +338,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
             if (P.early_rr && !(P.skip_first_rr && it == 0 && j == j0)) {
                 // Rayleigh-Ritz on the current basis, residual block = W (not yet normalised)
                 KL_TRY(E.sym_eig(j));
-                e = launch_gram(E.W(), E.N, b, E.W(), E.N, b, E.N, E.G(), b, E.Part(), E.maxparts, E.s);
+                e = E.gram(E.W(), E.N, b, E.W(), E.N, b, E.G(), b);
                 if (e != cudaSuccess) return cuda_fail(e, "gram");
                 const int nc = std::min(j, k);
                 e = launch_residual_norms(E.G(), b, E.S(), E.mmax, j - b, b, nc, E.Est(), E.s);
@@ -344,7 +355,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                 if (ok) {
                     // Ritz vectors into V[:, 0:ke]
                     const int ke = std::min(std::max(k, P.exit_vecs), j);
-                    e = launch_gemm_tall(1.0, E.V(), E.N, E.N, j, E.S(), E.mmax, ke, 0.0, E.Y(), E.N, E.s);
+                    e = E.gemm(1.0, E.V(), E.N, j, E.S(), E.mmax, ke, 0.0, E.Y(), E.N);
                     if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
                     e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, ke, E.s);
                     if (e != cudaSuccess) return cuda_fail(e, "copy");
@@ -376,7 +387,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         }
         // ---- Rayleigh-Ritz on the full basis ----
         KL_TRY(E.sym_eig(j));
-        cudaError_t e = launch_gram(E.W(), E.N, b, E.W(), E.N, b, E.N, E.G(), b, E.Part(), E.maxparts, E.s);
+        cudaError_t e = E.gram(E.W(), E.N, b, E.W(), E.N, b, E.G(), b);
         if (e != cudaSuccess) return cuda_fail(e, "gram");
         const int nk = std::min(P.keep, j);
         e = launch_residual_norms(E.G(), b, E.S(), E.mmax, j - b, b, nk, E.Est(), E.s);
@@ -392,7 +403,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         const bool last = (it >= P.maxrestart);
         const int keep = ok || last ? std::min(std::max(k, P.exit_vecs), j) : P.keep;
         // Ritz vectors V S[:, 0:keep] -> Y -> V[:, 0:keep]
-        e = launch_gemm_tall(1.0, E.V(), E.N, E.N, j, E.S(), E.mmax, keep, 0.0, E.Y(), E.N, E.s);
+        e = E.gemm(1.0, E.V(), E.N, j, E.S(), E.mmax, keep, 0.0, E.Y(), E.N);
         if (e != cudaSuccess) return cuda_fail(e, "ritz vectors");
         e = launch_copy_block(E.Y(), E.N, E.V(), E.N, E.N, keep, E.s);
         if (e != cudaSuccess) return cuda_fail(e, "copy");

@@ -190,6 +190,13 @@ int gram_parts(int64_t N);
 cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t N, int p,
                              const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
                              cudaStream_t s);
+// the same two products in double-float arithmetic on the float32 pipe (about 2^-46 of each
+// result's magnitude): for phases whose operator is float32-accurate
+cudaError_t launch_gram_df(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
+                           int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s);
+cudaError_t launch_gemm_tall_df(double alpha, const double* A, int64_t lda, int64_t N, int p,
+                                const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
+                                cudaStream_t s);
 cudaError_t launch_chol_inv(double* G, int ldg, int b, double* Rinv, double* R, int* flag,
                             cudaStream_t s);
 cudaError_t launch_random_block(double* V, int64_t ldv, int64_t N, int b, uint64_t seed,

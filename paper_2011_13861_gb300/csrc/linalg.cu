@@ -127,6 +127,128 @@ gemm_tall_kernel(double alpha, const double* __restrict__ A, int64_t lda, int64_
     }
 }
 
+// ---- the same two products in double-float arithmetic on the float32 pipe ----
+// For a phase whose operator is float32-accurate: every float64 input is split by integer
+// operations into a double-float (split_double_bits, within 2^-47), each product term is the
+// exact float32 product of the heads plus the two cross terms, and the sums are double-float
+// (TwoSum into the head, tail accumulated, renormalised every staged chunk of rows), so a Gram
+// entry or an updated basis entry carries about 2^-46 of its magnitude's error.  GB300's float32
+// pipe runs ~65x the float64 pipe's FMA rate; a term costs 12 float32 operations.
+__device__ __forceinline__ void df_madd(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float pe = __fmaf_rn(ah, bh, -p);
+    const float cr = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pe));
+    const float s = __fadd_rn(sh, p);
+    const float bb = __fsub_rn(s, sh);
+    const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(e, cr));
+}
+
+__device__ __forceinline__ void df_renorm(float& sh, float& sl) {
+    const float s = __fadd_rn(sh, sl);
+    sl = __fsub_rn(sl, __fsub_rn(s, sh));
+    sh = s;
+}
+
+__global__ void __launch_bounds__(kGramThreads)
+gram_partial_df(const double* __restrict__ A, int64_t lda, int p, const double* __restrict__ B,
+                int64_t ldb, int q, int64_t N, int64_t rows_per_part, double* __restrict__ part) {
+    extern __shared__ float2 sgdf[];
+    const int la = gram_ld(p), lb = gram_ld(q);
+    float2* sA = sgdf;                        // [kGramRows][la] (head, tail)
+    float2* sB = sgdf + kGramRows * la;       // [kGramRows][lb]
+    const int outs = p * q;
+    constexpr int kMaxPer = (kGramMaxP * kGramMaxQ + kGramThreads - 1) / kGramThreads;
+    float acch[kMaxPer], accl[kMaxPer];
+#pragma unroll
+    for (int t = 0; t < kMaxPer; ++t) acch[t] = accl[t] = 0.f;
+    const int64_t r_begin = int64_t(blockIdx.x) * rows_per_part;
+    int64_t r_end = r_begin + rows_per_part;
+    if (r_end > N) r_end = N;
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += kGramRows) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kGramRows * p; e += kGramThreads) {
+            const int c = e / kGramRows, rl = e - c * kGramRows;
+            const int64_t r = r0 + rl;
+            const df::F2 v = df::split_double_bits((r < r_end) ? A[c * lda + r] : 0.0);
+            sA[rl * la + c] = make_float2(v.h, v.l);
+        }
+        for (int e = threadIdx.x; e < kGramRows * q; e += kGramThreads) {
+            const int c = e / kGramRows, rl = e - c * kGramRows;
+            const int64_t r = r0 + rl;
+            const df::F2 v = df::split_double_bits((r < r_end) ? B[c * ldb + r] : 0.0);
+            sB[rl * lb + c] = make_float2(v.h, v.l);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kMaxPer; ++t) {
+            const int e = threadIdx.x + t * kGramThreads;
+            if (e < outs) {
+                const int i = e / q, j = e - i * q;
+                float sh = acch[t], sl = accl[t];
+#pragma unroll 4
+                for (int rr = 0; rr < kGramRows; ++rr) {
+                    const float2 a = sA[rr * la + i], b = sB[rr * lb + j];
+                    df_madd(sh, sl, a.x, a.y, b.x, b.y);
+                }
+                df_renorm(sh, sl);
+                acch[t] = sh;
+                accl[t] = sl;
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kMaxPer; ++t) {
+        const int e = threadIdx.x + t * kGramThreads;
+        if (e < outs) part[int64_t(blockIdx.x) * outs + e] = double(acch[t]) + double(accl[t]);
+    }
+}
+
+template <int QB>
+__global__ void __launch_bounds__(128)
+gemm_tall_df_kernel(double alpha, const double* __restrict__ A, int64_t lda, int64_t N, int p,
+                    const double* __restrict__ B, int ldb, int q, double beta, double* __restrict__ C,
+                    int64_t ldc) {
+    extern __shared__ float2 sBdf[];   // p x (ng * QB), row-major (head, tail)
+    const int ng = (q + QB - 1) / QB, lq = ng * QB;
+    for (int e = threadIdx.x; e < p * lq; e += blockDim.x) {
+        const int i = e / lq, j = e - i * lq;
+        const df::F2 v = df::split_double_bits((j < q) ? B[i + int64_t(j) * ldb] : 0.0);
+        sBdf[e] = make_float2(v.h, v.l);
+    }
+    __syncthreads();
+    const int64_t items = N * ng;
+    for (int64_t it = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; it < items;
+         it += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t g = it / N, r = it - g * N;
+        const int j0 = int(g) * QB;
+        float sh[QB], sl[QB];
+#pragma unroll
+        for (int j = 0; j < QB; ++j) sh[j] = sl[j] = 0.f;
+        for (int i = 0; i < p; ++i) {
+            const df::F2 a = df::split_double_bits(A[i * lda + r]);
+#pragma unroll
+            for (int j = 0; j < QB; ++j) {
+                const float2 b = sBdf[i * lq + j0 + j];
+                df_madd(sh[j], sl[j], a.h, a.l, b.x, b.y);
+            }
+            if ((i & 15) == 15) {
+#pragma unroll
+                for (int j = 0; j < QB; ++j) df_renorm(sh[j], sl[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < QB; ++j) {
+            if (j0 + j < q) {
+                double* c = C + (j0 + j) * ldc + r;
+                const double v = double(sh[j]) + double(sl[j]);
+                *c = (beta == 0.0) ? alpha * v : fma(alpha, v, beta * (*c));
+            }
+        }
+    }
+}
+
 // G (b x b, column-major) = R^T R with R upper triangular; also R^{-1}.  One CTA.
 // flag is set to 1 when a pivot is not positive (rank-deficient block).
 __global__ void chol_inv_kernel(const double* __restrict__ G, int ldg, int b, double* __restrict__ Rinv,
@@ -600,8 +722,9 @@ int gram_parts(int64_t N) {
     return int(parts);
 }
 
-cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
-                        int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s) {
+template <bool DF>
+cudaError_t gram_impl(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
+                      int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s) {
     if (p > kGramMaxP) return cudaErrorInvalidValue;
     if (p == 0 || q == 0) return cudaSuccess;
     int parts = gram_parts(N);
@@ -612,15 +735,16 @@ cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, in
     if (parts < 1) parts = 1;
     for (int j0 = 0; j0 < q; j0 += kGramMaxQ) {
         const int qq = (q - j0 < kGramMaxQ) ? q - j0 : kGramMaxQ;
-        const size_t smem = size_t(kGramRows) * (gram_ld(p) + gram_ld(qq)) * sizeof(double);
+        const size_t smem = size_t(kGramRows) * (gram_ld(p) + gram_ld(qq)) * sizeof(double);   // = float2 too
+        auto kern = DF ? gram_partial_df : gram_partial;
         if (smem > 48 * 1024) {
             // the largest request ever (set, never lowered: launches of other threads stay valid)
             const int smax = int(size_t(kGramRows) * (gram_ld(kGramMaxP) + gram_ld(kGramMaxQ)) * sizeof(double));
-            cudaError_t e = cudaFuncSetAttribute(gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
             if (e != cudaSuccess) return e;
         }
         count_launches(2);
-        gram_partial<<<parts, kGramThreads, smem, s>>>(A, lda, p, B + int64_t(j0) * ldb, ldb, qq, N, rpp, part);
+        kern<<<parts, kGramThreads, smem, s>>>(A, lda, p, B + int64_t(j0) * ldb, ldb, qq, N, rpp, part);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         gram_reduce<<<(p * qq + 31) / 32, 256, 0, s>>>(part, parts, p, qq, out + int64_t(j0) * ldo, ldo);
@@ -630,9 +754,10 @@ cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, in
     return cudaSuccess;
 }
 
-cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t N, int p,
-                             const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
-                             cudaStream_t s) {
+template <bool DF>
+cudaError_t gemm_tall_impl(double alpha, const double* A, int64_t lda, int64_t N, int p,
+                           const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
+                           cudaStream_t s) {
     if (N == 0 || q == 0) return cudaSuccess;
     if (p == 0) {
         // C = beta * C
@@ -649,23 +774,38 @@ cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t
         count_launches(1);
         double* Cj = C + int64_t(j0) * ldc;
         cudaError_t e = cudaSuccess;
-        if (QB == 1) {
-            if (smem > 48 * 1024)
-                e = cudaFuncSetAttribute(gemm_tall_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGemmMaxSmem);
-            if (e != cudaSuccess) return e;
-            gemm_tall_kernel<1><<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
-        } else {
-            if (smem > 48 * 1024)
-                e = cudaFuncSetAttribute(gemm_tall_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kGemmMaxSmem);
-            if (e != cudaSuccess) return e;
-            gemm_tall_kernel<4><<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
-        }
+        auto kern = (QB == 1) ? (DF ? gemm_tall_df_kernel<1> : gemm_tall_kernel<1>)
+                              : (DF ? gemm_tall_df_kernel<4> : gemm_tall_kernel<4>);
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmMaxSmem);
+        if (e != cudaSuccess) return e;
+        kern<<<blocks, 128, smem, s>>>(alpha, A, lda, N, p, Bj, ldb, qq, beta, Cj, ldc);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_gram(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
+                        int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s) {
+    return gram_impl<false>(A, lda, p, B, ldb, q, N, out, ldo, part, maxparts, s);
+}
+
+cudaError_t launch_gram_df(const double* A, int64_t lda, int p, const double* B, int64_t ldb, int q,
+                           int64_t N, double* out, int ldo, double* part, int maxparts, cudaStream_t s) {
+    return gram_impl<true>(A, lda, p, B, ldb, q, N, out, ldo, part, maxparts, s);
+}
+
+cudaError_t launch_gemm_tall(double alpha, const double* A, int64_t lda, int64_t N, int p,
+                             const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
+                             cudaStream_t s) {
+    return gemm_tall_impl<false>(alpha, A, lda, N, p, B, ldb, q, beta, C, ldc, s);
+}
+
+cudaError_t launch_gemm_tall_df(double alpha, const double* A, int64_t lda, int64_t N, int p,
+                                const double* B, int ldb, int q, double beta, double* C, int64_t ldc,
+                                cudaStream_t s) {
+    return gemm_tall_impl<true>(alpha, A, lda, N, p, B, ldb, q, beta, C, ldc, s);
 }
 
 cudaError_t launch_chol_inv(double* G, int ldg, int b, double* Rinv, double* R, int* flag,

@@ -72,8 +72,28 @@ int main() {
         const long double ref = sqrtl(val(af));
         sqrt_rel = std::fmax(sqrt_rel, (double)fabsl((val(r) - ref) / ref));
     }
+    // float64 -> double-float by bit operations: magnitudes from 2^-72 to 2^127, both signs,
+    // exact powers of two and values with few significant bits
+    double split_rel = 0;
+    int split_head_wrong = 0;
+    for (int i = 0; i < 600000; ++i) {
+        double x = std::ldexp(0.5 + 0.5 * U(rng), int(-71 + 198 * U(rng)));
+        if (i % 7 == 1) x = -x;
+        if (i % 11 == 2) x = std::ldexp(1.0, int(-72 + 199 * U(rng)));
+        if (i % 13 == 3) x = std::ldexp(std::floor(U(rng) * 4096.0) + 1.0, int(-60 + 120 * U(rng)));
+        const F2 f = split_double_bits(x);
+        const long double v = (long double)f.h + (long double)f.l;
+        split_rel = std::fmax(split_rel, (double)fabsl((v - (long double)x) / (long double)x));
+        // the head is x truncated to 24 significant bits: |x - h| < ulp(h), same sign
+        const long double r = (long double)x - (long double)f.h;
+        if (fabsl(r) >= std::ldexp(std::fabs((double)f.h), -23) || (r != 0 && (r > 0) != (x > 0))) ++split_head_wrong;
+    }
+    const F2 z = split_double_bits(0.0), tiny = split_double_bits(1e-300), big = split_double_bits(-3e300);
+    const int split_edges_ok = (z.h == 0.f && z.l == 0.f && tiny.h == 0.f && std::isinf(big.h) && big.h < 0) ? 1 : 0;
     std::printf("{\"exp_rel\": %.6e, \"exp_abs\": %.6e, \"exp_unnormalised\": %d, \"inexact_heads\": %d, "
-                "\"diff_abs\": %.6e, \"sum_sq_rel\": %.6e, \"sqrt_rel\": %.6e}\n",
-                exp_rel, exp_abs, exp_unnormalised, inexact_heads, diff_abs, sq_rel, sqrt_rel);
+                "\"diff_abs\": %.6e, \"sum_sq_rel\": %.6e, \"sqrt_rel\": %.6e, \"split_rel\": %.6e, "
+                "\"split_head_wrong\": %d, \"split_edges_ok\": %d}\n",
+                exp_rel, exp_abs, exp_unnormalised, inexact_heads, diff_abs, sq_rel, sqrt_rel, split_rel,
+                split_head_wrong, split_edges_ok);
     return 0;
 }

@@ -48,3 +48,11 @@ def test_square_root_from_an_approximate_seed(report):
     # double-float Heron correction is about 2^-22 of the root and carries that relative error,
     # so the root is good to about 2^-44.5 (4e-14), not to the 2^-48 of the representation
     assert report["sqrt_rel"] < 6e-14
+
+
+def test_float64_split_by_bit_operations(report):
+    # head: x truncated to 24 significant bits; head + tail within 2^-47 of x for magnitudes from
+    # 2^-72 to 2^127 (below and above, the float conversion)
+    assert report["split_head_wrong"] == 0
+    assert report["split_rel"] <= 2.0 ** -47
+    assert report["split_edges_ok"] == 1
