@@ -753,7 +753,7 @@ def main():
     line = {
         "metric": METRIC, "value": ms_c / 1e3, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_c, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 + f64-class (bf16 tcgen05 slices); f64 solver",
+        "vs_baseline": None, "dtype": "f32 + f64-class (bf16 tcgen05 slices); f64 polish solver, df64 float32-phase basis products",
         "data": "synthetic",
         "config": {"workload": args.workload, "dim": w["dim"], "degree": w["p"], "elements": w["ne"],
                    "kernel": w["kernel"], "L": w["L"], "sigma": w["sigma"], "N": N, "Ntilde": Nt, "k": k,
