@@ -153,6 +153,16 @@ static kl_status forward_generic(kl_handle h, const double* v, int64_t ldv, Tout
     const void* cur = v;
     int64_t ldcur = ldv;
     bool cur_is_double = true;
+    if (sizeof(Tc) == sizeof(float) && d > 0) {
+        // float32 arithmetic: round the input to float once (the same rounding the mode pass
+        // would apply to every element it reads, n_1 times each) into the buffer mode 0 does not
+        // write; mode 0 then runs float to float
+        cudaError_t e = launch_to_float(v, ldv, static_cast<float*>(bufB), ld, h->N, nvec, s);
+        if (e != cudaSuccess) return cuda_fail(e, "forward contraction");
+        cur = bufB;
+        ldcur = ld;
+        cur_is_double = false;
+    }
     for (int k = 0; k < d; ++k) {
         int64_t A = 1, B = 1;
         for (int i = k + 1; i < d; ++i) A *= h->n[i];
