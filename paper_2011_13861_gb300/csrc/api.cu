@@ -6,9 +6,6 @@
 #include <chrono>
 #include <type_traits>
 #include <cstring>
-#include <map>
-#include <mutex>
-#include <tuple>
 #include <string>
 #include <vector>
 
@@ -282,66 +279,6 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
                                covmv_splits(h->Nt, nvec, true), s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "stage-5 kernel product");
-    return KL_OK;
-}
-
-// The float32-class stage 5 for a block of nvec vectors: the CUDA-core kernel (KL_P_FP32, groups
-// of up to 16 vectors) or the tensor-core one (KL_P_TC32, one launch for up to 32), whichever ran
-// faster when both were timed on a zero block of this size and kernel kind (each launched twice,
-// the second timed with CUDA events on `s`).  The outcome is kept for the process, per
-// (Ntilde, kernel kind, nvec): later handles of the same problem size reuse it.
-kl_status choose_f32_class(kl_handle h, int nvec, cudaStream_t s, int* precision) {
-    using Key = std::tuple<int64_t, int, int>;
-    static std::mutex mu;
-    static std::map<Key, int> chosen;
-    const Key key{h->Nt, h->kernel.kind, nvec};
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        const auto it = chosen.find(key);
-        if (it != chosen.end()) {
-            *precision = it->second;
-            return KL_OK;
-        }
-    }
-    DevBuf bu, bz;
-    struct Release {
-        DevBuf &a, &b;
-        ~Release() {
-            release(a);
-            release(b);
-        }
-    } rel{bu, bz};
-    const size_t bytes = size_t(h->Nt) * nvec * sizeof(double);
-    KL_TRY(ensure(bu, bytes));
-    KL_TRY(ensure(bz, bytes));
-    KL_CUDA(cudaMemsetAsync(bu.ptr, 0, bytes, s));
-    const double* u = static_cast<const double*>(bu.ptr);
-    double* z = static_cast<double*>(bz.ptr);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    KL_CUDA(cudaEventCreate(&e0));
-    cudaError_t ce = cudaEventCreate(&e1);
-    if (ce != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return cuda_fail(ce, "event");
-    }
-    float ms[2] = {0.f, 0.f};
-    const int cand[2] = {KL_P_FP32, KL_P_TC32};
-    kl_status st = KL_OK;
-    for (int c = 0; c < 2 && st == KL_OK; ++c) {
-        st = covmv_impl(h, cand[c], u, h->Nt, z, h->Nt, nvec, true, s);
-        if (st == KL_OK && cudaEventRecord(e0, s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
-        if (st == KL_OK) st = covmv_impl(h, cand[c], u, h->Nt, z, h->Nt, nvec, true, s);
-        if (st == KL_OK && cudaEventRecord(e1, s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
-        if (st == KL_OK && cudaEventSynchronize(e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
-        if (st == KL_OK && cudaEventElapsedTime(&ms[c], e0, e1) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "event");
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    KL_TRY(st);
-    KL_TRY(check_device_status(h, s));
-    *precision = (ms[1] < ms[0]) ? KL_P_TC32 : KL_P_FP32;
-    std::lock_guard<std::mutex> lock(mu);
-    chosen[key] = *precision;
     return KL_OK;
 }
 

@@ -826,11 +826,12 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         ms32 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         // polish: V[:, 0:pb] holds the leading float32 Ritz vectors (orthonormal in float64);
         // they form the first, wide block of a float64 block Lanczos run.
-        // the correction blocks take the float32 class; for blocks wider than 16 vectors the
-        // faster of the CUDA-core kernel (16-wide groups) and the tensor-core one (one launch for
-        // up to 32 vectors; 23.1 ms against 2 x 13.6 ms at 132,651 points), timed once
-        int corr_p = lowp;
-        if (lowp == KL_P_FP32 && pb > 16 && !o.polish_accurate) KL_TRY(choose_f32_class(h, pb, s, &corr_p));
+        // the correction blocks take the float32 class; blocks wider than 16 vectors run on the
+        // tensor-core float32 kernel (one launch for up to 32 vectors, measured 23.1 ms against
+        // 2 x 13.6 ms for the CUDA-core kernel's two 16-wide groups at 132,651 points, 2.3 against
+        // 2.9 ms at 39,304; for many small instances solved together, 1.53 s against 2.4 s with
+        // the CUDA-core kernel's shared launches)
+        const int corr_p = (lowp == KL_P_FP32 && pb > 16) ? KL_P_TC32 : lowp;
         Phase P2{o.precision, pb, pol_m, pb, tol, true, maxrestart, pb, o.polish_accurate ? o.precision : corr_p};
         // With float32 correction blocks the residuals carried with the Ritz vectors are off by
         // about eps32 ||A~'|| |s|, s their coefficients on the correction blocks.  Where the

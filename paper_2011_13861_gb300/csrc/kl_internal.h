@@ -288,9 +288,6 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
 kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, int64_t ldy,
                         int nvec, bool zHasJ, cudaStream_t s);
 kl_status check_device_status(kl_handle h, cudaStream_t s);
-// KL_P_FP32 or KL_P_TC32 for a float32-class block of nvec vectors: the faster of the two when
-// timed once per (Ntilde, kernel kind, nvec) in this process
-kl_status choose_f32_class(kl_handle h, int nvec, cudaStream_t s, int* precision);
 kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host,
                     double* evecs_dev, int64_t ldv, kl_eig_info* info, cudaStream_t s);
 
