@@ -16,7 +16,9 @@
 // Method 1 ("mixed") runs the iteration with the float32 stage-5 kernel until the estimates
 // reach tol_low, then continues from the float32 Ritz vectors in one wide block (b = number
 // of kept vectors), which converges in a few block steps: the first block takes the float64
-// (-class) operator, the correction blocks after it the float32 one (see run_phase).
+// (-class) operator, the correction blocks after it the float32 one (see run_phase).  The
+// float32 phase orthogonalises with one pass of Gram-Schmidt and of Cholesky-QR and forms its
+// basis products in double-float on the float32 pipe; the polish keeps two float64 passes.
 // Everything stays on the device; per restart the host reads back the Ritz values and
 // residual estimates of the wanted pairs (a few hundred bytes).
 #include <math.h>
