@@ -131,9 +131,18 @@ CovParams cov_params(kl_handle h) {
 
 CovParams cov_params_of(kl_handle h) { return cov_params(h); }
 
+kl_status host_wait(kl_handle h, cudaStream_t s) {
+    if (!h->batch) return KL_OK;
+    if (!h->host_sync) KL_CUDA(cudaEventCreateWithFlags(&h->host_sync, cudaEventBlockingSync | cudaEventDisableTiming));
+    KL_CUDA(cudaEventRecord(h->host_sync, s));
+    KL_CUDA(cudaEventSynchronize(h->host_sync));
+    return KL_OK;
+}
+
 // Reads (and clears) the device status word written by kernels with bounded waits.
 kl_status check_device_status(kl_handle h, cudaStream_t s) {
     int st = 0;
+    KL_TRY(host_wait(h, s));
     KL_CUDA(cudaMemcpyAsync(&st, h->dStatus, sizeof(int), cudaMemcpyDeviceToHost, s));
     KL_CUDA(cudaStreamSynchronize(s));
     if (st != 0) {
@@ -719,6 +728,7 @@ void kl_destroy(kl_handle h) {
     release(h->w_part);
     release(h->w_tcimg);
     if (h->batch_ready) cudaEventDestroy(h->batch_ready);
+    if (h->host_sync) cudaEventDestroy(h->host_sync);
     for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
     delete h;
 }

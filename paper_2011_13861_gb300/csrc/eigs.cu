@@ -150,6 +150,7 @@ struct Eig {
         if (e == cudaSuccess) e = launch_gram(Y2(), N, cols, Y2(), N, cols, N, G(), cols, Part(), maxparts, s);
         if (e != cudaSuccess) return cuda_fail(e, "correction products");
         std::vector<double> g(size_t(cols) * cols);
+        KL_TRY(host_wait(h, s));
         KL_CUDA(cudaMemcpyAsync(g.data(), G(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         KL_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < cols; ++i) (*per_col)[i] = kEps32 * std::sqrt(std::max(g[size_t(i) * cols + i], 0.0));
@@ -186,6 +187,7 @@ struct Eig {
             if (e != cudaSuccess) return cuda_fail(e, "chol");
             e = gemm(1.0, Wb, N, b, Rinv(), b, b, 0.0, dst, N);
             if (e != cudaSuccess) return cuda_fail(e, "scale");
+            KL_TRY(host_wait(h, s));
             KL_CUDA(cudaMemcpyAsync(flags, Flag(), sizeof(int), cudaMemcpyDeviceToHost, s));
             KL_CUDA(cudaStreamSynchronize(s));
             *deficient = (flags[0] != 0);
@@ -207,6 +209,7 @@ struct Eig {
         // gemm_tall computes C[r, :] = A[r, :] B with A = R2 (b x b, ld b), B = R1.
         cudaError_t e = launch_gemm_tall(1.0, Rtmp(), b, b, b, R1(), b, b, 0.0, R(), b, s);
         if (e != cudaSuccess) return cuda_fail(e, "R product");
+        KL_TRY(host_wait(h, s));
         KL_CUDA(cudaMemcpyAsync(flags, Flag(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         KL_CUDA(cudaStreamSynchronize(s));
         *deficient = (flags[0] != 0);
@@ -232,6 +235,7 @@ struct Eig {
             cur = out;
             ccur = cout;
         }
+        KL_TRY(host_wait(h, s));
         KL_CUDA(cudaMemcpyAsync(flags, Flag(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         KL_CUDA(cudaStreamSynchronize(s));
         *deficient = (flags[0] != 0 || flags[1] != 0);
@@ -346,6 +350,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
                 e = launch_residual_norms(E.G(), b, E.S(), E.mmax, j - b, b, nc, E.Est(), E.s);
                 if (e != cudaSuccess) return cuda_fail(e, "residual norms");
                 std::vector<double> th(nc), rs(nc);
+                KL_TRY(host_wait(E.h, E.s));
                 KL_CUDA(cudaMemcpyAsync(th.data(), E.Theta(), nc * sizeof(double), cudaMemcpyDeviceToHost, E.s));
                 KL_CUDA(cudaMemcpyAsync(rs.data(), E.Est(), nc * sizeof(double), cudaMemcpyDeviceToHost, E.s));
                 KL_CUDA(cudaStreamSynchronize(E.s));
@@ -394,6 +399,7 @@ kl_status run_phase(Eig& E, const Phase& P, int k, int j0, int* restarts, std::v
         const int nk = std::min(P.keep, j);
         e = launch_residual_norms(E.G(), b, E.S(), E.mmax, j - b, b, nk, E.Est(), E.s);
         if (e != cudaSuccess) return cuda_fail(e, "residual norms");
+        KL_TRY(host_wait(E.h, E.s));
         KL_CUDA(cudaMemcpyAsync(theta.data(), E.Theta(), j * sizeof(double), cudaMemcpyDeviceToHost, E.s));
         KL_CUDA(cudaMemcpyAsync(est.data(), E.Est(), nk * sizeof(double), cudaMemcpyDeviceToHost, E.s));
         KL_CUDA(cudaStreamSynchronize(E.s));
@@ -479,6 +485,7 @@ kl_status run_lobpcg(Eig& E, int prec, int nx, int k, double tol, int maxit, boo
         // ---- convergence of the k wanted pairs ----
         e = launch_ritz_resid(AV, V, N, N, nx, E.Theta(), E.Part(), E.maxparts, E.Est(), E.s);
         if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
+        KL_TRY(host_wait(E.h, E.s));
         KL_CUDA(cudaMemcpyAsync(theta.data(), E.Theta(), nx * sizeof(double), cudaMemcpyDeviceToHost, E.s));
         KL_CUDA(cudaMemcpyAsync(est.data(), E.Est(), nx * sizeof(double), cudaMemcpyDeviceToHost, E.s));
         KL_CUDA(cudaStreamSynchronize(E.s));
@@ -568,6 +575,7 @@ static kl_status finish_eigs(kl_handle h, Eig& E, const kl_eig_opts& o, int k, d
         KL_CUDA(cudaMemcpyAsync(E.Theta(), theta.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
         e = launch_ritz_resid(AY, E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
         if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
+        KL_TRY(host_wait(h, s));
         KL_CUDA(cudaMemcpyAsync(resid.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
     if (evecs_dev) {
@@ -655,6 +663,7 @@ static kl_status lobpcg_impl(kl_handle h, int k, double tol, const kl_eig_opts& 
         if (e == cudaSuccess) e = launch_gram(E.W(), N, nx, E.W(), N, nx, N, E.G(), nx, E.Part(), E.maxparts, s);
         if (e != cudaSuccess) return cuda_fail(e, "start block");
         std::vector<double> g(size_t(nx) * nx);
+        KL_TRY(host_wait(h, s));
         KL_CUDA(cudaMemcpyAsync(g.data(), E.G(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         KL_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < nx; ++i)
@@ -773,6 +782,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
         if (e == cudaSuccess) e = launch_gram(E.W(), N, nst, E.W(), N, nst, N, E.G(), nst, E.Part(), E.maxparts, s);
         if (e != cudaSuccess) return cuda_fail(e, "start block");
         std::vector<double> g(size_t(nst) * nst);
+        KL_TRY(host_wait(h, s));
         KL_CUDA(cudaMemcpyAsync(g.data(), E.G(), g.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         KL_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < nst; ++i)
@@ -870,6 +880,7 @@ kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts_in, 
             e = launch_ritz_resid(E.AV(), E.V(), N, N, k, E.Theta(), E.Part(), E.maxparts, E.Est(), s);
             if (e != cudaSuccess) return cuda_fail(e, "ritz residuals");
             std::vector<double> rx(k);
+            KL_TRY(host_wait(h, s));
             KL_CUDA(cudaMemcpyAsync(rx.data(), E.Est(), k * sizeof(double), cudaMemcpyDeviceToHost, s));
             KL_CUDA(cudaStreamSynchronize(s));
             bool ok = true;   // rx holds ||A~'y - theta y|| / |theta|

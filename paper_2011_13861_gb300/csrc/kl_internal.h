@@ -255,6 +255,7 @@ struct kl_handle_s {
     std::vector<double> J_host;  // Nt: J = sqrt(det DF) at the Greville points
     kl::BatchRendezvous* batch = nullptr;   // set while kl_eigs_batched solves this instance
     cudaEvent_t batch_ready = nullptr;       // u of this instance is ready for the batched stage 5
+    cudaEvent_t host_sync = nullptr;         // blocking-sync event of host_wait inside a batched solve
     // device set-up data
     double* dCt[3] = {nullptr, nullptr, nullptr};   // forward operator of mode k, layout n_k x nt_k
     double* dC[3] = {nullptr, nullptr, nullptr};    // backward operator of mode k, layout nt_k x n_k
@@ -288,6 +289,12 @@ kl_status covmv_impl(kl_handle h, int precision, const double* u, int64_t ldu, d
 kl_status backward_impl(kl_handle h, const double* z, int64_t ldz, double* y, int64_t ldy,
                         int nvec, bool zHasJ, cudaStream_t s);
 kl_status check_device_status(kl_handle h, cudaStream_t s);
+// Called before a synchronous device-to-host read on `s`.  Inside kl_eigs_batched (one host
+// thread per instance, usually more threads than cores) it returns once `s` has drained, the
+// thread asleep on a blocking-sync event rather than spinning, so that the instances with work
+// to issue get the cores; otherwise it does nothing and the read itself waits (spinning: the
+// lowest latency for a lone solve).
+kl_status host_wait(kl_handle h, cudaStream_t s);
 kl_status eigs_impl(kl_handle h, int k, double tol, const kl_eig_opts* opts, double* evals_host,
                     double* evecs_dev, int64_t ldv, kl_eig_info* info, cudaStream_t s);
 

@@ -17,6 +17,12 @@ prints the measured float64/float32 FMA and MUFU ex2/rsqrt rates (kl_pipe_rates)
 
 times training steps of the warm-start network (4 inputs, 4 x 256 tanh, 32 x 6,859 outputs) on
 seeded synthetic inputs and targets: one warm-up epoch, then `reps` epochs of 256 samples.
+
+  python profile_kernels.py --annulus 64 [--annulus-sequential]
+
+solves the first 64 seeded quarter-annulus instances of the batched workload (10 eigenpairs each,
+residual 1e-8, mixed method, block 4, tensor-core float64-class polish) once, together through
+kl_eigs_batched or one after another, and prints the wall time and the summed solver counters.
 """
 import argparse
 import json
@@ -64,6 +70,31 @@ def contract(a):
     print(json.dumps({"workload": a.workload, "nvec": a.nvec, "N": G.N, "Ntilde": G.Nt, "ms": out}))
 
 
+def annulus(a):
+    import time
+    net = inputs.quarter_annulus_net()
+    cases = inputs.batched_instances(64)[:a.annulus]
+    Gs = [kl.KLProblem(c["dim"], c["p"], c["ne"], kernel=c["kernel"], L=c["L"], sigma=c["sigma"], nurbs=net)
+          for c in cases]
+    opts = dict(method=1, block=4, precision=kl.KL_P_TC64, want_vectors=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if a.annulus_sequential:
+        infos = [G.eigs(10, 1e-8, **opts)[2] for G in Gs]
+        bi = None
+    else:
+        _, _, infos, _, bi = kl.eigs_batched(Gs, 10, 1e-8, **opts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    keys = ("applies", "block_applies", "restarts", "ms_fp32_phase", "ms_stage5_fp32", "ms_stage5_tc32",
+            "ms_stage5_tc64")
+    print(json.dumps({"instances": len(Gs), "sequential": a.annulus_sequential, "wall_s": wall,
+                      "converged_all": all(i["converged"] >= 10 for i in infos),
+                      "sums": {k: sum(i[k] for i in infos) for k in keys}, "batch": bi}))
+    for G in Gs:
+        G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cube-p2-32^3-exp-L0.5")
@@ -87,6 +118,8 @@ def main():
     ap.add_argument("--sym-slot-limit", type=int, default=None,
                     help="bytes of the one-launch symmetric schedule's slots (kl_set_sym_slot_limit)")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--annulus", type=int, default=0, help="solve this many batched-workload instances (1..64)")
+    ap.add_argument("--annulus-sequential", action="store_true", help="--annulus one instance after another")
     ap.add_argument("--accurate", default="df64", choices=["fp64", "df64", "tc64"],
                     help="accurate-phase arithmetic of --solve plain_df / mixed")
     a = ap.parse_args()
@@ -98,6 +131,8 @@ def main():
         return mlp_train(a)
     if a.contract:
         return contract(a)
+    if a.annulus:
+        return annulus(a)
     if a.peaks:
         print(json.dumps(kl.pipe_rates()))
         return
