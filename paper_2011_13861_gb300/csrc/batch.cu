@@ -54,7 +54,13 @@ struct BatchHdr {
 
 namespace {
 
-constexpr int kBRows = 128;   // rows per item, one per thread
+constexpr int kBRows = 128;   // threads per CTA; rows per double-float item (one a thread)
+// rows a thread of a float32 item: two (rows t and t + 128) up to 16 vectors, so that each
+// shared-memory read of a column serves two kernel evaluations; one for wider groups, whose
+// packed sums would need twice the registers
+constexpr int rows_f32(int nv) { return nv <= 16 ? 2 : 1; }
+// rows of one work item
+inline int item_rows(int prec, int nv) { return prec == KL_P_FP32 ? kBRows * rows_f32(nv) : kBRows; }
 constexpr int kBTile = 128;   // column tile staged in shared memory
 
 __device__ __forceinline__ int find_req_item(const BatchReq* reqs, int nreq, int64_t item) {
@@ -176,24 +182,35 @@ batch_df_kernel(const BatchHdr* __restrict__ hdr, const BatchReq* __restrict__ r
 template <int KIND, int NV>
 __device__ void f32_item(const BatchReq& q, int64_t rb, int64_t sp, double* __restrict__ part, float4* sp3,
                          float (*su)[NV]) {
+    constexpr int ROWS = rows_f32(NV);
     const CovParams& cp = q.cp;
     const int64_t Nt = cp.Nt;
     const float* U = static_cast<const float*>(q.U);
     const float* P = cp.P32;
-    const int64_t row = rb * kBRows + threadIdx.x;
-    const bool valid = row < Nt;
-    const float x0 = valid ? P[row] : 0.f, y0 = valid ? P[cp.ldp + row] : 0.f, z0 = valid ? P[2 * cp.ldp + row] : 0.f;
+    int64_t row[ROWS];
+    float x0[ROWS], y0[ROWS], z0[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        row[r] = rb * (kBRows * ROWS) + threadIdx.x + r * kBRows;
+        const bool valid = row[r] < Nt;
+        x0[r] = valid ? P[row[r]] : 0.f;
+        y0[r] = valid ? P[cp.ldp + row[r]] : 0.f;
+        z0[r] = valid ? P[2 * cp.ldp + row[r]] : 0.f;
+    }
     const int64_t c_begin = sp * q.cps;
     int64_t c_end = c_begin + q.cps;
     if (c_end > Nt) c_end = Nt;
     // even widths: the sums of vectors (v, v + 1) in one 64-bit register pair, one packed FMA
     constexpr bool PACK = (NV % 2 == 0);
-    float acc[PACK ? 1 : NV];
-    unsigned long long acc2[PACK ? NV / 2 : 1];
+    float acc[ROWS][PACK ? 1 : NV];
+    unsigned long long acc2[ROWS][PACK ? NV / 2 : 1];
 #pragma unroll
-    for (int v = 0; v < (PACK ? 1 : NV); ++v) acc[v] = 0.f;
+    for (int r = 0; r < ROWS; ++r) {
 #pragma unroll
-    for (int w = 0; w < (PACK ? NV / 2 : 1); ++w) acc2[w] = 0ull;
+        for (int v = 0; v < (PACK ? 1 : NV); ++v) acc[r][v] = 0.f;
+#pragma unroll
+        for (int w = 0; w < (PACK ? NV / 2 : 1); ++w) acc2[r][w] = 0ull;
+    }
     for (int64_t c0 = c_begin; c0 < c_end; c0 += kBTile) {
         __syncthreads();
         const int64_t c = c0 + threadIdx.x;
@@ -206,27 +223,43 @@ __device__ void f32_item(const BatchReq& q, int64_t rb, int64_t sp, double* __re
 #pragma unroll 4
         for (int j = 0; j < jmax; ++j) {
             const float4 p = sp3[j];
-            const float g = kernel32<KIND>(x0 - p.x, y0 - p.y, z0 - p.z, x0, y0, z0, p.x, p.y, p.z, cp.poly_m);
-            if constexpr (PACK) {
-                const unsigned long long g2 = f2_dup(g);
+            float g[ROWS];
 #pragma unroll
-                for (int w = 0; w < NV / 2; ++w)
-                    acc2[w] = f2_fma(g2, *reinterpret_cast<const unsigned long long*>(&su[j][2 * w]), acc2[w]);
+            for (int r = 0; r < ROWS; ++r)
+                g[r] = kernel32<KIND>(x0[r] - p.x, y0[r] - p.y, z0[r] - p.z, x0[r], y0[r], z0[r], p.x, p.y, p.z,
+                                      cp.poly_m);
+            if constexpr (PACK) {
+                unsigned long long g2[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) g2[r] = f2_dup(g[r]);
+#pragma unroll
+                for (int w = 0; w < NV / 2; ++w) {
+                    const unsigned long long uu = *reinterpret_cast<const unsigned long long*>(&su[j][2 * w]);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) acc2[r][w] = f2_fma(g2[r], uu, acc2[r][w]);
+                }
             } else {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] = fmaf(g, su[j][v], acc[v]);
+                for (int v = 0; v < NV; ++v) {
+                    const float uu = su[j][v];
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) acc[r][v] = fmaf(g[r], uu, acc[r][v]);
+                }
             }
         }
     }
-    if (valid) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            float a;
-            if constexpr (PACK)
-                a = (v & 1) ? f2_hi(acc2[v >> 1]) : f2_lo(acc2[v >> 1]);
-            else
-                a = acc[v];
-            if (v < q.nv) part[q.part_off + (sp * q.nv + v) * Nt + row] = double(a);
+    for (int r = 0; r < ROWS; ++r) {
+        if (row[r] < Nt) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                float a;
+                if constexpr (PACK)
+                    a = (v & 1) ? f2_hi(acc2[r][v >> 1]) : f2_lo(acc2[r][v >> 1]);
+                else
+                    a = acc[r][v];
+                if (v < q.nv) part[q.part_off + (sp * q.nv + v) * Nt + row[r]] = double(a);
+            }
         }
     }
 }
@@ -356,7 +389,7 @@ namespace {
 constexpr int kMaxSplits = 16;
 
 // fill the table for a column split size; returns the partial-sum doubles needed
-size_t build_table(const std::vector<BatchRequest>& reqs, int prec, long long cps_target, BatchHdr* hdr,
+size_t build_table(const std::vector<BatchRequest>& reqs, int rows_per_item, long long cps_target, BatchHdr* hdr,
                    BatchReq* tbl) {
     int64_t item = 0, out = 0;
     size_t part = 0;
@@ -381,7 +414,7 @@ size_t build_table(const std::vector<BatchRequest>& reqs, int prec, long long cp
         q.item_begin = item;
         q.part_off = int64_t(part);
         q.out_begin = out;
-        item += ((Nt + kBRows - 1) / kBRows) * q.splits;
+        item += ((Nt + rows_per_item - 1) / rows_per_item) * q.splits;
         part += size_t(q.splits) * size_t(r.nv) * size_t(Nt);
         out += int64_t(r.nv) * Nt;
     }
@@ -389,7 +422,6 @@ size_t build_table(const std::vector<BatchRequest>& reqs, int prec, long long cp
     hdr->pad = 0;
     hdr->total_items = item;
     hdr->total_out = out;
-    (void)prec;
     return part;
 }
 
@@ -416,7 +448,7 @@ kl_status run_batch_nv(BatchExec& X, const std::vector<BatchRequest>& reqs, int 
             sl.cap = tbl_bytes * 2;
         }
         BatchReq* tbl = reinterpret_cast<BatchReq*>(sl.host + 1);
-        const size_t part_doubles = build_table(reqs, prec, cps, sl.host, tbl);
+        const size_t part_doubles = build_table(reqs, item_rows(prec, NV), cps, sl.host, tbl);
         if (sl.host->total_items > 2147483647LL) return fail(KL_ERR_INVALID_ARG, "batch too large (work items)");
         if (X.part.bytes < part_doubles * sizeof(double) || X.table.bytes < tbl_bytes) {
             KL_CUDA(cudaStreamSynchronize(s));
