@@ -279,8 +279,9 @@ typedef struct {
 
 /* ---- Many independent problems at once (no counterpart in the paper) ----------------
  * The instances (each its own kl_handle: size, degree, kernel, geometry may all differ) share
- * one persistent launch of stage 5 per step: items of 128 rows x a column range of every
- * instance are taken from a global work counter, the kernel kind is read per item, and the
+ * one persistent launch of stage 5 per step: items of 128 rows (256 in float32 up to 16
+ * vectors: two rows a thread) x a column range of every instance are taken from a global
+ * work counter, the kernel kind is read per item, and the
  * launch sequence is replayed from a captured CUDA graph; the column-range size is chosen by
  * timing candidates on the first batch.  Arithmetic as in KL_P_FP32 / KL_P_DF64. */
 
@@ -302,8 +303,12 @@ typedef struct {
 /* kl_eigs for count instances with the same k, tol and options (opts may be NULL): one host
  * thread and one CUDA stream per instance run the solver of kl_eigs; every KL_P_FP32 and
  * KL_P_DF64 operator application of every instance joins a rendezvous, and the last instance
- * to arrive launches the batched stage 5 for all of them (instances that finish leave the
- * rendezvous).  evals_host: count x k (row i = instance i); evecs_dev: NULL or count device
+ * to arrive launches the batched stage 5 for all of them, or the first one whose batching
+ * window has passed (200 microseconds; the environment variable KL_BATCH_WINDOW_US overrides
+ * it, a negative value waits for every instance); instances that finish leave the
+ * rendezvous.  Instance threads wait for the device asleep (blocking-sync events), not
+ * spinning, so more instances than host cores is fine.
+ * evals_host: count x k (row i = instance i); evecs_dev: NULL or count device
  * pointers (NULL entries allowed), leading dimensions ldv (NULL: N_i); infos, statuses,
  * binfo may be NULL.  Synchronous.  Returns the first non-KL_OK instance status (statuses[i]
  * holds every instance's), e.g. KL_ERR_NOT_CONVERGED. */
